@@ -1,0 +1,100 @@
+"""Pins of the oracle's turbo loop and TB handling: noiseless decoding in one
+iteration for every window count, the failure convention (max_iter + 1), the
+TB-fails-if-any-CB-fails rule, filler handling and HARQ combining."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def noiseless(e, amp=127):
+    return np.where(e == 0, amp, -amp).astype(np.int8)
+
+
+@pytest.mark.parametrize("P", [1, 2, 8, 64, 768])
+def test_noiseless_single_cb_one_iteration(orc, P):
+    A, G = 6120, 18444
+    a = synth.bits(0, 0, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    bits, res, _ = orc.decode_tb(noiseless(e), A, G, Qm=2, P=P)
+    assert res["cb_iters"] == [1] and res["tb_crc_ok"] and np.array_equal(bits, a)
+
+
+@pytest.mark.parametrize("A", [16, 40, 1000, 6120, 6128, 12000, 20000, 75376])
+def test_noiseless_tb_round_trip(orc, A):
+    s = orc.segment(A + 24)
+    G = 2 * ((3 * (A + 24 + 24 * s["C"]) + 40) // 2)
+    a = synth.bits(1, A, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    bits, res, _ = orc.decode_tb(noiseless(e), A, G, Qm=2, P=4)
+    assert res["tb_crc_ok"] and np.array_equal(bits, a)
+    assert res["cb_iters"] == [1] * s["C"]
+    assert (res["C"], res["Kp"], res["F"]) == (s["C"], s["Kp"], s["F"])
+
+
+def test_failure_convention_and_exact_iterations(orc):
+    A, G = 1000, 3200
+    a = synth.bits(2, 0, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    noise = synth.randint(2, 1, G, -127, 127).astype(np.int8)
+    _, res, _ = orc.decode_tb(noise, A, G, Qm=2, max_iter=4)
+    assert res["cb_iters"] == [5] and not res["tb_crc_ok"]
+    # early stop off: a decodable block reports exactly max_iter
+    _, res, _ = orc.decode_tb(noiseless(e), A, G, Qm=2, max_iter=6, early_stop=False)
+    assert res["cb_iters"] == [6] and res["tb_crc_ok"]
+
+
+def test_tb_fails_if_one_cb_fails(orc):
+    A = 20000
+    s = orc.segment(A + 24)
+    assert s["C"] == 4
+    G = 2 * 3 * (A + 24 + 96)
+    a = synth.bits(3, 0, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    llr = noiseless(e)
+    Es = [orc.e_r(G, 2, 1, s["C"], r) for r in range(s["C"])]
+    off = sum(Es[:2])
+    llr[off:off + Es[2]] = synth.randint(3, 1, Es[2], -127, 127)
+    bits, res, _ = orc.decode_tb(llr, A, G, Qm=2, max_iter=3)
+    assert res["cb_crc_ok"] == [True, True, False, True] and not res["tb_crc_ok"]
+    assert res["cb_iters"][2] == 4
+
+
+def test_awgn_single_cb_and_windows_agree_on_success(orc):
+    # Single-code-block workload at Eb/N0 = 1 dB: P = 1 decodes; P > 1 also
+    # decodes (possibly in more iterations).
+    A, G = 6120, 18444
+    a = synth.bits(0, 0, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    llr = synth.channel_llrs(e, 1, synth.sigma2_ebn0(1.0, A / G), 0, 1)
+    for P in (1, 8, 64):
+        bits, res, _ = orc.decode_tb(llr, A, G, Qm=2, P=P, max_iter=8)
+        assert res["tb_crc_ok"] and np.array_equal(bits, a), P
+
+
+def test_harq_retransmission_combines(orc):
+    A, G = 2000, 2400  # rate ~0.84 QPSK
+    a = synth.bits(5, 0, A)
+    sig = synth.sigma2_snr(1.0)
+    e0 = orc.encode_tb(a, G, Qm=2, rv=0)
+    e2 = orc.encode_tb(a, G, Qm=2, rv=2)
+    l0 = synth.channel_llrs(e0, 2, sig, 5, 1)
+    l2 = synth.channel_llrs(e2, 2, sig, 5, 2)
+    _, r0, soft = orc.decode_tb(l0, A, G, Qm=2, rv=0, max_iter=6)
+    assert not r0["tb_crc_ok"]
+    bits, r2, _ = orc.decode_tb(l2, A, G, Qm=2, rv=2, max_iter=6, soft=soft)
+    assert r2["tb_crc_ok"] and np.array_equal(bits, a)
+    _, r2alone, _ = orc.decode_tb(l2, A, G, Qm=2, rv=2, max_iter=6)
+    assert not r2alone["tb_crc_ok"]
+
+
+def test_filler_bits_are_known_zeros(orc):
+    A = 6128  # B = 6152 > 6144: C = 2
+    s = orc.segment(A + 24)
+    assert s["C"] == 2 and s["F"] > 0
+    c_len = s["Kp"] if s["Cm"] == 0 else s["Km"]
+    G = 2 * 3 * (A + 100)
+    a = synth.bits(6, 0, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    bits, res, _ = orc.decode_tb(noiseless(e, 60), A, G, Qm=2, P=2)
+    assert res["tb_crc_ok"] and np.array_equal(bits, a) and c_len > 0
