@@ -409,8 +409,9 @@ int orc_derm_cb(const int8_t* e, int E, int K, int F, int rv, int new_data, int8
 /*    saturated: alpha[s] = sat16(m[s] - m[0]).  Same for beta.        */
 /*  * Lambda = sat16(max_{u=0}(alpha+gamma+beta) - max_{u=1}(...)),    */
 /*    sums exact; Le = sat16(Lambda - S).                              */
-/*  * windows: P windows with boundaries floor(p*K/P); window 0 starts */
-/*    from the known state 0, the last window's beta comes from the    */
+/*  * windows: window p covers [p*W, min((p+1)*W, K)), W = ceil(K/P),  */
+/*    P clamped to [1, K/8].  Window 0 starts from the known state 0,  */
+/*    the last window's beta comes from the                            */
 /*    terminated tail; interior boundaries take zeros on the first     */
 /*    iteration and, later, the boundary metrics the neighbouring      */
 /*    window computed on the previous iteration of the same decoder.   */
@@ -476,8 +477,9 @@ static void siso(int K, const int8_t* Ls, const int8_t* Lp, const int16_t* La, c
     int16_t (*alpha)[8] = malloc(sizeof(*alpha) * (size_t)(K + 1));
     int16_t (*na)[8] = calloc((size_t)P, sizeof(*na));
     int16_t (*nb)[8] = calloc((size_t)P, sizeof(*nb));
+    int W = (K + P - 1) / P;
     for (int p = 0; p < P; p++) {
-        int lo = (int)((int64_t)p * K / P), hi = (int)((int64_t)(p + 1) * K / P);
+        int lo = p * W, hi = (p + 1) * W < K ? (p + 1) * W : K;
         /* forward */
         for (int s = 0; s < 8; s++) {
             if (p == 0) alpha[lo][s] = (int16_t)(s == 0 ? 0 : ORC_MINF);
@@ -527,11 +529,14 @@ static void siso(int K, const int8_t* Ls, const int8_t* Lp, const int16_t* La, c
     free(nb);
 }
 
+/* Window count actually used: P is clamped to [1, K/8]; windows have length
+ * W = ceil(K/P) except the last one, so ceil(K/W) of them are non-empty. */
 int orc_windows(int K, int P)
 {
     if (P > K / 8) P = K / 8;
     if (P < 1) P = 1;
-    return P;
+    int W = (K + P - 1) / P;
+    return (K + W - 1) / W;
 }
 
 /* A single SISO pass with explicit boundary seeds, exposed for tests.
