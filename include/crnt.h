@@ -1,0 +1,202 @@
+/*
+ * crnt.h -- C ABI of the GB300 (sm_103a) LTE uplink channel-decoding library.
+ *
+ * The library decodes the uplink shared-channel transport blocks (TBs) of
+ * many UEs and cells on one GPU: code-block segmentation, de-rate-matching
+ * with HARQ soft combining, fixed-point max-log-MAP turbo decoding with a
+ * CRC stop, and TB reassembly -- the channel-decoding function whose
+ * parallelisation by UE and by code block (CB) is the subject of
+ * "Higher aggregation of gNodeBs in Cloud-RAN architectures via parallel
+ * computing" (Sec. IV-B "Decoding function", Fig. 4; Algorithms 1-2).  The
+ * downlink turbo encoder and rate matcher (Sec. IV-B "Encoding function",
+ * Fig. 3) are provided too.  Numeric definitions follow TS 36.212 (CRC
+ * Sec. 5.1.1, segmentation Sec. 5.1.2, turbo code Sec. 5.1.3.2, rate
+ * matching Sec. 5.1.4.1).
+ *
+ * Conventions for every entry point:
+ *  - LLRs are int8, L = log P(bit=0)/P(bit=1) scaled by the caller (BPSK
+ *    0 -> +1); -128 is treated as -127.  Hard decision: bit = (L < 0).
+ *  - TB bits are packed MSB first, A/8 bytes per TB; A must be a multiple
+ *    of 8 in [16, 75376] (all LTE TB sizes are).
+ *  - Coded bits produced by the encoder are one bit per byte (0/1).
+ *  - Buffers are owned by the caller unless stated otherwise.  Pointers may
+ *    be host or device memory where a function says so; the library finds
+ *    out which with cudaPointerGetAttributes.
+ *  - Every function returns CRNT_OK (0) or a negative CRNT_E* code and
+ *    never throws across the ABI.  A TB that fails its CRC is not an error:
+ *    it is reported in crnt_tb_result.tb_crc_ok.
+ */
+#ifndef CRNT_H
+#define CRNT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRNT_VERSION 1
+
+#define CRNT_OK 0
+#define CRNT_EINVAL (-1)    /* malformed argument */
+#define CRNT_ENOMEM (-2)    /* device or host allocation failed / budget exceeded */
+#define CRNT_EAGAIN (-3)    /* admission refused for now: retry later */
+#define CRNT_ETIMEDOUT (-4) /* a bounded wait expired */
+#define CRNT_EDEVICE (-5)   /* CUDA error: the context should be destroyed */
+#define CRNT_ENOTFOUND (-6) /* no such ticket / HARQ process */
+
+#define CRNT_MAX_CB 16     /* code blocks per TB supported (A <= 75376 needs 13) */
+#define CRNT_MAX_P 128     /* windows per SISO pass */
+
+typedef struct crnt_ctx crnt_ctx;
+typedef struct crnt_plan crnt_plan;
+
+/* Context configuration.  Zero fields take the default in brackets. */
+typedef struct crnt_config {
+    int32_t device;          /* CUDA device ordinal [0] */
+    uint32_t harq_slots;     /* HARQ soft-buffer slots kept on the device [4096] */
+    uint64_t mem_budget;     /* device bytes for soft buffers + in-flight work [8 GiB] */
+    uint32_t max_inflight;   /* serving: TBs on the device at once [4096] */
+    uint32_t deadline_us;    /* serving: deadline for miss accounting [1000] */
+} crnt_config;
+
+/* Per-TB parameters (32 bytes). */
+typedef struct crnt_tb_params {
+    uint32_t A;          /* TB size in bits without CRC24A, multiple of 8, 16..75376 */
+    uint32_t G;          /* rate-matched bits (= LLRs) of the TB, multiple of Qm*NL */
+    uint16_t P;          /* windows per SISO pass, 0 = autotuned per K; clamped to
+                            [1, min(K/8, CRNT_MAX_P)] */
+    uint8_t Qm;          /* 2, 4 or 6 bits per modulation symbol (used for E_r) */
+    uint8_t NL;          /* 1 or 2 layers */
+    uint8_t rv;          /* redundancy version 0..3 */
+    uint8_t max_iter;    /* 1..16 turbo iterations */
+    uint8_t early_stop;  /* 1: stop each CB at its first CRC pass */
+    uint8_t new_data;    /* 1: clear the HARQ soft buffer before combining */
+    uint32_t cell, ue, harq_pid; /* HARQ process key (flags bit 0 set) */
+    uint32_t flags;      /* bit 0 (CRNT_F_HARQ): combine into the library-owned
+                            soft buffer of (cell, ue, harq_pid) */
+} crnt_tb_params;
+
+#define CRNT_F_HARQ 1u
+
+/* Per-TB result (80 bytes). */
+typedef struct crnt_tb_result {
+    int32_t status;                 /* CRNT_OK or a negative code for this TB */
+    uint8_t tb_crc_ok;              /* 1: every CB CRC and the TB CRC24A passed */
+    uint8_t C;                      /* code blocks */
+    uint16_t K_plus, K_minus, F;    /* segmentation (TS 36.212 5.1.2) */
+    uint8_t cb_iters[CRNT_MAX_CB];  /* iterations run per CB; max_iter+1 = failure
+                                       (the paper's loss convention, Sec. IV-B) */
+    uint8_t cb_crc_ok[CRNT_MAX_CB];
+    uint16_t P_used;                /* window count requested after clamping, for K+ */
+    uint16_t pad0;
+    uint64_t ticket;                /* serving ticket (0 elsewhere) */
+    uint64_t t_submit_ns, t_start_ns, t_done_ns; /* serving timestamps (CLOCK_MONOTONIC) */
+} crnt_tb_result;
+
+/* One code block of a TB as laid out by the library (host-side query). */
+typedef struct crnt_cb_layout {
+    uint32_t K, F, E, k0, Ncb;  /* size, filler, rate-matched length, start, buffer */
+    uint32_t llr_offset;        /* first LLR of the CB inside the TB's G LLRs */
+    uint32_t soft_offset;       /* first byte of its soft buffer inside the TB's */
+    uint32_t crc_b;             /* 1: CRC24B attached (C > 1) */
+    uint32_t P;                 /* window count after clamping (tb->P, or autotuned) */
+    uint32_t W;                 /* window length ceil(K/P); ceil(K/W) windows are used */
+} crnt_cb_layout;
+
+/* Aggregate sizes of a plan (host-side query). */
+typedef struct crnt_plan_info {
+    uint32_t n_tb, n_cb;
+    uint64_t llr_bytes;   /* sum of G: input LLRs, concatenated in TB order */
+    uint64_t out_bytes;   /* sum of A/8: output bytes, concatenated in TB order */
+    uint64_t info_bits;   /* sum of A */
+    uint64_t trellis_steps; /* sum of K over CBs (one SISO pass visits each once) */
+    uint64_t dbg_elems;   /* sum of (K+4) over CBs: length of the debug arrays */
+    uint32_t n_items, grid;
+} crnt_plan_info;
+
+/* ---- library ---------------------------------------------------------- */
+int crnt_version(void);
+const char* crnt_strerror(int code);
+
+/* ---- host-side parameter queries (no GPU needed) ---------------------- */
+
+/* QPP interleaver parameters (f1, f2) of CB size K (TS 36.212 Table
+ * 5.1.3-3; turbo interleaver of Sec. IV-B Figs. 3-4).  CRNT_EINVAL if K is
+ * not one of the 188 CB sizes. */
+int crnt_qpp_params(uint32_t K, uint32_t* f1, uint32_t* f2);
+
+/* Segmentation and rate-matching layout of one TB (TS 36.212 5.1.2 and
+ * 5.1.4.1; replaces the split loop of Algorithm 1).  cbs must hold
+ * CRNT_MAX_CB entries; *C receives the CB count.  Validates A, G, Qm, NL, rv
+ * as described at crnt_tb_params; CRNT_EINVAL otherwise. */
+int crnt_tb_layout(const crnt_tb_params* tb, crnt_cb_layout* cbs, uint32_t* C);
+
+/* ---- context ---------------------------------------------------------- */
+/* Create a context on cfg->device (NULL cfg = defaults).  Allocates the
+ * HARQ soft-buffer arena lazily.  CRNT_EDEVICE if CUDA is unusable. */
+int crnt_create(crnt_ctx** out, const crnt_config* cfg);
+/* Destroy a context and every plan and buffer it owns. */
+int crnt_destroy(crnt_ctx* ctx);
+
+/* ---- batched decode: one persistent launch per batch ------------------- */
+/* Plan a batch of n TBs: segmentation, per-CB parameters, the window count
+ * per K and the work queue (the device counterpart of Algorithms 1-2).
+ * Copies tbs; allocates the plan's device descriptors and result buffers.
+ * HARQ keys (CRNT_F_HARQ) are bound to soft-buffer slots here. */
+int crnt_plan_create(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan** out);
+int crnt_plan_get_info(const crnt_plan* plan, crnt_plan_info* info);
+/* Enqueue the decode of the planned batch on a CUDA stream (NULL = default):
+ * llr (device, llr_bytes) in, out (device, out_bytes) out.  Asynchronous,
+ * allocates nothing and may be captured in a CUDA graph.  The optional debug
+ * arrays (device, may be NULL) receive per CB at offset o = sum of (K+4) of
+ * the CBs before it in TB order: dbg_d[3o ..] the de-rate-matched streams
+ * d0|d1|d2 (K+4 int8 each), dbg_ext[o ..] the final exchanged extrinsic
+ * (K int16, natural order), dbg_hard[o ..] the final hard decisions (K). */
+int crnt_plan_launch(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream);
+int crnt_plan_launch_debug(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream,
+                           int8_t* dbg_d, int16_t* dbg_ext, uint8_t* dbg_hard);
+/* Wait for the stream and fill res[n] (host).  CRNT_EDEVICE on a CUDA error. */
+int crnt_plan_results(crnt_plan* plan, crnt_tb_result* res, void* stream);
+int crnt_plan_destroy(crnt_plan* plan);
+
+/* Blocking decode of n TBs.  llr: concatenated G LLRs of every TB (host or
+ * device); out: concatenated A/8 bytes (host or device); res: n results
+ * (host).  Host buffers are staged through the context's device arena. */
+int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, const int8_t* llr,
+                      uint8_t* out, crnt_tb_result* res);
+/* Blocking decode of one TB (n = 1 of the above). */
+int crnt_decode_tb(crnt_ctx* ctx, const int8_t* llr, const crnt_tb_params* tb, uint8_t* out,
+                   crnt_tb_result* res);
+
+/* ---- downlink encode (Sec. IV-B "Encoding function", Fig. 3) ------------ */
+/* Encode n TBs: CRC24A, segmentation with CRC24B and filler, turbo encode
+ * (2 RSC + QPP, trellis termination), sub-block interleave and bit
+ * selection from k0(rv).  bits: concatenated A/8 bytes per TB (host or
+ * device); e_out: concatenated G bytes (one coded bit per byte, host or
+ * device). */
+int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, const uint8_t* bits,
+                      uint8_t* e_out);
+int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb, uint8_t* e_out);
+
+/* ---- serving: continuous batching ------------------------------------- */
+/* Submit n TBs whose LLRs are host buffers llrs[i] (G_i bytes each).  The
+ * LLRs are copied before return.  Work starts on the device as soon as
+ * in-flight capacity and memory allow; tickets_out[i] receives a ticket.
+ * CRNT_EAGAIN when admission is refused (nothing of the call is queued). */
+int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* llrs, uint32_t n,
+                uint64_t* tickets_out);
+/* Collect up to max finished TBs, waiting at most timeout_us for the first.
+ * done[i] gets the result (ticket set); bits[i] a pointer to its A/8 output
+ * bytes, owned by the library and valid until the next crnt_poll.  Returns
+ * the number collected (>= 0) or a negative code. */
+int crnt_poll(crnt_ctx* ctx, crnt_tb_result* done, const uint8_t** bits, uint32_t max,
+              uint32_t timeout_us);
+/* Forget the soft buffer of a HARQ process.  CRNT_ENOTFOUND if unknown. */
+int crnt_harq_release(crnt_ctx* ctx, uint32_t cell, uint32_t ue, uint32_t harq_pid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRNT_H */

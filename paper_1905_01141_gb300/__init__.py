@@ -1,0 +1,281 @@
+"""Python binding of the GB300 LTE uplink decoding library (``libcrnt.so``).
+
+Argument marshalling only: every step of the decoding path runs in the
+library's CUDA kernels.  The C ABI is declared in ``include/crnt.h``; the
+names here mirror it.  Buffers may be numpy arrays (host) or torch tensors
+(host or CUDA); device buffers are passed by ``data_ptr()``.
+
+The shared library is built in-tree by ``build.build()`` into ``_build/``.
+Importing this module does not need a GPU; calls that do raise ``CrntError``
+when CUDA is unavailable.  There is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcrnt.so")
+
+OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEVICE, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+MAX_CB = 16
+MAX_P = 128
+F_HARQ = 1
+
+
+class CrntError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code) if _lib else "", code))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("harq_slots", ctypes.c_uint32),
+                ("mem_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("deadline_us", ctypes.c_uint32)]
+
+
+class TbParams(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_uint32), ("G", ctypes.c_uint32), ("P", ctypes.c_uint16),
+                ("Qm", ctypes.c_uint8), ("NL", ctypes.c_uint8), ("rv", ctypes.c_uint8),
+                ("max_iter", ctypes.c_uint8), ("early_stop", ctypes.c_uint8),
+                ("new_data", ctypes.c_uint8), ("cell", ctypes.c_uint32), ("ue", ctypes.c_uint32),
+                ("harq_pid", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class TbResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("tb_crc_ok", ctypes.c_uint8), ("C", ctypes.c_uint8),
+                ("K_plus", ctypes.c_uint16), ("K_minus", ctypes.c_uint16), ("F", ctypes.c_uint16),
+                ("cb_iters", ctypes.c_uint8 * MAX_CB), ("cb_crc_ok", ctypes.c_uint8 * MAX_CB),
+                ("P_used", ctypes.c_uint16), ("pad0", ctypes.c_uint16),
+                ("ticket", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
+                ("t_start_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+    def as_dict(self):
+        C = self.C
+        return dict(status=self.status, tb_crc_ok=bool(self.tb_crc_ok), C=C, Kp=self.K_plus,
+                    Km=self.K_minus, F=self.F, cb_iters=list(self.cb_iters[:C]),
+                    cb_crc_ok=[bool(x) for x in self.cb_crc_ok[:C]], P_used=self.P_used,
+                    ticket=self.ticket, t_submit_ns=self.t_submit_ns,
+                    t_start_ns=self.t_start_ns, t_done_ns=self.t_done_ns)
+
+
+class CbLayout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("K", "F", "E", "k0", "Ncb", "llr_offset", "soft_offset", "crc_b", "P", "W")]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_tb", ctypes.c_uint32), ("n_cb", ctypes.c_uint32),
+                ("llr_bytes", ctypes.c_uint64), ("out_bytes", ctypes.c_uint64),
+                ("info_bits", ctypes.c_uint64), ("trellis_steps", ctypes.c_uint64),
+                ("dbg_elems", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported C ABI.
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+SIGNATURES = {
+    "crnt_version": (ctypes.c_int, []),
+    "crnt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "crnt_qpp_params": (ctypes.c_int, [_U32, _P, _P]),
+    "crnt_tb_layout": (ctypes.c_int, [_P, _P, _P]),
+    "crnt_create": (ctypes.c_int, [_P, _P]),
+    "crnt_destroy": (ctypes.c_int, [_P]),
+    "crnt_plan_create": (ctypes.c_int, [_P, _P, _U32, _P]),
+    "crnt_plan_get_info": (ctypes.c_int, [_P, _P]),
+    "crnt_plan_launch": (ctypes.c_int, [_P, _P, _P, _P]),
+    "crnt_plan_launch_debug": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "crnt_plan_results": (ctypes.c_int, [_P, _P, _P]),
+    "crnt_plan_destroy": (ctypes.c_int, [_P]),
+    "crnt_decode_batch": (ctypes.c_int, [_P, _P, _U32, _P, _P, _P]),
+    "crnt_decode_tb": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "crnt_encode_batch": (ctypes.c_int, [_P, _P, _U32, _P, _P]),
+    "crnt_encode_tb": (ctypes.c_int, [_P, _P, _P, _P]),
+    "crnt_submit": (ctypes.c_int, [_P, _P, _P, _U32, _P]),
+    "crnt_poll": (ctypes.c_int, [_P, _P, _P, _U32, _U32]),
+    "crnt_harq_release": (ctypes.c_int, [_P, _U32, _U32, _U32]),
+}
+
+
+def load(path=None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError("libcrnt.so not built: run paper_1905_01141_gb300.build.build()")
+        L = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return load().crnt_strerror(code).decode()
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise CrntError(rc, what)
+    return rc
+
+
+def _ptr(x):
+    """Address of a numpy array / torch tensor / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def version():
+    return load().crnt_version()
+
+
+def qpp_params(K):
+    f1, f2 = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().crnt_qpp_params(K, ctypes.byref(f1), ctypes.byref(f2)), "crnt_qpp_params")
+    return f1.value, f2.value
+
+
+def make_params(A, G, Qm=2, NL=1, rv=0, max_iter=6, P=0, early_stop=1, new_data=1, cell=0,
+                ue=0, harq_pid=0, flags=0):
+    return TbParams(A=A, G=G, P=P, Qm=Qm, NL=NL, rv=rv, max_iter=max_iter,
+                    early_stop=early_stop, new_data=new_data, cell=cell, ue=ue,
+                    harq_pid=harq_pid, flags=flags)
+
+
+def params_array(tbs):
+    arr = (TbParams * len(tbs))()
+    for i, t in enumerate(tbs):
+        arr[i] = t if isinstance(t, TbParams) else make_params(**t)
+    return arr
+
+
+def tb_layout(tb):
+    cbs = (CbLayout * MAX_CB)()
+    C = ctypes.c_uint32()
+    t = tb if isinstance(tb, TbParams) else make_params(**tb)
+    _check(load().crnt_tb_layout(ctypes.byref(t), cbs, ctypes.byref(C)), "crnt_tb_layout")
+    keys = [f[0] for f in CbLayout._fields_]
+    return [{k: getattr(cbs[r], k) for k in keys} for r in range(C.value)]
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device=0, harq_slots=0, mem_budget=0, max_inflight=0, deadline_us=0):
+        L = load()
+        cfg = Config(device=device, harq_slots=harq_slots, mem_budget=mem_budget,
+                     max_inflight=max_inflight, deadline_us=deadline_us)
+        h = ctypes.c_void_p()
+        _check(L.crnt_create(ctypes.byref(h), ctypes.byref(cfg)), "crnt_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().crnt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def plan(self, tbs):
+        return Plan(self, tbs)
+
+    def decode_batch(self, tbs, llr, out):
+        """Blocking decode; llr/out host (numpy) or device (torch) buffers."""
+        arr = params_array(tbs)
+        res = (TbResult * len(arr))()
+        _check(load().crnt_decode_batch(self.h, arr, len(arr), _ptr(llr), _ptr(out), res),
+               "crnt_decode_batch")
+        return [r.as_dict() for r in res]
+
+    def encode_batch(self, tbs, bits, e_out):
+        arr = params_array(tbs)
+        _check(load().crnt_encode_batch(self.h, arr, len(arr), _ptr(bits), _ptr(e_out)),
+               "crnt_encode_batch")
+
+    def submit(self, tbs, llrs):
+        arr = params_array(tbs)
+        ptrs = (ctypes.c_void_p * len(arr))(*[_ptr(x) for x in llrs])
+        tickets = (ctypes.c_uint64 * len(arr))()
+        rc = load().crnt_submit(self.h, arr, ptrs, len(arr), tickets)
+        if rc == EAGAIN:
+            return None
+        _check(rc, "crnt_submit")
+        return list(tickets)
+
+    def poll(self, max_n=256, timeout_us=0, out_sizes=None):
+        """Returns a list of (result dict, bytes of the decoded TB)."""
+        res = (TbResult * max_n)()
+        bits = (ctypes.c_void_p * max_n)()
+        n = load().crnt_poll(self.h, res, bits, max_n, timeout_us)
+        if n < 0:
+            _check(n, "crnt_poll")
+        out = []
+        for i in range(n):
+            d = res[i].as_dict()
+            out.append((d, bits[i]))
+        return out
+
+    def harq_release(self, cell, ue, pid):
+        return load().crnt_harq_release(self.h, cell, ue, pid)
+
+
+class Plan:
+    """A planned batch: one persistent launch per call of ``launch``."""
+
+    def __init__(self, ctx, tbs):
+        self.ctx = ctx
+        self.params = params_array(tbs)
+        h = ctypes.c_void_p()
+        _check(load().crnt_plan_create(ctx.h, self.params, len(self.params), ctypes.byref(h)),
+               "crnt_plan_create")
+        self.h = h
+        inf = PlanInfo()
+        _check(load().crnt_plan_get_info(h, ctypes.byref(inf)), "crnt_plan_get_info")
+        self.info = {f[0]: getattr(inf, f[0]) for f in PlanInfo._fields_}
+
+    def launch(self, llr, out, stream=0, dbg_d=None, dbg_ext=None, dbg_hard=None):
+        if dbg_d is None and dbg_ext is None:
+            rc = load().crnt_plan_launch(self.h, _ptr(llr), _ptr(out), stream or None)
+        else:
+            rc = load().crnt_plan_launch_debug(self.h, _ptr(llr), _ptr(out), stream or None,
+                                               _ptr(dbg_d), _ptr(dbg_ext), _ptr(dbg_hard))
+        _check(rc, "crnt_plan_launch")
+
+    def results(self, stream=0):
+        res = (TbResult * len(self.params))()
+        _check(load().crnt_plan_results(self.h, res, stream or None), "crnt_plan_results")
+        return [r.as_dict() for r in res]
+
+    def close(self):
+        if self.h:
+            load().crnt_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

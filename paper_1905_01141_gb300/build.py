@@ -1,0 +1,66 @@
+"""Build the library: every CUDA translation unit of ``csrc/`` is compiled for
+sm_103a in parallel and linked into ``_build/libcrnt.so`` (in-tree)."""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libcrnt.so")
+UNITS = ["decode.cu", "encode.cu", "crnt_api.cu", "serve.cu"]
+NVCC = os.environ.get("NVCC", "nvcc")
+FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+         "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v"]
+
+
+def _units():
+    return [u for u in UNITS if os.path.exists(os.path.join(SRC, u))]
+
+
+def _deps():
+    return [os.path.join(SRC, f) for f in os.listdir(SRC)] + [
+        os.path.join(HERE, "..", "include", "crnt.h"), os.path.abspath(__file__)]
+
+
+def up_to_date():
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(d) <= t for d in _deps() if os.path.exists(d))
+
+
+def _compile(unit):
+    obj = os.path.join(OUT, unit + ".o")
+    cmd = [NVCC] + FLAGS + ["-c", os.path.join(SRC, unit), "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return unit, obj, r.returncode, r.stdout + r.stderr
+
+
+def build(force=False, verbose=False):
+    """Compile and link; returns the path of the shared library."""
+    if not force and up_to_date():
+        return LIB
+    os.makedirs(OUT, exist_ok=True)
+    units = _units()
+    with cf.ThreadPoolExecutor(max_workers=len(units)) as ex:
+        res = list(ex.map(_compile, units))
+    for unit, obj, rc, log in res:
+        if verbose or rc:
+            sys.stderr.write(log)
+        if rc:
+            raise RuntimeError("nvcc failed on %s" % unit)
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + \
+        [obj for _, obj, _, _ in res] + ["-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("link failed")
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

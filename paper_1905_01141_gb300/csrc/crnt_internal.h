@@ -1,0 +1,129 @@
+// crnt_internal.h -- descriptors shared by the host planner and the kernels.
+//
+// The host planner (crnt_api.cu) turns transport blocks into code-block (CB)
+// descriptors and work items; the decode kernel (decode.cu) and the encode
+// kernel (encode.cu) consume them.  Nothing here is part of the public C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace crnt {
+
+constexpr int kThreads = 128;          // threads per decode CTA
+constexpr int kCtasPerSm = 3;          // resident decode CTAs per SM (register-bound)
+constexpr int kSmemBudget = 72 * 1024; // dynamic smem per decode CTA
+constexpr int kMaxP = kThreads;        // windows per SISO pass (one thread each)
+constexpr int kSub = 4;                // sub-window length of the alpha recompute
+constexpr int kMaxK = 6144;
+constexpr int kMaxCb = 16;
+
+// One code block of a batch, fixed at plan time.
+struct CbDesc {
+  int32_t K, F, E, k0;     // CB size, filler bits, rate-matched length, start
+  int32_t P, W;            // windows and window length (W = ceil(K/P))
+  int32_t divM, divS;      // q / W == (q * divM) >> divS for 0 <= q < K + 4
+  int32_t f1, f2;          // QPP parameters
+  int32_t f2x2, f2x16, f2x128;  // 2 f2, 16 f2, 128 f2 (all mod K)
+  int32_t R, ND, Nv, rank0;     // sub-block rows, dummies, non-NULL count, rank of k0
+  uint32_t maskB, mask2;   // column masks of the rank formula (see derm)
+  int32_t tb;              // transport block index in the batch
+  int32_t r;               // CB index inside the TB
+  int64_t llr_off;         // byte offset of the CB's E LLRs in the LLR buffer
+  int64_t soft_off;        // byte offset of the CB's Ncb soft buffer, -1 = none
+  int32_t pay_bits;        // payload bits in the TB (K - F - L)
+  int32_t pay_off;         // TB bit offset of the payload (multiple of 8)
+  int32_t n_after;         // TB bits after the payload (for the TB CRC)
+  int32_t dbg_off;         // element offset of the CB in debug arrays
+  uint8_t crc_b;           // 1: CRC24B per CB (C > 1); 0: CRC24A (C == 1)
+  uint8_t max_iter, early_stop, new_data;
+  uint8_t pad0[4];
+};
+
+struct TbDesc {
+  int64_t out_off;  // byte offset of the TB's A/8 output bytes
+  int32_t A, C;
+  int32_t cb0;      // index of its first CB in the CB array (TB order)
+  int32_t pad0;
+};
+
+// A work item: n consecutive CBs (sorted order) of equal K and P, decoded
+// together by one CTA.
+struct WorkItem {
+  int32_t cb0, n;
+  int32_t smem_per_cb;
+  int32_t pad0;
+};
+
+// Per-batch device state written by the kernel.
+struct DecState {
+  int32_t head;       // work-queue head
+  int32_t err;        // first error code seen by a CTA (0 = none)
+};
+
+struct DecParams {
+  const CbDesc* cbs;      // sorted by work item
+  const TbDesc* tbs;
+  const WorkItem* items;
+  int32_t n_items, n_cbs, n_tbs;
+  const int8_t* llr;
+  uint8_t* out;
+  int8_t* soft;           // soft-buffer arena base
+  DecState* state;
+  int32_t* tb_done;       // [n_tbs] CBs finished
+  uint32_t* tb_crc;       // [n_tbs] xor of CRC24A contributions
+  uint8_t* cb_iters;      // [n_cbs] by sorted CB index
+  uint8_t* cb_ok;         // [n_cbs]
+  uint8_t* tb_ok;         // [n_tbs]
+  const uint32_t* xpowA;  // x^(32 s) mod gCRC24A, s < 2400
+  const uint32_t* xpowB;  // x^(32 s) mod gCRC24B, s < 200
+  int8_t* dbg_d;          // optional: [sum (K+4)] x 3 d-streams per CB
+  int16_t* dbg_ext;       // optional: [sum K] final extrinsic, natural order
+  uint8_t* dbg_hard;      // optional: [sum K] hard decisions
+};
+
+// Encoder launch description.
+struct EncCb {
+  int32_t K, F, E, k0;
+  int32_t R, ND;
+  int32_t f1, f2;
+  int32_t tb, r;
+  int32_t pay_bits, pay_off;  // payload bits and TB bit offset
+  int64_t e_off;              // output offset (bits, one per byte)
+  uint8_t crc_b;
+  uint8_t pad0[7];
+};
+
+struct EncParams {
+  const EncCb* cbs;
+  int32_t n_cbs;
+  const uint8_t* tb_bits;     // packed TB payload bits (MSB first), per TB at tb_in_off
+  const int64_t* tb_in_off;   // [n_tbs] byte offsets
+  const uint32_t* tb_crc;     // [n_tbs] CRC24A of each TB (computed by a first pass)
+  const int32_t* tb_A;        // [n_tbs]
+  uint8_t* e_out;
+  uint32_t* tb_crc_rw;        // writable alias of tb_crc for the CRC pass
+  const uint32_t* xpowA;
+};
+
+// Kernel launchers (decode.cu / encode.cu).
+cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s);
+int decode_max_smem();
+int decode_occupancy(int smem);  // resident decode CTAs per SM at this smem
+cudaError_t launch_encode(const EncParams& p, int n_tbs, cudaStream_t s);
+
+// Shared-memory bytes of one CB slot in the decode kernel.
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int dec_cb_smem(int K, int P, int W) {
+  int tp = W * P;                       // transposed array length (>= K)
+  int nck = (W + kSub - 1) / kSub;      // checkpoints per window
+  int nwords = (K + 31) / 32 + 1;       // hard-decision words
+  return align16(3 * tp)                // sys, par1, par2 (int8)
+         + align16(2 * tp)              // ext (int16)
+         + 16                           // 12 tail LLRs
+         + align16(4 * nwords)          // hard bits
+         + 4 * P * 16                   // alpha/beta seeds of both decoders
+         + P * nck * 16                 // alpha checkpoints
+         + 16;                          // per-CB flags
+}
+
+}  // namespace crnt

@@ -1,0 +1,696 @@
+// decode.cu -- fused uplink decode of a batch of LTE code blocks on sm_103a.
+//
+// One persistent launch decodes every CB of a batch of transport blocks:
+//   de-rate-matching + HARQ combining (the "decoder-bits conditioning" the
+//   paper counts in its pre-processing, Sec. V), the iterative turbo decoder
+//   (Sec. IV-B "Decoding function", Fig. 4: SISO1 -> interleave -> SISO2 ->
+//   de-interleave), the hard decision with a CRC stop after each iteration,
+//   and TB reassembly with the TB CRC24A check (a TB is good only when all of
+//   its CBs are, Sec. IV-B "Scheduler").  CTAs pull work items from a device
+//   queue, the GPU counterpart of the paper's FIFO thread pool (Algorithm 2).
+//
+// Arithmetic (identical to the CPU oracle, written independently):
+//   S = Ls + La, gamma(u,p) = [u=0] S + [p=0] Lp,
+//   alpha'[s] = sat16(m[s] - m[0]) with m[s] the exact best incoming sum,
+//   beta likewise, Lambda = sat16(best_u0 - best_u1), Le = sat16(Lambda - S),
+//   exchanged a-priori = floor(3 Le / 4).
+// Windows: W = ceil(K/P), window p = [pW, min(pW+W, K)), one thread each;
+// interior boundaries start from zeros, then from the neighbour's boundary
+// metrics of the previous iteration (next-iteration initialisation).
+//
+// Layout in shared memory (per CB slot): channel LLRs and the extrinsic are
+// stored transposed, element k at (k mod W) * P + k / W, so that the P
+// window threads of a warp touch consecutive addresses at every step.
+// Forward metrics are checkpointed every 8 steps and recomputed, 8 steps at a
+// time, into registers during the backward pass.
+#include <cstdint>
+#include "crnt_internal.h"
+
+namespace crnt {
+namespace {
+
+constexpr int MINF = -16384;
+constexpr uint32_t GA = 0x1864CFBu;  // gCRC24A with the D^24 term
+constexpr uint32_t GB = 0x1800063u;  // gCRC24B with the D^24 term
+
+// ---------------------------------------------------------------- trellis
+// State s = 4 r1 + 2 r2 + r3 of the 8-state RSC (g0 = 1+D^2+D^3 feedback,
+// g1 = 1+D+D^3).  Input u: register input a = u ^ r2 ^ r3, next state
+// (a, r1, r2), parity a ^ r1 ^ r3 = u ^ r1 ^ r2.
+__host__ __device__ constexpr int nxt(int s, int u) {
+  return (((u ^ (s >> 1) ^ s) & 1) << 2) | ((s >> 1) & 3);
+}
+__host__ __device__ constexpr int par(int s, int u) { return (u ^ (s >> 2) ^ (s >> 1)) & 1; }
+// branch-metric code: bit1 = [u == 0] (carries S), bit0 = [p == 0] (carries Lp)
+__host__ __device__ constexpr int gcode(int s, int u) {
+  return ((u == 0) ? 2 : 0) | ((par(s, u) == 0) ? 1 : 0);
+}
+
+// Predecessor k (k = r3 of the old state) of state n and its branch code.
+__host__ __device__ constexpr int pred(int n, int k) { return 2 * (n & 3) + k; }
+__host__ __device__ constexpr int pred_u(int n, int k) { return ((n >> 2) ^ n ^ k) & 1; }
+__host__ __device__ constexpr int pcode(int n, int k) { return gcode(pred(n, k), pred_u(n, k)); }
+
+constexpr bool check_pred() {
+  for (int n = 0; n < 8; n++)
+    for (int k = 0; k < 2; k++)
+      if (nxt(pred(n, k), pred_u(n, k)) != n) return false;
+  return true;
+}
+static_assert(check_pred(), "trellis predecessor formula");
+
+__device__ __forceinline__ int gval(int code, int S, int T, int Lp) {
+  return code == 3 ? T : code == 2 ? S : code == 1 ? Lp : 0;
+}
+
+// max(x0 + g0, x1 + g1) with the add folded into a DPX add-max when one of
+// the branch metrics is zero.
+__device__ __forceinline__ int acs2(int x0, int c0, int x1, int c1, int S, int T, int Lp) {
+  if (c1 == 0) return __viaddmax_s32(x0, gval(c0, S, T, Lp), x1);
+  if (c0 == 0) return __viaddmax_s32(x1, gval(c1, S, T, Lp), x0);
+  return __viaddmax_s32(x0, gval(c0, S, T, Lp), x1 + gval(c1, S, T, Lp));
+}
+
+// sat16(m - m0) given nm0 = -m0
+__device__ __forceinline__ int norm16(int m, int nm0) {
+  return max(__viaddmin_s32(m, nm0, 32767), -32768);
+}
+
+__device__ __forceinline__ void alpha_step(int a[8], int S, int T, int Lp) {
+  int m[8];
+#pragma unroll
+  for (int n = 0; n < 8; n++)
+    m[n] = acs2(a[pred(n, 0)], pcode(n, 0), a[pred(n, 1)], pcode(n, 1), S, T, Lp);
+  const int nm0 = -m[0];
+  a[0] = 0;
+#pragma unroll
+  for (int n = 1; n < 8; n++) a[n] = norm16(m[n], nm0);
+}
+
+__device__ __forceinline__ void beta_step(int b[8], int S, int T, int Lp) {
+  int m[8];
+#pragma unroll
+  for (int s = 0; s < 8; s++)
+    m[s] = acs2(b[nxt(s, 0)], gcode(s, 0), b[nxt(s, 1)], gcode(s, 1), S, T, Lp);
+  const int nm0 = -m[0];
+  b[0] = 0;
+#pragma unroll
+  for (int s = 1; s < 8; s++) b[s] = norm16(m[s], nm0);
+}
+
+// Terminating tail step: each state leaves on the branch that feeds a = 0.
+__device__ __forceinline__ void beta_tail_step(int b[8], int Ls, int Lp) {
+  int m[8];
+#pragma unroll
+  for (int s = 0; s < 8; s++) {
+    const int u = ((s >> 1) ^ s) & 1;  // r2 ^ r3
+    const int c = gcode(s, u);
+    m[s] = b[nxt(s, u)] + gval(c, Ls, Ls + Lp, Lp);
+  }
+  const int nm0 = -m[0];
+  b[0] = 0;
+#pragma unroll
+  for (int s = 1; s < 8; s++) b[s] = norm16(m[s], nm0);
+}
+
+// Lambda and the extrinsic of one step: returns Le, writes Lambda.
+__device__ __forceinline__ int app_step(const int a[8], const int b[8], int S, int Lp, int* lam_out) {
+  int acc[4];
+  bool first[4] = {true, true, true, true};
+#pragma unroll
+  for (int s = 0; s < 8; s++)
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int c = gcode(s, u);
+      const int n = nxt(s, u);
+      if (first[c]) {
+        acc[c] = a[s] + b[n];
+        first[c] = false;
+      } else {
+        acc[c] = __viaddmax_s32(a[s], b[n], acc[c]);
+      }
+    }
+  // u = 0: codes 3 (p = 0, + Lp) and 2; u = 1: codes 1 (+ Lp) and 0.  The
+  // common S of the u = 0 branches is added back below.
+  const int best0 = __viaddmax_s32(acc[3], Lp, acc[2]);
+  const int best1 = __viaddmax_s32(acc[1], Lp, acc[0]);
+  const int lam = max(__viaddmin_s32(S, best0 - best1, 32767), -32768);
+  *lam_out = lam;
+  return max(__viaddmin_s32(lam, -S, 32767), -32768);
+}
+
+__device__ __forceinline__ int scale_ext(int le) { return (le * 3) >> 2; }
+
+__device__ __forceinline__ uint4 pack8(const int v[8]) {
+  uint4 r;
+  r.x = __byte_perm(v[0], v[1], 0x5410);
+  r.y = __byte_perm(v[2], v[3], 0x5410);
+  r.z = __byte_perm(v[4], v[5], 0x5410);
+  r.w = __byte_perm(v[6], v[7], 0x5410);
+  return r;
+}
+__device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xFFFFu); }
+__device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
+__device__ __forceinline__ void unpack8(uint4 r, int v[8]) {
+  v[0] = lo16(r.x); v[1] = hi16(r.x);
+  v[2] = lo16(r.y); v[3] = hi16(r.y);
+  v[4] = lo16(r.z); v[5] = hi16(r.z);
+  v[6] = lo16(r.w); v[7] = hi16(r.w);
+}
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ int modadd(int x, int y, int K) {
+  const unsigned s = (unsigned)(x + y);
+  return (int)min(s, s - (unsigned)K);
+}
+__device__ __forceinline__ int modsub(int x, int y, int K) {
+  const unsigned s = (unsigned)(x - y);
+  return (int)min(s, s + (unsigned)K);
+}
+__device__ __forceinline__ int qpp_at(int x, int f1, int f2, int K) {
+  int t = (f2 * x) % K;
+  t = (t * x) % K;
+  return (t + f1 * x) % K;
+}
+struct CbSlot {
+  int8_t* sys;
+  int8_t* par1;
+  int8_t* par2;
+  int16_t* ext;
+  int8_t* tail;
+  uint32_t* hard;
+  uint4* seed;   // [4][P]: alpha dec0, alpha dec1, beta dec0, beta dec1
+  uint4* ck;     // [P][nck]
+  int* flags;    // [0] done, [1] iterations, [2] crc accumulator, [3] spare
+};
+__device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
+  CbSlot s;
+  const int tp = W * P;
+  const int nck = (W + kSub - 1) / kSub;
+  const int nwords = (K + 31) / 32 + 1;
+  s.sys = (int8_t*)base;
+  s.par1 = s.sys + tp;
+  s.par2 = s.sys + 2 * tp;
+  uint8_t* q = base + align16(3 * tp);
+  s.ext = (int16_t*)q;
+  q += align16(2 * tp);
+  s.tail = (int8_t*)q;
+  q += 16;
+  s.hard = (uint32_t*)q;
+  q += align16(4 * nwords);
+  s.seed = (uint4*)q;
+  q += 4 * P * 16;
+  s.ck = (uint4*)q;
+  q += P * nck * 16;
+  s.flags = (int*)q;
+  return s;
+}
+// transposed shared-memory index of natural position q < K
+__device__ __forceinline__ int tr_idx(int q, const CbDesc& d) {
+  const int w = (int)(((unsigned)q * (unsigned)d.divM) >> d.divS);
+  return (q - w * d.W) * d.P + w;
+}
+
+__device__ __forceinline__ uint32_t gf_mulmod(uint32_t a, uint32_t b, uint32_t g) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int i = 23; i >= 0; i--) {
+    r <<= 1;
+    if (r & 0x1000000u) r ^= g;
+    if ((a >> i) & 1u) r ^= b;
+  }
+  return r;
+}
+
+// CRC register update over one 32-bit word (MSB first), byte table tab.
+__device__ __forceinline__ uint32_t crc_word(uint32_t r, uint32_t w, const uint32_t* tab) {
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint32_t byte = (w >> (24 - 8 * k)) & 0xFFu;
+    r = ((r << 8) & 0xFFFFFFu) ^ tab[((r >> 16) ^ byte) & 0xFFu];
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- de-RM
+// De-rate-matching + HARQ combining of one CB into its shared-memory slot.
+// Circular buffer w (TS 36.212 5.1.4.1): v0 = 32 columns x R rows read by
+// column after the bit-reversal column permutation; then v1/v2 interlaced.
+// Unit u < 32 is column u of v0; unit 32 + c holds rows of column c of v1
+// and v2.  The rank (count of non-NULL positions before a position) has a
+// closed form: with X = ND + F = 32 a + b, column c of v0/v1 has
+// n0(c) = a + [P(c) < b] leading NULLs and column c of v2 has
+// n2(c) = [P(c) < ND - 1] (plus the wrapped NULL at the end of column 31).
+__device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restrict__ llr,
+                        int8_t* __restrict__ soft_arena, int tid, int nthr) {
+  const int K = d.K, F = d.F, R = d.R, ND = d.ND, E = d.E, Nv = d.Nv;
+  const int KPI = 32 * R;
+  const int X = ND + F, xa = X >> 5;
+  const int8_t* e = llr + d.llr_off;
+  int8_t* soft = d.soft_off >= 0 ? soft_arena + d.soft_off : nullptr;
+  const bool combine = soft != nullptr && !d.new_data;
+  const int nrows = 64 * R;
+  for (int x = tid; x < nrows; x += nthr) {
+    const int unit = x / R;
+    const int i = x - unit * R;
+    const int c = unit & 31;
+    const int Pc = (int)(__brev((unsigned)c) >> 27);
+    const unsigned low = (1u << c) - 1u;
+    const int n0c = xa + ((d.maskB >> c) & 1u);
+    const int pre0 = xa * c + __popc(d.maskB & low);
+    if (unit < 32) {
+      const int p = c * R + i;
+      const int y = Pc + 32 * i;
+      int8_t v = 0;
+      if (y >= X) {
+        const int rank = c * R - pre0 + (i - n0c);
+        int k = rank - d.rank0;
+        if (k < 0) k += Nv;
+        int acc = combine ? soft[p] : 0;
+        for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
+        v = (int8_t)acc;
+        const int di = y - ND;
+        if (di < K) sl.sys[tr_idx(di, d)] = v;
+        else sl.tail[3 * (di - K)] = v;
+        if (soft) soft[p] = v;
+      } else if (soft && !combine) {
+        soft[p] = 0;
+      }
+    } else {
+      const int n2c = (d.mask2 >> c) & 1u;
+      const int pre2 = __popc(d.mask2 & low);
+      const int base = (KPI - X) + 2 * R * c - pre0 - pre2;
+      const int r1 = base + max(0, i - n0c) + max(0, i - n2c);
+      const int p1 = KPI + 2 * (c * R + i);
+      // v1 (parity of encoder 1)
+      const int y1 = Pc + 32 * i;
+      const bool nn1 = y1 >= X;
+      int8_t v1 = 0, v2 = 0;
+      if (nn1) {
+        int k = r1 - d.rank0;
+        if (k < 0) k += Nv;
+        int acc = combine ? soft[p1] : 0;
+        for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
+        v1 = (int8_t)acc;
+        const int di = y1 - ND;
+        if (di < K) sl.par1[tr_idx(di, d)] = v1;
+        else sl.tail[3 * (di - K) + 1] = v1;
+      }
+      // v2 (parity of encoder 2)
+      int y2 = Pc + 32 * i + 1;
+      if (y2 == KPI) y2 = 0;
+      const bool nn2 = y2 >= ND;
+      if (nn2) {
+        int k = r1 + (nn1 ? 1 : 0) - d.rank0;
+        if (k < 0) k += Nv;
+        int acc = combine ? soft[p1 + 1] : 0;
+        for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
+        v2 = (int8_t)acc;
+        const int di = y2 - ND;
+        if (di < K) sl.par2[tr_idx(di, d)] = v2;
+        else sl.tail[3 * (di - K) + 2] = v2;
+      }
+      if (soft) {
+        if (nn1 || !combine) soft[p1] = v1;
+        if (nn2 || !combine) soft[p1 + 1] = v2;
+      }
+    }
+  }
+  // filler: known zero bits in the systematic stream, unknown parity 1
+  for (int k = tid; k < F; k += nthr) {
+    const int t = tr_idx(k, d);
+    sl.sys[t] = 127;
+    sl.par1[t] = 0;
+  }
+  const int tp = d.W * d.P;
+  for (int k = tid; k < tp; k += nthr) sl.ext[k] = 0;
+  if (tid == 0) {
+    sl.flags[0] = 0;
+    sl.flags[1] = 0;
+    sl.flags[2] = 0;
+    sl.flags[3] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- SISO
+// One SISO pass of window p of one CB.  DEC = 0: natural order (encoder 1),
+// DEC = 1: QPP order (encoder 2).  All threads of the CTA call it (run =
+// false for idle threads) because it contains barriers.
+template <int DEC>
+__device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t* base, int p,
+                                          bool run, bool first) {
+  const int K = dp->K, P = dp->P, W = dp->W;
+  const CbSlot sl = make_slot(base, K, P, W);
+  CbDesc d;
+  d.W = W;
+  d.P = P;
+  d.divM = dp->divM;
+  d.divS = dp->divS;
+  const int lo = p * W;
+  const int len = min(W, K - lo);
+  const int8_t* __restrict__ par = DEC ? sl.par2 : sl.par1;
+  uint4* seedA = sl.seed + DEC * P;
+  uint4* seedB = sl.seed + (2 + DEC) * P;
+  uint4* ck = sl.ck + p * ((W + kSub - 1) / kSub);
+
+  int a[8], b[8];
+  if (run) {
+    if (p == 0) {
+      a[0] = 0;
+#pragma unroll
+      for (int s = 1; s < 8; s++) a[s] = MINF;
+    } else if (first) {
+#pragma unroll
+      for (int s = 0; s < 8; s++) a[s] = 0;
+    } else {
+      unpack8(seedA[p], a);
+    }
+    if (p == P - 1) {
+      b[0] = 0;
+#pragma unroll
+      for (int s = 1; s < 8; s++) b[s] = MINF;
+    } else if (first) {
+#pragma unroll
+      for (int s = 0; s < 8; s++) b[s] = 0;
+    } else {
+      unpack8(seedB[p], b);
+    }
+    if (DEC == 1) {
+      const int nwords = (K + 31) / 32;
+      for (int w = p; w < nwords; w += P) sl.hard[w] = 0u;
+    }
+  }
+  __syncthreads();
+  if (run) {
+    const int f1 = dp->f1, f2 = dp->f2;
+    const int f2x2 = dp->f2x2;
+    // ---- forward pass with checkpoints
+    int pi = 0, dl = 0;
+    if (DEC == 1) {
+      pi = qpp_at(lo, f1, f2, K);
+      dl = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
+    }
+    int idx = p;
+    for (int j0 = 0; j0 < len; j0 += kSub) {
+      ck[j0 / kSub] = pack8(a);
+      const int slen = min(kSub, len - j0);
+#pragma unroll
+      for (int jj = 0; jj < kSub; jj++) {
+        if (jj < slen) {
+          int Ls, La;
+          if (DEC == 0) {
+            Ls = sl.sys[idx];
+            La = sl.ext[idx];
+          } else {
+            const int t = tr_idx(pi, d);
+            Ls = sl.sys[t];
+            La = sl.ext[t];
+            pi = modadd(pi, dl, K);
+            dl = modadd(dl, f2x2, K);
+          }
+          const int Lp = par[idx];
+          const int S = Ls + La;
+          alpha_step(a, S, S + Lp, Lp);
+          idx += P;
+        }
+      }
+    }
+    if (p + 1 < P) seedA[p + 1] = pack8(a);
+
+    // ---- backward pass
+    if (p == P - 1) {
+      const int8_t* t = sl.tail + (DEC ? 6 : 0);
+#pragma unroll
+      for (int j = 2; j >= 0; j--) beta_tail_step(b, t[2 * j], t[2 * j + 1]);
+    }
+    const int nsub = (len + kSub - 1) / kSub;
+    int pis = 0, dls = 0, d8 = 0;
+    const int pad = ((K + 31) / 32) * 32 - K;
+    if (DEC == 1) {
+      const int is = lo + kSub * (nsub - 1);
+      pis = qpp_at(is, f1, f2, K);
+      dls = (f1 + (f2 * ((2 * is + 1) % K)) % K) % K;
+      int t = (16 * is - 64) % K;
+      if (t < 0) t += K;
+      d8 = ((8 * f1) % K + (f2 * t) % K) % K;
+    }
+    for (int sw = nsub - 1; sw >= 0; sw--) {
+      const int j0 = sw * kSub;
+      const int slen = min(kSub, len - j0);
+      int A[kSub][8];
+      int Sv[kSub], Lv[kSub], Qv[kSub];
+      unpack8(ck[sw], A[0]);
+      int q = pis, dq = dls;
+      int idx2 = (j0)*P + p;
+#pragma unroll
+      for (int jj = 0; jj < kSub; jj++) {
+        if (jj < slen) {
+          int Ls, La, t;
+          if (DEC == 0) {
+            t = idx2;
+          } else {
+            t = tr_idx(q, d);
+            Qv[jj] = q;
+            q = modadd(q, dq, K);
+            dq = modadd(dq, f2x2, K);
+          }
+          Ls = sl.sys[t];
+          La = sl.ext[t];
+          const int Lp = par[idx2];
+          Sv[jj] = Ls + La;
+          Lv[jj] = Lp;
+          if (jj + 1 < kSub && jj + 1 < slen) {
+#pragma unroll
+            for (int s = 0; s < 8; s++) A[jj + 1][s] = A[jj][s];
+            alpha_step(A[jj + 1], Sv[jj], Sv[jj] + Lp, Lp);
+          }
+          idx2 += P;
+        }
+      }
+#pragma unroll
+      for (int jj = kSub - 1; jj >= 0; jj--) {
+        if (jj < slen) {
+          const int S = Sv[jj], Lp = Lv[jj];
+          int lam;
+          const int le = app_step(A[jj], b, S, Lp, &lam);
+          const int t = (DEC == 0) ? (j0 + jj) * P + p : tr_idx(Qv[jj], d);
+          sl.ext[t] = (int16_t)scale_ext(le);
+          if (DEC == 1 && lam < 0) {
+            const int qq = Qv[jj] + pad;
+            atomicOr(&sl.hard[qq >> 5], 1u << (31 - (qq & 31)));
+          }
+          beta_step(b, S, S + Lp, Lp);
+        }
+      }
+      if (DEC == 1) {
+        pis = modsub(pis, d8, K);
+        dls = modsub(dls, dp->f2x16, K);
+        d8 = modsub(d8, dp->f2x128, K);
+      }
+    }
+    if (p > 0) seedB[p - 1] = pack8(b);
+  }
+  __syncthreads();
+}
+
+// CRC of the CB's hard bits held by this thread's share of words.  mode 0:
+// the CB's own CRC over bits [F, K); mode 1: CRC24A over [F, K - 24) followed
+// by 24 zeros (the TB CRC contribution).
+__device__ uint32_t crc_share(const CbDesc& d, const CbSlot& sl, int p, const uint32_t* tab,
+                              uint32_t g, const uint32_t* xpow, int mode) {
+  const int K = d.K, P = d.P;
+  const int nw = (K + 31) / 32;
+  const int pad = nw * 32 - K;
+  const int per = (nw + P - 1) / P;
+  const int w0 = p * per;
+  const int w1 = min(nw, w0 + per);
+  if (w0 >= w1) return 0u;
+  const int fq = pad + d.F;  // first message bit position in padded order
+  uint32_t r = 0;
+  for (int w = w0; w < w1; w++) {
+    uint32_t word = sl.hard[w];
+    const int wq = 32 * w;
+    if (fq > wq) word = (fq >= wq + 32) ? 0u : (word & (0xFFFFFFFFu >> (fq - wq)));
+    if (mode == 1 && w == nw - 1) word &= 0xFFFFFF00u;
+    r = crc_word(r, word, tab);
+  }
+  const int after = nw - w1;
+  return after ? gf_mulmod(r, __ldg(&xpow[after]), g) : r;
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams prm) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int s_item;
+  __shared__ int s_remaining;
+  __shared__ int s_maxit;
+  uint32_t* tabA = (uint32_t*)smem;
+  uint32_t* tabB = tabA + 256;
+  uint8_t* slots = smem + 2048;
+  const int tid = threadIdx.x;
+
+  for (int i = tid; i < 512; i += kThreads) {
+    const uint32_t g = (i < 256) ? GA : GB;
+    uint32_t r = (uint32_t)(i & 255) << 16;
+    for (int k = 0; k < 8; k++) r = (r & 0x800000u) ? ((r << 1) ^ g) : (r << 1);
+    (i < 256 ? tabA : tabB)[i & 255] = r & 0xFFFFFFu;
+  }
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(&prm.state->head, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= prm.n_items) break;
+    const WorkItem wi = prm.items[item];
+    const CbDesc* cbs = prm.cbs + wi.cb0;
+    const int P = cbs[0].P;
+    const int G = wi.n;
+    const int mycb = tid / P;
+    const int p = tid - mycb * P;
+    const bool mine = mycb < G;
+    const CbDesc* dp = cbs + (mine ? mycb : 0);
+
+    // ---- phase 0: de-rate-matching of every CB of the item
+    for (int g = 0; g < G; g++) {
+      const CbDesc& dg = cbs[g];
+      const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
+      derm_cb(dg, sg, prm.llr, prm.soft, tid, kThreads);
+    }
+    if (tid == 0) {
+      s_remaining = G;
+      int mx = 0;
+      for (int g = 0; g < G; g++) mx = max(mx, (int)cbs[g].max_iter);
+      s_maxit = mx;
+    }
+    __syncthreads();
+    uint8_t* mybase = slots + (mine ? mycb : 0) * wi.smem_per_cb;
+    const CbDesc d = *dp;
+    const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
+    if (prm.dbg_d) {
+      for (int g = 0; g < G; g++) {
+        const CbDesc& dg = cbs[g];
+        const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
+        const int D = dg.K + 4;
+        int8_t* out = prm.dbg_d + 3 * (int64_t)dg.dbg_off;
+        for (int k = tid; k < D; k += kThreads) {
+          if (k < dg.K) {
+            const int t = tr_idx(k, dg);
+            out[k] = sg.sys[t];
+            out[D + k] = sg.par1[t];
+            out[2 * D + k] = sg.par2[t];
+          } else {
+            out[k] = sg.tail[3 * (k - dg.K)];
+            out[D + k] = sg.tail[3 * (k - dg.K) + 1];
+            out[2 * D + k] = sg.tail[3 * (k - dg.K) + 2];
+          }
+        }
+      }
+    }
+
+    // ---- phase 1: turbo iterations
+    const int maxit = s_maxit;
+    for (int it = 1; it <= maxit; it++) {
+      const bool run = mine && sl.flags[0] == 0 && it <= d.max_iter;
+      const bool first = (it == 1);
+      siso_pass<0>(dp, mybase, p, run, first);
+      siso_pass<1>(dp, mybase, p, run, first);
+      const bool check = run && (d.early_stop || it == d.max_iter);
+      if (check) {
+        const uint32_t r = crc_share(d, sl, p, d.crc_b ? tabB : tabA, d.crc_b ? GB : GA,
+                                     d.crc_b ? prm.xpowB : prm.xpowA, 0);
+        if (r) atomicXor((unsigned*)&sl.flags[2], r);
+      }
+      __syncthreads();
+      if (run && p == 0) {
+        const bool ok = check && sl.flags[2] == 0;
+        sl.flags[2] = 0;
+        if (ok || it == d.max_iter) {
+          sl.flags[0] = 1;
+          sl.flags[1] = ok ? it : d.max_iter + 1;
+          atomicSub(&s_remaining, 1);
+        }
+      }
+      __syncthreads();
+      if (s_remaining == 0) break;
+    }
+
+    // ---- phase 2: results, payload bytes, TB CRC, debug copies
+    const int sorted_idx = wi.cb0 + (mine ? mycb : 0);
+    const bool cb_ok = mine && sl.flags[1] <= d.max_iter;
+    if (mine) {
+      const TbDesc tb = prm.tbs[d.tb];
+      const int nw = (d.K + 31) / 32;
+      const int pad = nw * 32 - d.K;
+      const int nbytes = d.pay_bits / 8;
+      uint8_t* out = prm.out + tb.out_off;
+      for (int m = p; m < nbytes; m += d.P) {
+        const int tbbit = d.pay_off + 8 * m;
+        if (tbbit >= tb.A) break;
+        const int q = pad + d.F + 8 * m;
+        out[tbbit >> 3] = (uint8_t)(sl.hard[q >> 5] >> (24 - (q & 31)));
+      }
+      if (d.crc_b) {
+        const uint32_t r = crc_share(d, sl, p, tabA, GA, prm.xpowA, 1);
+        if (r) atomicXor((unsigned*)&sl.flags[3], r);
+      }
+      if (prm.dbg_ext) {
+        for (int k = p; k < d.K; k += d.P) {
+          prm.dbg_ext[d.dbg_off + k] = sl.ext[tr_idx(k, d)];
+          const int q = pad + k;
+          prm.dbg_hard[d.dbg_off + k] = (uint8_t)((sl.hard[q >> 5] >> (31 - (q & 31))) & 1u);
+        }
+      }
+    }
+    __syncthreads();
+    if (mine && p == 0) {
+      prm.cb_iters[sorted_idx] = (uint8_t)sl.flags[1];
+      prm.cb_ok[sorted_idx] = cb_ok ? 1 : 0;
+      const TbDesc tb = prm.tbs[d.tb];
+      if (tb.C == 1) {
+        prm.tb_ok[d.tb] = cb_ok ? 1 : 0;
+      } else {
+        uint32_t contrib = (uint32_t)sl.flags[3];
+        // shift past the TB bits that follow this CB's payload: 32 a + 8 b
+        const int na = d.n_after >> 5, nb = (d.n_after >> 3) & 3;
+        if (na) contrib = gf_mulmod(contrib, __ldg(&prm.xpowA[na]), GA);
+        for (int k = 0; k < nb; k++)
+          contrib = ((contrib << 8) & 0xFFFFFFu) ^ tabA[(contrib >> 16) & 0xFFu];
+        atomicXor(&prm.tb_crc[2 * d.tb], contrib);
+        if (!cb_ok) atomicOr(&prm.tb_crc[2 * d.tb + 1], 1u);
+        __threadfence();
+        const int done = atomicAdd(&prm.tb_done[d.tb], 1);
+        if (done == tb.C - 1) {
+          __threadfence();
+          const uint32_t x = atomicOr(&prm.tb_crc[2 * d.tb], 0u);
+          const uint32_t bad = atomicOr(&prm.tb_crc[2 * d.tb + 1], 0u);
+          prm.tb_ok[d.tb] = (x == 0u && bad == 0u) ? 1 : 0;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int decode_max_smem() { return kSmemBudget + 2048; }
+
+static cudaError_t set_attr() {
+  return cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              decode_max_smem());
+}
+
+int decode_occupancy(int smem) {
+  if (set_attr() != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_kernel, kThreads, smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s) {
+  if (smem > decode_max_smem()) return cudaErrorInvalidValue;
+  decode_kernel<<<grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace crnt

@@ -18,3 +18,14 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def crnt_lib():
+    """The product library, built in-tree if needed (nvcc cross-compiles
+    without a GPU)."""
+    from paper_1905_01141_gb300 import build
+    build.build()
+    import paper_1905_01141_gb300 as crnt
+    crnt.load()
+    return crnt

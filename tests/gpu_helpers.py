@@ -1,0 +1,117 @@
+"""Helpers of the GPU parity tests: seeded workloads encoded by the oracle,
+the library run through its C ABI with the debug outputs, and the oracle's
+per-CB and per-TB expectations."""
+import numpy as np
+
+import synth
+
+
+def make_tb(orc, A, G, Qm, seed, rv=0, ebn0=None, snr=None, noiseless=False):
+    """Payload bits and int8 LLRs of one TB (oracle encoder, synth channel)."""
+    a = synth.bits(seed, 100, A)
+    e = orc.encode_tb(a, G, Qm=Qm, rv=rv)
+    if noiseless:
+        llr = np.where(e == 0, 100, -100).astype(np.int8)
+    elif ebn0 is not None:
+        llr = synth.channel_llrs(e, 1, synth.sigma2_ebn0(ebn0, A / G), seed, 200)
+    else:
+        llr = synth.channel_llrs(e, Qm, synth.sigma2_snr(snr), seed, 200)
+    return a, llr
+
+
+def run_gpu(crnt, ctx, tbs, llr_cat, debug=True):
+    """Decode a batch through crnt_plan_launch_debug; returns host copies."""
+    import torch
+    plan = ctx.plan(tbs)
+    inf = plan.info
+    dev = torch.device("cuda")
+    llr_d = torch.from_numpy(np.ascontiguousarray(llr_cat)).to(dev)
+    out_d = torch.zeros(max(1, inf["out_bytes"]), dtype=torch.uint8, device=dev)
+    n = inf["dbg_elems"]
+    stream = torch.cuda.current_stream().cuda_stream
+    if debug:
+        dd = torch.full((3 * n,), -99, dtype=torch.int8, device=dev)
+        de = torch.zeros(n, dtype=torch.int16, device=dev)
+        dh = torch.zeros(n, dtype=torch.uint8, device=dev)
+        plan.launch(llr_d, out_d, stream, dbg_d=dd, dbg_ext=de, dbg_hard=dh)
+    else:
+        plan.launch(llr_d, out_d, stream)
+    res = plan.results(stream)
+    torch.cuda.synchronize()
+    out = dict(res=res, out=out_d.cpu().numpy(), info=inf)
+    if debug:
+        out.update(d=dd.cpu().numpy(), ext=de.cpu().numpy(), hard=dh.cpu().numpy())
+    plan.close()
+    return out
+
+
+def oracle_tb(orc, crnt, tb, llr, soft=None):
+    """Oracle decode of one TB CB by CB, with the library's per-CB window
+    counts (reported by crnt_tb_layout, which needs no GPU).  Returns per-CB
+    (d0, d1, d2, iters, hard, ext), the A payload bits, tb_ok and the soft
+    buffer."""
+    lay = crnt.tb_layout(tb)
+    A, G, Qm, NL, rv = tb["A"], tb["G"], tb.get("Qm", 2), tb.get("NL", 1), tb.get("rv", 0)
+    C = len(lay)
+    L = 24 if C > 1 else 0
+    new = soft is None
+    if new:
+        soft = np.zeros(sum(c["Ncb"] for c in lay), dtype=np.int8)
+    cbs = []
+    payload = []
+    ok_all = True
+    for r, c in enumerate(lay):
+        e = llr[c["llr_offset"]:c["llr_offset"] + c["E"]]
+        sb = soft[c["soft_offset"]:c["soft_offset"] + c["Ncb"]]
+        if new:
+            d0, d1, d2, sb2 = orc.derm_cb(e, c["K"], c["F"], rv)
+        else:
+            d0, d1, d2, sb2 = orc.derm_cb(e, c["K"], c["F"], rv, soft=sb.copy())
+        soft[c["soft_offset"]:c["soft_offset"] + c["Ncb"]] = sb2
+        it, hard, ext = orc.turbo_decode_cb(d0, d1, d2, F=c["F"], crc="B" if C > 1 else "A",
+                                            P=c["P"], max_iter=tb.get("max_iter", 6),
+                                            early_stop=bool(tb.get("early_stop", 1)))
+        ok_all &= it <= tb.get("max_iter", 6)
+        cbs.append((d0, d1, d2, it, hard, ext))
+        payload.append(hard[c["F"]:c["K"] - L])
+    b = np.concatenate(payload)
+    tb_ok = bool(ok_all and orc.crc24(b, "A") == 0)
+    return cbs, b[:A], tb_ok, soft
+
+
+def check_batch(orc, crnt, tbs, llrs, g, sample=None):
+    """Compare every (or a sample of) TB of a GPU run with the oracle:
+    de-rate-matched streams, hard decisions, extrinsics, iteration counts,
+    CRC flags and payload bytes -- all bit-exact."""
+    idx = range(len(tbs)) if sample is None else sample
+    dbg_off = [0]
+    for t in tbs:
+        for c in crnt.tb_layout(t):
+            dbg_off.append(dbg_off[-1] + c["K"] + 4)
+    cb_index = []
+    k = 0
+    for t in tbs:
+        cb_index.append(k)
+        k += len(crnt.tb_layout(t))
+    out_off = np.cumsum([0] + [t["A"] // 8 for t in tbs])
+    for t in idx:
+        tb = tbs[t]
+        cbs, bits, tb_ok, _ = oracle_tb(orc, crnt, tb, llrs[t])
+        res = g["res"][t]
+        assert res["C"] == len(cbs)
+        for r, (d0, d1, d2, it, hard, ext) in enumerate(cbs):
+            K = len(hard)
+            o = dbg_off[cb_index[t] + r]
+            D = K + 4
+            if "d" in g:
+                gd = g["d"][3 * o:3 * o + 3 * D]
+                assert np.array_equal(gd[:D], d0), ("d0", t, r)
+                assert np.array_equal(gd[D:2 * D], d1), ("d1", t, r)
+                assert np.array_equal(gd[2 * D:], d2), ("d2", t, r)
+                assert np.array_equal(g["hard"][o:o + K], hard), ("hard", t, r)
+                assert np.array_equal(g["ext"][o:o + K], ext), ("ext", t, r)
+            assert res["cb_iters"][r] == it, ("iters", t, r, res["cb_iters"][r], it)
+            assert res["cb_crc_ok"][r] == (it <= tb.get("max_iter", 6)), ("cbok", t, r)
+        assert res["tb_crc_ok"] == tb_ok, ("tbok", t)
+        got = np.unpackbits(g["out"][out_off[t]:out_off[t + 1]])
+        assert np.array_equal(got, bits), ("payload", t)

@@ -1,0 +1,80 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/crnt.h declares, its structs match the header's sizes, and its
+host-side parameter arithmetic agrees with the oracle (independent code)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                   "crnt.h")
+
+
+def declared_functions():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(crnt_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(crnt_lib):
+    names = declared_functions()
+    assert "crnt_decode_batch" in names and len(names) >= 18
+    lib = crnt_lib.load()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(crnt_lib.SIGNATURES)
+
+
+def test_struct_sizes(crnt_lib):
+    assert ctypes.sizeof(crnt_lib.TbParams) == 32
+    assert ctypes.sizeof(crnt_lib.TbResult) == 80
+    assert ctypes.sizeof(crnt_lib.CbLayout) == 40
+    assert crnt_lib.version() == 1
+    assert crnt_lib.strerror(-1) == "invalid argument"
+
+
+def test_qpp_table_matches_oracle(crnt_lib, orc):
+    for K in orc.k_table():
+        assert crnt_lib.qpp_params(K) == orc.qpp_params(K), K
+    with pytest.raises(crnt_lib.CrntError):
+        crnt_lib.qpp_params(41)
+
+
+def test_tb_layout_matches_oracle(crnt_lib, orc):
+    rng_A = 8 * synth.randint(9, 0, 300, 2, 9422)
+    cases = [(6120, 18444, 2, 1, 0), (75376, 86400, 6, 1, 0), (16, 132, 2, 1, 3), (6128, 13000, 2, 2, 2)]
+    for t, A in enumerate(rng_A):
+        Qm = (2, 4, 6)[t % 3]
+        G = Qm * int(np.ceil((A + 24) * 1.3 / Qm))
+        cases.append((int(A), G, Qm, 1 + (t % 2), t % 4))
+    for A, G, Qm, NL, rv in cases:
+        G = G - G % (Qm * NL)
+        lay = crnt_lib.tb_layout(dict(A=A, G=G, Qm=Qm, NL=NL, rv=rv))
+        s = orc.segment(A + 24)
+        assert len(lay) == s["C"]
+        eoff = soff = 0
+        for r, c in enumerate(lay):
+            K = s["Km"] if r < s["Cm"] else s["Kp"]
+            assert c["K"] == K and c["F"] == (s["F"] if r == 0 else 0)
+            assert c["E"] == orc.e_r(G, Qm, NL, s["C"], r)
+            assert c["k0"] == orc.k0(K, rv) and c["Ncb"] == orc.ncb(K)
+            assert c["llr_offset"] == eoff and c["soft_offset"] == soff
+            assert c["crc_b"] == (s["C"] > 1)
+            assert 1 <= c["P"] <= min(128, max(1, K // 8)) and c["W"] == -(-K // c["P"])
+            eoff += c["E"]
+            soff += c["Ncb"]
+        assert eoff == G
+
+
+def test_invalid_params_rejected(crnt_lib):
+    bad = [dict(A=15, G=100), dict(A=17, G=100), dict(A=75384, G=100000), dict(A=100, G=101),
+           dict(A=100, G=300, Qm=3), dict(A=100, G=300, rv=4), dict(A=100, G=300, max_iter=0),
+           dict(A=100, G=300, NL=3)]
+    for b in bad:
+        with pytest.raises(crnt_lib.CrntError) as ei:
+            crnt_lib.tb_layout(b)
+        assert ei.value.code == crnt_lib.EINVAL

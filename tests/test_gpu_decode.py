@@ -1,0 +1,158 @@
+"""GPU parity of the fused decode path (de-rate-matching + HARQ combining,
+turbo decoding, CRC stop, TB reassembly, batched work queue) against the CPU
+oracle, through the C ABI.  All integer work: every output is compared
+bit-exactly (tolerance 0)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import check_batch, make_tb, oracle_tb, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx(crnt_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = crnt_lib.Context(0)
+    yield c
+    c.close()
+
+
+def batch(orc, specs):
+    tbs, llrs = [], []
+    for s in specs:
+        s = dict(s)
+        seed = s.pop("seed")
+        kw = {k: s.pop(k) for k in ("ebn0", "snr", "noiseless") if k in s}
+        a, llr = make_tb(orc, s["A"], s["G"], s.get("Qm", 2), seed, rv=s.get("rv", 0), **kw)
+        tbs.append(s)
+        llrs.append(llr)
+    return tbs, llrs
+
+
+@pytest.mark.parametrize("P", [1, 8, 64, 128])
+def test_single_cb_workload(orc, crnt_lib, ctx, P):
+    # A=6120 + CRC24A -> one K=6144 CB, rate 1/3 (E=18444), BPSK at Eb/N0 1 dB
+    tbs, llrs = batch(orc, [dict(A=6120, G=18444, Qm=2, P=P, max_iter=6, seed=s, ebn0=1.0)
+                            for s in range(3)])
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
+    assert all(r["P_used"] == P for r in g["res"])
+
+
+@pytest.mark.parametrize("P", [1, 8, 32])
+@pytest.mark.parametrize("snr", [18.0, 20.0, 22.0])
+def test_20mhz_subframe_workload(orc, crnt_lib, ctx, P, snr):
+    # TBS 75376 -> 13 CBs of K=5824, G=86400 (100 PRB x 144 RE x 6), 64QAM
+    tbs, llrs = batch(orc, [dict(A=75376, G=86400, Qm=6, P=P, max_iter=6, seed=int(snr),
+                                 snr=snr)])
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
+    assert g["res"][0]["C"] == 13 and g["res"][0]["Kp"] == 5824
+
+
+def test_mixed_batch_autotuned(orc, crnt_lib, ctx):
+    # uneven load: A across the whole LTE range (K 40..6144, C 1..13), mixed
+    # modulation, SNR around the decoding threshold so iterations vary
+    shapes = synth.tti_batch(seed=7, n_tb=40, amax=30000)
+    shapes += synth.tti_batch(seed=8, n_tb=4, amin=60000)
+    specs = []
+    for i, s in enumerate(shapes):
+        specs.append(dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=6,
+                          early_stop=1 if i % 3 else 0, rv=i % 4, seed=100 + i,
+                          snr=s["snr_db"]))
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
+    iters = [it for r in g["res"] for it in r["cb_iters"]]
+    assert len(set(iters)) > 2  # uneven iteration counts really occurred
+
+
+def test_edge_cases(orc, crnt_lib, ctx):
+    specs = [
+        dict(A=16, G=132, Qm=2, seed=1, snr=2.0),              # K = 40, smallest CB
+        dict(A=16, G=1200, Qm=2, seed=2, snr=-4.0),            # heavy repetition E >> 3D
+        dict(A=6128, G=13000, Qm=2, seed=3, snr=3.0),          # C = 2 with filler bits
+        dict(A=1000, G=1400, Qm=4, seed=4, snr=30.0, max_iter=1),
+        dict(A=2000, G=2600, Qm=2, seed=5, snr=6.0, early_stop=0, max_iter=3),
+        dict(A=512, G=900, Qm=2, seed=6, snr=0.0, P=500),      # P beyond K/8: clamped
+        dict(A=40000, G=60000, Qm=4, NL=2, rv=1, seed=7, snr=9.0, max_iter=8),
+        dict(A=3000, G=3100, Qm=2, seed=8, snr=-10.0),         # undecodable: max_iter + 1
+    ]
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
+    assert g["res"][7]["cb_iters"] == [7] and not g["res"][7]["tb_crc_ok"]
+    assert g["res"][3]["cb_iters"][0] in (1, 2)
+
+
+def test_batch_invariance(orc, crnt_lib, ctx):
+    # a TB's result alone equals its result inside a mixed batch
+    shapes = synth.tti_batch(seed=11, n_tb=12, amax=40000)
+    specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], seed=200 + i, snr=s["snr_db"])
+             for i, s in enumerate(shapes)]
+    tbs, llrs = batch(orc, specs)
+    gall = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs), debug=False)
+    off = np.cumsum([0] + [t["A"] // 8 for t in tbs])
+    for t in (0, 5, 11):
+        g1 = run_gpu(crnt_lib, ctx, [tbs[t]], llrs[t], debug=False)
+        assert g1["res"][0]["cb_iters"] == gall["res"][t]["cb_iters"]
+        assert g1["res"][0]["tb_crc_ok"] == gall["res"][t]["tb_crc_ok"]
+        assert np.array_equal(g1["out"], gall["out"][off[t]:off[t + 1]])
+
+
+def test_harq_combining(orc, crnt_lib, ctx):
+    # first transmission (rv 0) fails; the retransmission (rv 2) combined in
+    # the library-owned soft buffer decodes; both match the oracle's combine
+    A, G, Qm = 2000, 2400, 2
+    a = synth.bits(5, 100, A)
+    e0 = orc.encode_tb(a, G, Qm=Qm, rv=0)
+    e2 = orc.encode_tb(a, G, Qm=Qm, rv=2)
+    sig = synth.sigma2_snr(1.0)
+    l0 = synth.channel_llrs(e0, 2, sig, 5, 1)
+    l2 = synth.channel_llrs(e2, 2, sig, 5, 2)
+    key = dict(cell=3, ue=7, harq_pid=2, flags=crnt_lib.F_HARQ)
+    t0 = dict(A=A, G=G, Qm=Qm, rv=0, new_data=1, **key)
+    t2 = dict(A=A, G=G, Qm=Qm, rv=2, new_data=0, **key)
+    g0 = run_gpu(crnt_lib, ctx, [t0], l0)
+    cbs0, _, ok0, soft = oracle_tb(orc, crnt_lib, t0, l0)
+    check_batch(orc, crnt_lib, [t0], [l0], g0)
+    assert not ok0 and not g0["res"][0]["tb_crc_ok"]
+    g2 = run_gpu(crnt_lib, ctx, [t2], l2)
+    cbs2, bits2, ok2, _ = oracle_tb(orc, crnt_lib, t2, l2, soft=soft)
+    assert ok2 and g2["res"][0]["tb_crc_ok"]
+    d0, d1, d2, it, hard, ext = cbs2[0]
+    D = len(d0)
+    assert np.array_equal(g2["d"][:D], d0) and np.array_equal(g2["d"][2 * D:3 * D], d2)
+    assert g2["res"][0]["cb_iters"][0] == it
+    assert np.array_equal(np.unpackbits(g2["out"]), bits2)
+    assert ctx.harq_release(3, 7, 2) == 0
+    assert ctx.harq_release(3, 7, 2) == crnt_lib.ENOTFOUND
+
+
+def test_harq_unknown_process_rejected(crnt_lib, ctx):
+    t = dict(A=2000, G=2400, Qm=2, rv=2, new_data=0, cell=9, ue=9, harq_pid=9,
+             flags=crnt_lib.F_HARQ)
+    with pytest.raises(crnt_lib.CrntError) as ei:
+        ctx.plan([t])
+    assert ei.value.code == crnt_lib.ENOTFOUND
+
+
+def test_full_tti_sampled(orc, crnt_lib, ctx):
+    # the benchmark's workload (40 cells x 8 UEs, A uniform over 16..75376,
+    # exactly 6 iterations) in its launch configuration; the oracle checks a
+    # sample of TBs one by one, and every TB's CRC must agree with the
+    # payload the library wrote
+    shapes = synth.tti_batch(seed=1, n_tb=320)
+    specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=6, early_stop=0, seed=300 + i,
+                  snr=s["snr_db"]) for i, s in enumerate(shapes)]
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs), debug=False)
+    sample = list(synth.randint(4, 0, 10, 0, 319))
+    sample = sorted(set(int(x) for x in sample))
+    check_batch(orc, crnt_lib, tbs, llrs, g, sample=sample)
+    assert sum(r["C"] for r in g["res"]) == g["info"]["n_cb"]
