@@ -384,8 +384,8 @@ int crnt_plan_create(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_
       d.f1 = lte::kF1[ki];
       d.f2 = lte::kF2[ki];
       d.f2x2 = (int)((2ll * d.f2) % K);
-      d.f2x16 = (int)((16ll * d.f2) % K);
-      d.f2x128 = (int)((128ll * d.f2) % K);
+      d.f2sub = (int)((2ll * kSub * d.f2) % K);
+      d.f2jump = (int)((2ll * kSub * kSub * d.f2) % K);
       d.R = lte::rows(K);
       d.ND = 32 * d.R - (K + 4);
       d.Nv = 3 * (K + 4) - 2 * F;

@@ -23,7 +23,9 @@ struct CbDesc {
   int32_t P, W;            // windows and window length (W = ceil(K/P))
   int32_t divM, divS;      // q / W == (q * divM) >> divS for 0 <= q < K + 4
   int32_t f1, f2;          // QPP parameters
-  int32_t f2x2, f2x16, f2x128;  // 2 f2, 16 f2, 128 f2 (all mod K)
+  int32_t f2x2;            // 2 f2 mod K: step of the QPP first difference
+  int32_t f2sub, f2jump;   // 2 kSub f2 and 2 kSub^2 f2 mod K: steps of the
+                           // kSub-step QPP differences (sub-window jumps)
   int32_t R, ND, Nv, rank0;     // sub-block rows, dummies, non-NULL count, rank of k0
   uint32_t maskB, mask2;   // column masks of the rank formula (see derm)
   int32_t tb;              // transport block index in the batch

@@ -424,15 +424,19 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
       for (int j = 2; j >= 0; j--) beta_tail_step(b, t[2 * j], t[2 * j + 1]);
     }
     const int nsub = (len + kSub - 1) / kSub;
-    int pis = 0, dls = 0, d8 = 0;
+    // QPP state at the start of the last sub-window, walked backwards by
+    // kSub steps: PI(x - kSub) = PI(x) - J(x - kSub) with
+    // J(x) = kSub f1 + f2 (2 kSub x + kSub^2), J(x - kSub) = J(x) - 2 kSub^2 f2,
+    // delta(x - kSub) = delta(x) - 2 kSub f2.
+    int pis = 0, dls = 0, jmp = 0;
     const int pad = ((K + 31) / 32) * 32 - K;
     if (DEC == 1) {
       const int is = lo + kSub * (nsub - 1);
       pis = qpp_at(is, f1, f2, K);
       dls = (f1 + (f2 * ((2 * is + 1) % K)) % K) % K;
-      int t = (16 * is - 64) % K;
+      int t = (2 * kSub * is - kSub * kSub) % K;
       if (t < 0) t += K;
-      d8 = ((8 * f1) % K + (f2 * t) % K) % K;
+      jmp = ((kSub * f1) % K + (f2 * t) % K) % K;
     }
     for (int sw = nsub - 1; sw >= 0; sw--) {
       const int j0 = sw * kSub;
@@ -483,9 +487,9 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
         }
       }
       if (DEC == 1) {
-        pis = modsub(pis, d8, K);
-        dls = modsub(dls, dp->f2x16, K);
-        d8 = modsub(d8, dp->f2x128, K);
+        pis = modsub(pis, jmp, K);
+        dls = modsub(dls, dp->f2sub, K);
+        jmp = modsub(jmp, dp->f2jump, K);
       }
     }
     if (p > 0) seedB[p - 1] = pack8(b);
@@ -511,7 +515,7 @@ __device__ uint32_t crc_share(const CbDesc& d, const CbSlot& sl, int p, const ui
     uint32_t word = sl.hard[w];
     const int wq = 32 * w;
     if (fq > wq) word = (fq >= wq + 32) ? 0u : (word & (0xFFFFFFFFu >> (fq - wq)));
-    if (mode == 1 && w == nw - 1) word &= 0xFFFFFF00u;
+    if (mode == 1 && w == nw - 1) word &= 0xFF000000u;  // drop the CB CRC (last 24 bits)
     r = crc_word(r, word, tab);
   }
   const int after = nw - w1;

@@ -79,6 +79,12 @@ def oracle_tb(orc, crnt, tb, llr, soft=None):
     return cbs, b[:A], tb_ok, soft
 
 
+def _diff(x, y):
+    """Mismatch summary: count and first few differing indices / values."""
+    d = np.nonzero(np.asarray(x) != np.asarray(y))[0]
+    return dict(n=len(d), first=[(int(i), int(x[i]), int(y[i])) for i in d[:4]])
+
+
 def check_batch(orc, crnt, tbs, llrs, g, sample=None):
     """Compare every (or a sample of) TB of a GPU run with the oracle:
     de-rate-matched streams, hard decisions, extrinsics, iteration counts,
@@ -108,8 +114,10 @@ def check_batch(orc, crnt, tbs, llrs, g, sample=None):
                 assert np.array_equal(gd[:D], d0), ("d0", t, r)
                 assert np.array_equal(gd[D:2 * D], d1), ("d1", t, r)
                 assert np.array_equal(gd[2 * D:], d2), ("d2", t, r)
-                assert np.array_equal(g["hard"][o:o + K], hard), ("hard", t, r)
-                assert np.array_equal(g["ext"][o:o + K], ext), ("ext", t, r)
+                gh, ge = g["hard"][o:o + K], g["ext"][o:o + K]
+                assert np.array_equal(gh, hard), ("hard", t, r, _diff(gh, hard),
+                                                  res["cb_iters"][r], it)
+                assert np.array_equal(ge, ext), ("ext", t, r, _diff(ge, ext))
             assert res["cb_iters"][r] == it, ("iters", t, r, res["cb_iters"][r], it)
             assert res["cb_crc_ok"][r] == (it <= tb.get("max_iter", 6)), ("cbok", t, r)
         assert res["tb_crc_ok"] == tb_ok, ("tbok", t)
