@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched uplink decode on GB300.
+
+One step = one 1 ms TTI of the batched uneven load: 40 cells x 8 UEs = 320
+transport blocks, A uniform over multiples of 8 in [16, 75376] (K 40..6144,
+C 1..13), QPSK/16QAM/64QAM, SNR within +-3 dB of each block's threshold,
+exactly 6 turbo iterations (early stop off), window count autotuned per K.
+The whole hot path runs in one persistent launch per step: de-rate-matching,
+turbo decoding, CRC, TB reassembly.  Inputs are synthetic (seeded), encoded
+by the library's own encoder and resident in HBM before timing; L2 is
+flushed before every timed step.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on the host cores, over bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "decoded info Gbit/s per GB300 at 6 iters"
+OPS_PER_STEP = 98        # algorithmic int ops per trellis step of one SISO pass
+LANES_PER_SM = 128       # int32 lanes issuing per SM per clock (4 SMSPs x 32)
+WORKLOAD = ("batched uneven load: 40 cells x 8 UEs per 1 ms TTI (320 TBs), A uniform over "
+            "multiples of 8 in [16, 75376], QPSK/16QAM/64QAM, SNR +-3 dB around threshold, "
+            "6 iterations, early stop off, P autotuned per K")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-tb", type=int, default=320)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def tti_shapes(seed, n_tb):
+    return synth.tti_batch(seed, n_tb=n_tb)
+
+
+def params(shapes, max_iter=6, early_stop=0):
+    return [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=max_iter, early_stop=early_stop)
+            for s in shapes]
+
+
+def channel(shapes, coded, seed):
+    """int8 LLRs of every TB (modulation, AWGN, max-log demap, quantise)."""
+    out, off = [], 0
+    for t, s in enumerate(shapes):
+        e = coded[off:off + s["G"]]
+        off += s["G"]
+        out.append(synth.channel_llrs(e, s["Qm"], synth.sigma2_snr(s["snr_db"]), seed,
+                                      1000 + t))
+    return np.concatenate(out)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+def oracle_sample_decoder(shapes, seed):
+    """Inputs for the oracle legs: the same TTI shapes, encoded by the oracle."""
+    import oracle
+    oracle.build()
+    items = []
+    for t, s in enumerate(shapes):
+        a = synth.bits(seed, 5000 + t, s["A"])
+        e = oracle.encode_tb(a, s["G"], Qm=s["Qm"])
+        llr = synth.channel_llrs(e, s["Qm"], synth.sigma2_snr(s["snr_db"]), seed, 1000 + t)
+        K = oracle.segment(s["A"] + 24)["Kp"]
+        items.append((s, llr, max(1, min(128, -(-K // 48)))))
+    return oracle, items
+
+
+def oracle_run(oracle, items, budget_s, pool, start=0):
+    """Decode TBs (exactly 6 iterations) on a thread pool until budget_s has
+    elapsed; returns (info bits, seconds, TBs decoded, next start)."""
+    t0 = time.perf_counter()
+    done_bits, n, i = 0, 0, start
+    futs = []
+
+    def one(it):
+        s, llr, P = it
+        oracle.decode_tb(llr, s["A"], s["G"], Qm=s["Qm"], P=P, max_iter=6, early_stop=False)
+        return s["A"]
+
+    while True:
+        while len(futs) < pool._max_workers and time.perf_counter() - t0 < budget_s:
+            futs.append(pool.submit(one, items[i % len(items)]))
+            i += 1
+        if not futs:
+            break
+        done_bits += futs.pop(0).result()
+        n += 1
+    return done_bits, time.perf_counter() - t0, n, i
+
+
+def run_reference(args):
+    import concurrent.futures as cf
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    shapes = tti_shapes(args.seed, args.n_tb)
+    oracle, items = oracle_sample_decoder(shapes, args.seed)
+    step_budget = max(0.2, min(5.0, 120.0 / max(1, args.steps + args.warmup)))
+    pool = cf.ThreadPoolExecutor(max_workers=cores)
+    pos = 0
+    for _ in range(args.warmup):
+        _, _, _, pos = oracle_run(oracle, items, step_budget, pool, pos)
+    bits = secs = tbs = 0
+    for _ in range(args.steps):
+        b, s, n, pos = oracle_run(oracle, items, step_budget, pool, pos)
+        bits, secs, tbs = bits + b, secs + s, tbs + n
+    pool.shutdown()
+    val = bits / secs / 1e9
+    sample = ("%d TBs of the TTI (mean A %.0f bits) per step, %.2f s budget per step, "
+              "thread pool of %d" % (tbs // max(1, args.steps), bits / max(1, tbs), step_budget,
+                                     cores))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gbit/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_tb": args.n_tb},
+            "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def profile_traffic():
+    """DRAM bytes per decode launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "decode_tti_320tb_ncu.txt")
+    src = os.path.join(ROOT, "paper_1905_01141_gb300", "csrc", "decode.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("decode_cu_sha256_16") == h and "dram_bytes_per_launch" in kv:
+            return float(kv["dram_bytes_per_launch"])
+    except OSError:
+        pass
+    return None
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1905_01141_gb300 as crnt
+    from paper_1905_01141_gb300 import build as crnt_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    crnt_build.build()
+    ctx = crnt.Context(local)
+
+    # ---- workload: this rank's TTI (weak scaling: cells partitioned by rank)
+    shapes = tti_shapes(args.seed + 7919 * rank, args.n_tb)
+    tbs = params(shapes)
+    pay = np.concatenate([np.packbits(synth.bits(args.seed + rank, 5000 + t, s["A"]))
+                          for t, s in enumerate(shapes)])
+    coded = np.zeros(sum(s["G"] for s in shapes), dtype=np.uint8)
+    ctx.encode_batch(tbs, pay, coded)
+    llr_h = channel(shapes, coded, args.seed + rank)
+    plan = ctx.plan(tbs)
+    info = plan.info
+    llr_d = torch.from_numpy(llr_h).to(dev)
+    out_d = torch.zeros(info["out_bytes"], dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+
+    def step():
+        plan.launch(llr_d, out_d, sh)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize()
+    res = plan.results(sh)
+    ok_frac = sum(r["tb_crc_ok"] for r in res) / len(res)
+    truth_ok = np.array_equal(out_d.cpu().numpy()[:len(pay)], pay) if ok_frac == 1.0 else None
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    bits_rank = info["info_bits"] * args.steps
+    if ws > 1:
+        t = torch.tensor([dev_s, float(bits_rank)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        dev_s, bits_all = float(tmax[0]), float(t[1])
+    else:
+        bits_all = float(bits_rank)
+    value = bits_all / dev_s / 1e9
+    mean_launch_s = sum(step_ms) / len(step_ms) / 1e3
+
+    # ---- roofline of the decode kernel (integer ALU issue)
+    ops = info["trellis_steps"] * OPS_PER_STEP * 2 * 6
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = sms * LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = ops / mean_launch_s / 1e12
+    traffic = profile_traffic()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_basis": "%d SMs x %d int32 lanes x %.0f MHz (median SM clock sampled in the "
+                          "timed region)" % (sms, LANES_PER_SM, mhz),
+            "ops_per_launch": ops}
+
+    line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_tb": args.n_tb, "n_cb": info["n_cb"],
+                       "info_bits_per_step": info["info_bits"], "llr_bytes": info["llr_bytes"],
+                       "work_items": info["n_items"], "grid": info["grid"],
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
+            "wall_s_timed_region": t_wall, "tb_crc_ok_fraction": ok_frac,
+            "payload_matches_truth": truth_ok}
+
+    if not args.no_extras and rank == 0:
+        line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
+        line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(shapes, args.seed)
+    plan.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_leg(ctx, tbs, llr_h, info, args):
+    """The same metric through crnt_decode_batch with pinned host buffers:
+    planning, H2D of the LLRs, the decode, D2H of bits and results."""
+    import torch
+    llr_p = torch.from_numpy(llr_h).pin_memory()
+    out_p = torch.zeros(info["out_bytes"], dtype=torch.uint8).pin_memory()
+    ln, on = llr_p.numpy(), out_p.numpy()
+    ctx.decode_batch(tbs, ln, on)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.decode_batch(tbs, ln, on)
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    return {"value": info["info_bits"] / dt / 1e9, "unit": "Gbit/s",
+            "h2d_bytes_per_step": int(info["llr_bytes"]),
+            "d2h_bytes_per_step": int(info["out_bytes"]) + 2 * int(info["n_cb"]) + len(tbs),
+            "ms_per_step": dt * 1e3, "steps": args.e2e_steps,
+            "api": "crnt_decode_batch (host pinned buffers)"}
+
+
+def subframe_latency(crnt, ctx, dev):
+    """Device latency of one 20 MHz uplink subframe (TBS 75376 -> 13 CBs of
+    K = 5824, G = 86400, 64QAM at 18..22 dB, early stop on, P autotuned)."""
+    import torch
+    lat = []
+    stream = torch.cuda.Stream(device=dev)
+    for i in range(30):
+        A, G = 75376, 86400
+        tb = [dict(A=A, G=G, Qm=6, P=0, max_iter=6, early_stop=1)]
+        pay = np.packbits(synth.bits(77, i, A))
+        coded = np.zeros(G, dtype=np.uint8)
+        ctx.encode_batch(tb, pay, coded)
+        llr = synth.channel_llrs(coded, 6, synth.sigma2_snr(18.0 + 4.0 * (i % 5) / 4), 77, i)
+        plan = ctx.plan(tb)
+        ld = torch.from_numpy(llr).to(dev)
+        od = torch.zeros(A // 8, dtype=torch.uint8, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            plan.launch(ld, od, stream.cuda_stream)
+            e0.record(stream)
+            plan.launch(ld, od, stream.cuda_stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1) * 1e3)
+        plan.close()
+    lat.sort()
+    return {"p50_us": lat[len(lat) // 2], "p99_us": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "max_us": lat[-1], "n": len(lat),
+            "what": "device time of one 20 MHz subframe decode (13 CBs, early stop)"}
+
+
+def cpu_baseline(shapes, seed):
+    import concurrent.futures as cf
+    cores = os.cpu_count() or 1
+    oracle, items = oracle_sample_decoder(shapes[:96], seed)
+    with cf.ThreadPoolExecutor(max_workers=cores) as pool:
+        bits, secs, n, _ = oracle_run(oracle, items, 15.0, pool)
+    return {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "sample": "%d TBs of the TTI workload (first 96 shapes, cycled), 6 iterations, "
+                      "thread pool of %d, %.1f s" % (n, cores, secs)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -636,11 +636,87 @@ int crnt_decode_tb(crnt_ctx* ctx, const int8_t* llr, const crnt_tb_params* tb, u
   return crnt_decode_batch(ctx, tb, 1, llr, out, res);
 }
 
-// not yet implemented entry points
-int crnt_encode_batch(crnt_ctx*, const crnt_tb_params*, uint32_t, const uint8_t*, uint8_t*) {
-  return CRNT_EINVAL;
+int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, const uint8_t* bits,
+                      uint8_t* e_out) {
+  if (!ctx || !tbs || !bits || !e_out || n == 0) return CRNT_EINVAL;
+  cudaSetDevice(ctx->device);
+  std::vector<EncCb> cbs;
+  std::vector<int64_t> in_off(n);
+  std::vector<int32_t> As(n);
+  int64_t ioff = 0, eoff = 0;
+  for (uint32_t t = 0; t < n; t++) {
+    lte::Seg s;
+    int rc = validate(tbs[t], &s);
+    if (rc) return rc;
+    in_off[t] = ioff;
+    As[t] = (int32_t)tbs[t].A;
+    int pay_off = 0;
+    for (int r = 0; r < s.C; r++) {
+      EncCb c;
+      memset(&c, 0, sizeof c);
+      const int K = lte::cb_k(s, r);
+      c.K = K;
+      c.F = r == 0 ? s.F : 0;
+      c.E = lte::e_r((int)tbs[t].G, tbs[t].Qm, tbs[t].NL, s.C, r);
+      c.R = lte::rows(K);
+      c.ND = 32 * c.R - (K + 4);
+      const int k0 = lte::k0(K, tbs[t].rv);
+      int rank0 = 0;
+      for (int w = 0; w < k0; w++) rank0 += lte::w_non_null(K, c.F, w) ? 1 : 0;
+      c.rank0 = rank0;
+      const int ki = lte::index_of(K);
+      c.f1 = lte::kF1[ki];
+      c.f2 = lte::kF2[ki];
+      c.tb = (int)t;
+      c.pay_bits = K - c.F - s.L;
+      c.pay_off = pay_off;
+      c.crc_b = s.C > 1;
+      c.e_off = eoff;
+      pay_off += c.pay_bits;
+      eoff += c.E;
+      cbs.push_back(c);
+    }
+    ioff += tbs[t].A / 8;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = ctx->stream;
+  const size_t b_cbs = sizeof(EncCb) * cbs.size(), b_off = 8 * n, b_A = 4 * n;
+  const size_t o_off = (b_cbs + 255) & ~size_t(255), o_A = o_off + ((b_off + 255) & ~size_t(255));
+  const size_t o_bits = o_A + ((b_A + 255) & ~size_t(255));
+  const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(e_out);
+  const size_t total = o_bits + (bits_dev ? 0 : (size_t)ioff);
+  if (ctx->stage_in.ensure(total) != cudaSuccess) return CRNT_ENOMEM;
+  if (!out_dev && ctx->stage_out.ensure((size_t)eoff) != cudaSuccess) return CRNT_ENOMEM;
+  std::vector<uint8_t> host(o_bits, 0);
+  memcpy(host.data(), cbs.data(), b_cbs);
+  memcpy(host.data() + o_off, in_off.data(), b_off);
+  memcpy(host.data() + o_A, As.data(), b_A);
+  uint8_t* base = (uint8_t*)ctx->stage_in.p;
+  if (cudaMemcpyAsync(base, host.data(), o_bits, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CRNT_EDEVICE;
+  if (!bits_dev &&
+      cudaMemcpyAsync(base + o_bits, bits, (size_t)ioff, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CRNT_EDEVICE;
+  EncParams p;
+  p.cbs = (const EncCb*)base;
+  p.tb_in_off = (const int64_t*)(base + o_off);
+  p.tb_A = (const int32_t*)(base + o_A);
+  p.tb_bits = bits_dev ? bits : base + o_bits;
+  p.e_out = out_dev ? e_out : (uint8_t*)ctx->stage_out.p;
+  p.xpowA = ctx->xpowA;
+  p.xpowB = ctx->xpowB;
+  if (launch_encode(p, (int)cbs.size(), st) != cudaSuccess) return CRNT_EDEVICE;
+  if (!out_dev &&
+      cudaMemcpyAsync(e_out, p.e_out, (size_t)eoff, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CRNT_EDEVICE;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CRNT_EDEVICE;
+  return CRNT_OK;
 }
-int crnt_encode_tb(crnt_ctx*, const uint8_t*, const crnt_tb_params*, uint8_t*) { return CRNT_EINVAL; }
+
+int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb, uint8_t* e_out) {
+  return crnt_encode_batch(ctx, tb, 1, bits, e_out);
+}
+
 int crnt_submit(crnt_ctx*, const crnt_tb_params*, const int8_t* const*, uint32_t, uint64_t*) {
   return CRNT_EINVAL;
 }

@@ -83,35 +83,33 @@ struct DecParams {
   uint8_t* dbg_hard;      // optional: [sum K] hard decisions
 };
 
-// Encoder launch description.
+// Encoder launch description: one CB per CTA.
 struct EncCb {
-  int32_t K, F, E, k0;
-  int32_t R, ND;
-  int32_t f1, f2;
-  int32_t tb, r;
-  int32_t pay_bits, pay_off;  // payload bits and TB bit offset
-  int64_t e_off;              // output offset (bits, one per byte)
-  uint8_t crc_b;
-  uint8_t pad0[7];
+  int32_t K, F, E;
+  int32_t R, ND, rank0;       // circular-buffer geometry and rank of k0
+  int32_t f1, f2;             // QPP parameters
+  int32_t tb;                 // transport block index
+  int32_t pay_bits, pay_off;  // payload bits of the CB and their TB bit offset
+  uint8_t crc_b;              // 1: CRC24B attached (C > 1)
+  uint8_t pad0[3];
+  int64_t e_off;              // first output byte (one coded bit per byte)
 };
 
 struct EncParams {
   const EncCb* cbs;
-  int32_t n_cbs;
-  const uint8_t* tb_bits;     // packed TB payload bits (MSB first), per TB at tb_in_off
-  const int64_t* tb_in_off;   // [n_tbs] byte offsets
-  const uint32_t* tb_crc;     // [n_tbs] CRC24A of each TB (computed by a first pass)
-  const int32_t* tb_A;        // [n_tbs]
+  const uint8_t* tb_bits;     // packed TB payloads (MSB first)
+  const int64_t* tb_in_off;   // [n_tbs] byte offset of each payload
+  const int32_t* tb_A;        // [n_tbs] payload bits
   uint8_t* e_out;
-  uint32_t* tb_crc_rw;        // writable alias of tb_crc for the CRC pass
-  const uint32_t* xpowA;
+  const uint32_t* xpowA;      // x^(32 s) mod gCRC24A
+  const uint32_t* xpowB;      // x^(32 s) mod gCRC24B
 };
 
 // Kernel launchers (decode.cu / encode.cu).
 cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s);
 int decode_max_smem();
 int decode_occupancy(int smem);  // resident decode CTAs per SM at this smem
-cudaError_t launch_encode(const EncParams& p, int n_tbs, cudaStream_t s);
+cudaError_t launch_encode(const EncParams& p, int n_cbs, cudaStream_t s);
 
 // Shared-memory bytes of one CB slot in the decode kernel.
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }

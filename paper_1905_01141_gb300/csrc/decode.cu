@@ -21,10 +21,11 @@
 // Layout in shared memory (per CB slot): channel LLRs and the extrinsic are
 // stored transposed, element k at (k mod W) * P + k / W, so that the P
 // window threads of a warp touch consecutive addresses at every step.
-// Forward metrics are checkpointed every 8 steps and recomputed, 8 steps at a
-// time, into registers during the backward pass.
+// Forward metrics are checkpointed every kSub steps and recomputed, kSub
+// steps at a time, into registers during the backward pass.
 #include <cstdint>
 #include "crnt_internal.h"
+#include "rm_geom.cuh"
 
 namespace crnt {
 namespace {
@@ -233,88 +234,38 @@ __device__ __forceinline__ uint32_t crc_word(uint32_t r, uint32_t w, const uint3
 }
 
 // ---------------------------------------------------------------- de-RM
-// De-rate-matching + HARQ combining of one CB into its shared-memory slot.
-// Circular buffer w (TS 36.212 5.1.4.1): v0 = 32 columns x R rows read by
-// column after the bit-reversal column permutation; then v1/v2 interlaced.
-// Unit u < 32 is column u of v0; unit 32 + c holds rows of column c of v1
-// and v2.  The rank (count of non-NULL positions before a position) has a
-// closed form: with X = ND + F = 32 a + b, column c of v0/v1 has
-// n0(c) = a + [P(c) < b] leading NULLs and column c of v2 has
-// n2(c) = [P(c) < ND - 1] (plus the wrapped NULL at the end of column 31).
+// De-rate-matching + HARQ combining of one CB into its shared-memory slot:
+// every non-NULL circular-buffer position gathers, in order, the received
+// LLRs e_k with k = rank - rank(k0) (mod Nv), k < E, adding them with
+// saturation to [-127, 127] onto the stored soft value (or 0 for new data),
+// and writes the result to its d-stream (and back to the soft buffer).
 __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restrict__ llr,
                         int8_t* __restrict__ soft_arena, int tid, int nthr) {
-  const int K = d.K, F = d.F, R = d.R, ND = d.ND, E = d.E, Nv = d.Nv;
-  const int KPI = 32 * R;
-  const int X = ND + F, xa = X >> 5;
+  const int K = d.K, F = d.F, R = d.R, E = d.E, Nv = d.Nv, rank0 = d.rank0;
+  const RmGeom g{K, F, R, d.ND, d.maskB, d.mask2};
   const int8_t* e = llr + d.llr_off;
   int8_t* soft = d.soft_off >= 0 ? soft_arena + d.soft_off : nullptr;
   const bool combine = soft != nullptr && !d.new_data;
+  int8_t* const streams[3] = {sl.sys, sl.par1, sl.par2};
   const int nrows = 64 * R;
   for (int x = tid; x < nrows; x += nthr) {
     const int unit = x / R;
     const int i = x - unit * R;
-    const int c = unit & 31;
-    const int Pc = (int)(__brev((unsigned)c) >> 27);
-    const unsigned low = (1u << c) - 1u;
-    const int n0c = xa + ((d.maskB >> c) & 1u);
-    const int pre0 = xa * c + __popc(d.maskB & low);
-    if (unit < 32) {
-      const int p = c * R + i;
-      const int y = Pc + 32 * i;
-      int8_t v = 0;
-      if (y >= X) {
-        const int rank = c * R - pre0 + (i - n0c);
-        int k = rank - d.rank0;
-        if (k < 0) k += Nv;
-        int acc = combine ? soft[p] : 0;
-        for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
-        v = (int8_t)acc;
-        const int di = y - ND;
-        if (di < K) sl.sys[tr_idx(di, d)] = v;
-        else sl.tail[3 * (di - K)] = v;
-        if (soft) soft[p] = v;
-      } else if (soft && !combine) {
-        soft[p] = 0;
-      }
-    } else {
-      const int n2c = (d.mask2 >> c) & 1u;
-      const int pre2 = __popc(d.mask2 & low);
-      const int base = (KPI - X) + 2 * R * c - pre0 - pre2;
-      const int r1 = base + max(0, i - n0c) + max(0, i - n2c);
-      const int p1 = KPI + 2 * (c * R + i);
-      // v1 (parity of encoder 1)
-      const int y1 = Pc + 32 * i;
-      const bool nn1 = y1 >= X;
-      int8_t v1 = 0, v2 = 0;
-      if (nn1) {
-        int k = r1 - d.rank0;
-        if (k < 0) k += Nv;
-        int acc = combine ? soft[p1] : 0;
-        for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
-        v1 = (int8_t)acc;
-        const int di = y1 - ND;
-        if (di < K) sl.par1[tr_idx(di, d)] = v1;
-        else sl.tail[3 * (di - K) + 1] = v1;
-      }
-      // v2 (parity of encoder 2)
-      int y2 = Pc + 32 * i + 1;
-      if (y2 == KPI) y2 = 0;
-      const bool nn2 = y2 >= ND;
-      if (nn2) {
-        int k = r1 + (nn1 ? 1 : 0) - d.rank0;
-        if (k < 0) k += Nv;
-        int acc = combine ? soft[p1 + 1] : 0;
-        for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
-        v2 = (int8_t)acc;
-        const int di = y2 - ND;
-        if (di < K) sl.par2[tr_idx(di, d)] = v2;
-        else sl.tail[3 * (di - K) + 2] = v2;
-      }
-      if (soft) {
-        if (nn1 || !combine) soft[p1] = v1;
-        if (nn2 || !combine) soft[p1 + 1] = v2;
-      }
-    }
+    rm_visit(
+        g, unit, i,
+        [&](int p, int st, int di, int rank) {
+          int k = rank - rank0;
+          if (k < 0) k += Nv;
+          int acc = combine ? soft[p] : 0;
+          for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
+          const int8_t v = (int8_t)acc;
+          if (di < K) streams[st][tr_idx(di, d)] = v;
+          else sl.tail[3 * (di - K) + st] = v;
+          if (soft) soft[p] = v;
+        },
+        [&](int p) {
+          if (soft && !combine) soft[p] = 0;
+        });
   }
   // filler: known zero bits in the systematic stream, unknown parity 1
   for (int k = tid; k < F; k += nthr) {
