@@ -64,6 +64,12 @@ __device__ __forceinline__ int gval(int code, int S, int T, int Lp) {
   return code == 3 ? T : code == 2 ? S : code == 1 ? Lp : 0;
 }
 
+// State metrics are held with an offset: stored value = metric + OFF, so a
+// saturated int16 metric occupies exactly [0, 65535].  Offsets cancel in
+// every comparison and in Lambda.
+constexpr int OFF = 32768;
+constexpr int MINF_OFF = MINF + OFF;
+
 // max(x0 + g0, x1 + g1) with the add folded into a DPX add-max when one of
 // the branch metrics is zero.
 __device__ __forceinline__ int acs2(int x0, int c0, int x1, int c1, int S, int T, int Lp) {
@@ -72,20 +78,29 @@ __device__ __forceinline__ int acs2(int x0, int c0, int x1, int c1, int S, int T
   return __viaddmax_s32(x0, gval(c0, S, T, Lp), x1 + gval(c1, S, T, Lp));
 }
 
-// sat16(m - m0) given nm0 = -m0
-__device__ __forceinline__ int norm16(int m, int nm0) {
-  return max(__viaddmin_s32(m, nm0, 32767), -32768);
+// Normalisation by state 0 with int16 saturation, in offset form:
+// o[s] = sat16(m[s] - m[0]) + OFF.  The subtraction runs on the FMA pipe;
+// one OR over the results detects the (rare) case where a value left
+// [0, 65535], and only then are the clamps applied -- the result equals the
+// saturating definition in every case.
+__device__ __forceinline__ void normalise(const int m[8], int o[8]) {
+  const int base = OFF - m[0];
+  o[0] = OFF;
+#pragma unroll
+  for (int s = 1; s < 8; s++) o[s] = m[s] + base;
+  const unsigned any = (unsigned)(o[1] | o[2] | o[3] | o[4] | o[5] | o[6] | o[7]);
+  if (any > 0xFFFFu) {
+#pragma unroll
+    for (int s = 1; s < 8; s++) o[s] = min(max(o[s], 0), 65535);
+  }
 }
 
-__device__ __forceinline__ void alpha_step(int a[8], int S, int T, int Lp) {
+__device__ __forceinline__ void alpha_step(const int a[8], int o[8], int S, int T, int Lp) {
   int m[8];
 #pragma unroll
   for (int n = 0; n < 8; n++)
     m[n] = acs2(a[pred(n, 0)], pcode(n, 0), a[pred(n, 1)], pcode(n, 1), S, T, Lp);
-  const int nm0 = -m[0];
-  a[0] = 0;
-#pragma unroll
-  for (int n = 1; n < 8; n++) a[n] = norm16(m[n], nm0);
+  normalise(m, o);
 }
 
 __device__ __forceinline__ void beta_step(int b[8], int S, int T, int Lp) {
@@ -93,10 +108,7 @@ __device__ __forceinline__ void beta_step(int b[8], int S, int T, int Lp) {
 #pragma unroll
   for (int s = 0; s < 8; s++)
     m[s] = acs2(b[nxt(s, 0)], gcode(s, 0), b[nxt(s, 1)], gcode(s, 1), S, T, Lp);
-  const int nm0 = -m[0];
-  b[0] = 0;
-#pragma unroll
-  for (int s = 1; s < 8; s++) b[s] = norm16(m[s], nm0);
+  normalise(m, b);
 }
 
 // Terminating tail step: each state leaves on the branch that feeds a = 0.
@@ -105,39 +117,39 @@ __device__ __forceinline__ void beta_tail_step(int b[8], int Ls, int Lp) {
 #pragma unroll
   for (int s = 0; s < 8; s++) {
     const int u = ((s >> 1) ^ s) & 1;  // r2 ^ r3
-    const int c = gcode(s, u);
-    m[s] = b[nxt(s, u)] + gval(c, Ls, Ls + Lp, Lp);
+    m[s] = b[nxt(s, u)] + gval(gcode(s, u), Ls, Ls + Lp, Lp);
   }
-  const int nm0 = -m[0];
-  b[0] = 0;
-#pragma unroll
-  for (int s = 1; s < 8; s++) b[s] = norm16(m[s], nm0);
+  normalise(m, b);
 }
 
-// Lambda and the extrinsic of one step: returns Le, writes Lambda.
+__device__ __forceinline__ int max8(const int v[8]) {
+  return max(__vimax3_s32(__vimax3_s32(v[0], v[1], v[2]), __vimax3_s32(v[3], v[4], v[5]), v[6]),
+             v[7]);
+}
+
+// Lambda and the extrinsic of one step: returns Le, writes Lambda.  The
+// sums alpha + beta (+ Lp when the branch parity is 0) are formed on the FMA
+// pipe; the two maxima use 3-input max.  The S common to the u = 0 branches
+// is added back at the end.
 __device__ __forceinline__ int app_step(const int a[8], const int b[8], int S, int Lp, int* lam_out) {
-  int acc[4];
-  bool first[4] = {true, true, true, true};
+  int v0[8], v1[8];
 #pragma unroll
   for (int s = 0; s < 8; s++)
 #pragma unroll
     for (int u = 0; u < 2; u++) {
-      const int c = gcode(s, u);
-      const int n = nxt(s, u);
-      if (first[c]) {
-        acc[c] = a[s] + b[n];
-        first[c] = false;
-      } else {
-        acc[c] = __viaddmax_s32(a[s], b[n], acc[c]);
-      }
+      const int t = a[s] + b[nxt(s, u)] + ((gcode(s, u) & 1) ? Lp : 0);
+      if (u == 0) v0[s] = t;
+      else v1[s] = t;
     }
-  // u = 0: codes 3 (p = 0, + Lp) and 2; u = 1: codes 1 (+ Lp) and 0.  The
-  // common S of the u = 0 branches is added back below.
-  const int best0 = __viaddmax_s32(acc[3], Lp, acc[2]);
-  const int best1 = __viaddmax_s32(acc[1], Lp, acc[0]);
-  const int lam = max(__viaddmin_s32(S, best0 - best1, 32767), -32768);
+  const int d = max8(v0) - max8(v1);
+  int lam = S + d;
+  int le = d;
+  if (((unsigned)(lam + 32768) | (unsigned)(le + 32768)) > 0xFFFFu) {
+    lam = min(max(lam, -32768), 32767);
+    le = min(max(lam - S, -32768), 32767);
+  }
   *lam_out = lam;
-  return max(__viaddmin_s32(lam, -S, 32767), -32768);
+  return le;
 }
 
 __device__ __forceinline__ int scale_ext(int le) { return (le * 3) >> 2; }
@@ -150,13 +162,11 @@ __device__ __forceinline__ uint4 pack8(const int v[8]) {
   r.w = __byte_perm(v[6], v[7], 0x5410);
   return r;
 }
-__device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xFFFFu); }
-__device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
 __device__ __forceinline__ void unpack8(uint4 r, int v[8]) {
-  v[0] = lo16(r.x); v[1] = hi16(r.x);
-  v[2] = lo16(r.y); v[3] = hi16(r.y);
-  v[4] = lo16(r.z); v[5] = hi16(r.z);
-  v[6] = lo16(r.w); v[7] = hi16(r.w);
+  v[0] = r.x & 0xFFFF; v[1] = r.x >> 16;
+  v[2] = r.y & 0xFFFF; v[3] = r.y >> 16;
+  v[4] = r.z & 0xFFFF; v[5] = r.z >> 16;
+  v[6] = r.w & 0xFFFF; v[7] = r.w >> 16;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -284,6 +294,76 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restr
 }
 
 // ---------------------------------------------------------------- SISO
+// Per-window state of one SISO pass.
+struct Win {
+  const int8_t* __restrict__ sys;
+  const int8_t* __restrict__ par;
+  int16_t* ext;
+  uint32_t* hard;
+  int K, P, W, divM, divS;  // geometry (tr_idx)
+  int f2x2;                 // QPP first-difference step
+  int p, lo, len, pad;
+};
+
+__device__ __forceinline__ int tr_w(const Win& w, int q) {
+  const int t = (int)(((unsigned)q * (unsigned)w.divM) >> w.divS);
+  return (q - t * w.W) * w.P + t;
+}
+
+// Load the branch-metric inputs of step j (window-relative) of pass DEC.
+// DEC 1 walks the QPP addresses (q, dq) and returns the natural position.
+template <int DEC>
+__device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, int& S, int& Lp,
+                                          int& t) {
+  const int idx = j * w.P + w.p;
+  if (DEC == 0) {
+    t = idx;
+  } else {
+    t = tr_w(w, q);
+  }
+  S = (int)w.sys[t] + (int)w.ext[t];
+  Lp = w.par[idx];
+  if (DEC == 1) {
+    q = modadd(q, dq, w.K);
+    dq = modadd(dq, w.f2x2, w.K);
+  }
+}
+
+// Backward processing of one sub-window [j0, j0 + slen) of a window:
+// recompute forward metrics from the checkpoint into registers, then walk
+// back computing Lambda / Le and the backward metrics.  FULL: slen == kSub
+// (no per-step guards).
+template <int DEC, bool FULL>
+__device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
+                                                int dq, int b[8]) {
+  int A[kSub][8];
+  int Sv[kSub], Lv[kSub], Tv[kSub], Qv[kSub];
+  unpack8(ck, A[0]);
+#pragma unroll
+  for (int jj = 0; jj < kSub; jj++) {
+    if (FULL || jj < slen) {
+      Qv[jj] = q;
+      load_step<DEC>(w, j0 + jj, q, dq, Sv[jj], Lv[jj], Tv[jj]);
+      if (jj + 1 < kSub && (FULL || jj + 1 < slen))
+        alpha_step(A[jj], A[jj + 1], Sv[jj], Sv[jj] + Lv[jj], Lv[jj]);
+    }
+  }
+#pragma unroll
+  for (int jj = kSub - 1; jj >= 0; jj--) {
+    if (FULL || jj < slen) {
+      const int S = Sv[jj], Lp = Lv[jj];
+      int lam;
+      const int le = app_step(A[jj], b, S, Lp, &lam);
+      w.ext[Tv[jj]] = (int16_t)scale_ext(le);
+      if (DEC == 1 && lam < 0) {
+        const int qq = Qv[jj] + w.pad;
+        atomicOr(&w.hard[qq >> 5], 1u << (31 - (qq & 31)));
+      }
+      beta_step(b, S, S + Lp, Lp);
+    }
+  }
+}
+
 // One SISO pass of window p of one CB.  DEC = 0: natural order (encoder 1),
 // DEC = 1: QPP order (encoder 2).  All threads of the CTA call it (run =
 // false for idle threads) because it contains barriers.
@@ -292,14 +372,6 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
                                           bool run, bool first) {
   const int K = dp->K, P = dp->P, W = dp->W;
   const CbSlot sl = make_slot(base, K, P, W);
-  CbDesc d;
-  d.W = W;
-  d.P = P;
-  d.divM = dp->divM;
-  d.divS = dp->divS;
-  const int lo = p * W;
-  const int len = min(W, K - lo);
-  const int8_t* __restrict__ par = DEC ? sl.par2 : sl.par1;
   uint4* seedA = sl.seed + DEC * P;
   uint4* seedB = sl.seed + (2 + DEC) * P;
   uint4* ck = sl.ck + p * ((W + kSub - 1) / kSub);
@@ -307,22 +379,22 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
   int a[8], b[8];
   if (run) {
     if (p == 0) {
-      a[0] = 0;
+      a[0] = OFF;
 #pragma unroll
-      for (int s = 1; s < 8; s++) a[s] = MINF;
+      for (int s = 1; s < 8; s++) a[s] = MINF_OFF;
     } else if (first) {
 #pragma unroll
-      for (int s = 0; s < 8; s++) a[s] = 0;
+      for (int s = 0; s < 8; s++) a[s] = OFF;
     } else {
       unpack8(seedA[p], a);
     }
     if (p == P - 1) {
-      b[0] = 0;
+      b[0] = OFF;
 #pragma unroll
-      for (int s = 1; s < 8; s++) b[s] = MINF;
+      for (int s = 1; s < 8; s++) b[s] = MINF_OFF;
     } else if (first) {
 #pragma unroll
-      for (int s = 0; s < 8; s++) b[s] = 0;
+      for (int s = 0; s < 8; s++) b[s] = OFF;
     } else {
       unpack8(seedB[p], b);
     }
@@ -333,42 +405,55 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
   }
   __syncthreads();
   if (run) {
+    Win w;
+    w.sys = sl.sys;
+    w.par = DEC ? sl.par2 : sl.par1;
+    w.ext = sl.ext;
+    w.hard = sl.hard;
+    w.K = K;
+    w.P = P;
+    w.W = W;
+    w.divM = dp->divM;
+    w.divS = dp->divS;
+    w.f2x2 = dp->f2x2;
+    w.p = p;
+    w.lo = p * W;
+    w.len = min(W, K - w.lo);
+    w.pad = ((K + 31) / 32) * 32 - K;
+    const int lo = w.lo, len = w.len;
     const int f1 = dp->f1, f2 = dp->f2;
-    const int f2x2 = dp->f2x2;
-    // ---- forward pass with checkpoints
-    int pi = 0, dl = 0;
+
+    // ---- forward pass with a checkpoint every kSub steps
+    int q = 0, dq = 0;
     if (DEC == 1) {
-      pi = qpp_at(lo, f1, f2, K);
-      dl = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
+      q = qpp_at(lo, f1, f2, K);
+      dq = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
     }
-    int idx = p;
-    for (int j0 = 0; j0 < len; j0 += kSub) {
+    int j0 = 0;
+    for (; j0 + kSub <= len; j0 += kSub) {
       ck[j0 / kSub] = pack8(a);
-      const int slen = min(kSub, len - j0);
 #pragma unroll
-      for (int jj = 0; jj < kSub; jj++) {
-        if (jj < slen) {
-          int Ls, La;
-          if (DEC == 0) {
-            Ls = sl.sys[idx];
-            La = sl.ext[idx];
-          } else {
-            const int t = tr_idx(pi, d);
-            Ls = sl.sys[t];
-            La = sl.ext[t];
-            pi = modadd(pi, dl, K);
-            dl = modadd(dl, f2x2, K);
-          }
-          const int Lp = par[idx];
-          const int S = Ls + La;
-          alpha_step(a, S, S + Lp, Lp);
-          idx += P;
-        }
+      for (int jj = 0; jj < kSub; jj += 2) {
+        int S, Lp, t, o[8];
+        load_step<DEC>(w, j0 + jj, q, dq, S, Lp, t);
+        alpha_step(a, o, S, S + Lp, Lp);
+        load_step<DEC>(w, j0 + jj + 1, q, dq, S, Lp, t);
+        alpha_step(o, a, S, S + Lp, Lp);
+      }
+    }
+    if (j0 < len) {
+      ck[j0 / kSub] = pack8(a);
+      for (int j = j0; j < len; j++) {
+        int S, Lp, t, o[8];
+        load_step<DEC>(w, j, q, dq, S, Lp, t);
+        alpha_step(a, o, S, S + Lp, Lp);
+#pragma unroll
+        for (int s = 0; s < 8; s++) a[s] = o[s];
       }
     }
     if (p + 1 < P) seedA[p + 1] = pack8(a);
 
-    // ---- backward pass
+    // ---- backward pass, one sub-window at a time from the end
     if (p == P - 1) {
       const int8_t* t = sl.tail + (DEC ? 6 : 0);
 #pragma unroll
@@ -380,7 +465,6 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     // J(x) = kSub f1 + f2 (2 kSub x + kSub^2), J(x - kSub) = J(x) - 2 kSub^2 f2,
     // delta(x - kSub) = delta(x) - 2 kSub f2.
     int pis = 0, dls = 0, jmp = 0;
-    const int pad = ((K + 31) / 32) * 32 - K;
     if (DEC == 1) {
       const int is = lo + kSub * (nsub - 1);
       pis = qpp_at(is, f1, f2, K);
@@ -389,54 +473,19 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
       if (t < 0) t += K;
       jmp = ((kSub * f1) % K + (f2 * t) % K) % K;
     }
-    for (int sw = nsub - 1; sw >= 0; sw--) {
-      const int j0 = sw * kSub;
-      const int slen = min(kSub, len - j0);
-      int A[kSub][8];
-      int Sv[kSub], Lv[kSub], Qv[kSub];
-      unpack8(ck[sw], A[0]);
-      int q = pis, dq = dls;
-      int idx2 = (j0)*P + p;
-#pragma unroll
-      for (int jj = 0; jj < kSub; jj++) {
-        if (jj < slen) {
-          int Ls, La, t;
-          if (DEC == 0) {
-            t = idx2;
-          } else {
-            t = tr_idx(q, d);
-            Qv[jj] = q;
-            q = modadd(q, dq, K);
-            dq = modadd(dq, f2x2, K);
-          }
-          Ls = sl.sys[t];
-          La = sl.ext[t];
-          const int Lp = par[idx2];
-          Sv[jj] = Ls + La;
-          Lv[jj] = Lp;
-          if (jj + 1 < kSub && jj + 1 < slen) {
-#pragma unroll
-            for (int s = 0; s < 8; s++) A[jj + 1][s] = A[jj][s];
-            alpha_step(A[jj + 1], Sv[jj], Sv[jj] + Lp, Lp);
-          }
-          idx2 += P;
-        }
+    int sw = nsub - 1;
+    const int last_len = len - kSub * sw;
+    if (last_len < kSub) {
+      sub_window_back<DEC, false>(w, ck[sw], kSub * sw, last_len, pis, dls, b);
+      if (DEC == 1) {
+        pis = modsub(pis, jmp, K);
+        dls = modsub(dls, dp->f2sub, K);
+        jmp = modsub(jmp, dp->f2jump, K);
       }
-#pragma unroll
-      for (int jj = kSub - 1; jj >= 0; jj--) {
-        if (jj < slen) {
-          const int S = Sv[jj], Lp = Lv[jj];
-          int lam;
-          const int le = app_step(A[jj], b, S, Lp, &lam);
-          const int t = (DEC == 0) ? (j0 + jj) * P + p : tr_idx(Qv[jj], d);
-          sl.ext[t] = (int16_t)scale_ext(le);
-          if (DEC == 1 && lam < 0) {
-            const int qq = Qv[jj] + pad;
-            atomicOr(&sl.hard[qq >> 5], 1u << (31 - (qq & 31)));
-          }
-          beta_step(b, S, S + Lp, Lp);
-        }
-      }
+      sw--;
+    }
+    for (; sw >= 0; sw--) {
+      sub_window_back<DEC, true>(w, ck[sw], kSub * sw, kSub, pis, dls, b);
       if (DEC == 1) {
         pis = modsub(pis, jmp, K);
         dls = modsub(dls, dp->f2sub, K);
