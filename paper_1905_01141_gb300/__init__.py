@@ -216,26 +216,36 @@ class Context:
                "crnt_encode_batch")
 
     def submit(self, tbs, llrs):
+        """Queue TBs with their host LLR arrays; returns tickets, or None when
+        admission is refused (CRNT_EAGAIN)."""
         arr = params_array(tbs)
-        ptrs = (ctypes.c_void_p * len(arr))(*[_ptr(x) for x in llrs])
+        keep = [np.ascontiguousarray(x, dtype=np.int8) for x in llrs]
+        ptrs = (ctypes.c_void_p * len(arr))(*[x.ctypes.data for x in keep])
         tickets = (ctypes.c_uint64 * len(arr))()
         rc = load().crnt_submit(self.h, arr, ptrs, len(arr), tickets)
         if rc == EAGAIN:
             return None
         _check(rc, "crnt_submit")
+        if not hasattr(self, "_nbytes"):
+            self._nbytes = {}
+        for t, p in zip(tickets, arr):
+            self._nbytes[t] = p.A // 8
         return list(tickets)
 
-    def poll(self, max_n=256, timeout_us=0, out_sizes=None):
-        """Returns a list of (result dict, bytes of the decoded TB)."""
+    def poll(self, max_n=256, timeout_us=0):
+        """Returns a list of (result dict, decoded payload bytes)."""
         res = (TbResult * max_n)()
         bits = (ctypes.c_void_p * max_n)()
         n = load().crnt_poll(self.h, res, bits, max_n, timeout_us)
         if n < 0:
             _check(n, "crnt_poll")
+        nb = getattr(self, "_nbytes", {})
         out = []
         for i in range(n):
             d = res[i].as_dict()
-            out.append((d, bits[i]))
+            size = nb.pop(d["ticket"], 0)
+            data = ctypes.string_at(bits[i], size) if bits[i] and size else b""
+            out.append((d, data))
         return out
 
     def harq_release(self, cell, ue, pid):

@@ -3,33 +3,26 @@
 // The planner turns a batch of transport blocks into code-block descriptors
 // and work items (the device counterpart of the paper's Algorithm 1 queuing
 // step), binds HARQ processes to device soft buffers, and launches the fused
-// decode kernel whose CTAs drain the work queue (Algorithm 2).  The serving
-// loop (crnt_submit / crnt_poll) batches requests continuously on a pool of
-// CUDA streams.
+// decode kernel whose CTAs drain the work queue (Algorithm 2).  Plans keep
+// grow-only buffers, so re-planning a batch no larger than a previous one
+// allocates nothing.  The serving loop lives in serve.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <chrono>
-#include <condition_variable>
 #include <cstdint>
-#include <cstdio>
 #include <cstring>
-#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <new>
-#include <thread>
-#include <tuple>
-#include <unordered_map>
 #include <vector>
 
-#include "../../include/crnt.h"
-#include "crnt_internal.h"
-#include "lte_params.h"
+#include "runtime.h"
 
 using namespace crnt;
+
+namespace crnt {
 
 namespace {
 
@@ -52,7 +45,7 @@ uint32_t gf_mul(uint32_t a, uint32_t b, uint32_t g) {
 // x^(32 s) mod g for s = 0..n-1
 std::vector<uint32_t> xpow_table(uint32_t g, int n) {
   std::vector<uint32_t> t(n);
-  uint32_t x32 = 1;  // x^32 mod g by 32 shifts of 1
+  uint32_t x32 = 1;
   for (int i = 0; i < 32; i++) {
     x32 <<= 1;
     if (x32 & 0x1000000u) x32 ^= g;
@@ -65,64 +58,32 @@ std::vector<uint32_t> xpow_table(uint32_t g, int n) {
   return t;
 }
 
-// Exact division q / W as (q * M) >> s for 0 <= q < qmax.
+// Exact division q / W as (q * M) >> s for 0 <= q < qmax, verified
+// exhaustively; cached per (W, qmax).
 bool find_divider(int W, int qmax, int* M, int* s) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, std::pair<int, int>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(W, qmax);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *M = it->second.first;
+    *s = it->second.second;
+    return true;
+  }
   for (int sh = 0; sh < 32; sh++) {
     const uint64_t m = ((1ull << sh) + W - 1) / W;
     if (m * (uint64_t)qmax >= (1ull << 32)) break;
     bool ok = true;
     for (int q = 0; q < qmax && ok; q++) ok = (int)((q * m) >> sh) == q / W;
     if (ok) {
+      cache[key] = std::make_pair((int)m, sh);
       *M = (int)m;
       *s = sh;
       return true;
     }
   }
   return false;
-}
-
-int64_t now_ns() {
-  return std::chrono::duration_cast<std::chrono::nanoseconds>(
-             std::chrono::steady_clock::now().time_since_epoch())
-      .count();
-}
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t n = 0;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= n) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e == cudaSuccess) n = bytes;
-    return e;
-  }
-};
-
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-int validate(const crnt_tb_params& t, lte::Seg* seg) {
-  if (t.A < 16 || t.A > 75376 || (t.A & 7)) return CRNT_EINVAL;
-  if (t.Qm != 2 && t.Qm != 4 && t.Qm != 6) return CRNT_EINVAL;
-  if (t.NL != 1 && t.NL != 2) return CRNT_EINVAL;
-  if (t.rv > 3 || t.max_iter < 1 || t.max_iter > 16) return CRNT_EINVAL;
-  if (t.G == 0 || t.G % (t.Qm * t.NL)) return CRNT_EINVAL;
-  if (!lte::segment((int)t.A + 24, seg) || seg->C > CRNT_MAX_CB) return CRNT_EINVAL;
-  // every CB must receive at least one LLR
-  if (lte::e_r((int)t.G, t.Qm, t.NL, seg->C, 0) < 1) return CRNT_EINVAL;
-  return CRNT_OK;
 }
 
 // Window count for a CB of size K: the caller's P clamped to [1, K/8] and
@@ -134,56 +95,326 @@ int clamp_p(int K, int P) {
   return std::max(P, 1);
 }
 
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Column masks of the circular-buffer rank formula (see rm_geom.cuh).
+void rm_masks(int ND, int F, uint32_t* maskB, uint32_t* mask2) {
+  const int X = ND + F;
+  uint32_t mb = 0, m2 = 0;
+  for (int c = 0; c < 32; c++) {
+    const int pc = lte::bitrev5(c);
+    if (pc < (X & 31)) mb |= 1u << c;
+    if (pc < ND - 1) m2 |= 1u << c;
+  }
+  *maskB = mb;
+  *mask2 = m2;
+}
+
+// Non-NULL positions before k0.  k0 = R (24 rv + 2) always starts a column:
+// column 2 or 26 of v0 (rv 0, 1) or column 9 or 21 of the v1/v2 part.
+int rank_of_k0(int K, int F, int rv, uint32_t maskB, uint32_t mask2) {
+  const int R = lte::rows(K), ND = 32 * R - (K + 4), X = ND + F, xa = X >> 5;
+  const int k0 = lte::k0(K, rv);
+  auto pre0 = [&](int c) { return xa * c + __builtin_popcount(maskB & ((1u << c) - 1u)); };
+  if (k0 < 32 * R) {
+    const int c = k0 / R;
+    return c * R - pre0(c);
+  }
+  const int c = (k0 - 32 * R) / (2 * R);
+  return (32 * R - X) + 2 * R * c - pre0(c) - __builtin_popcount(mask2 & ((1u << c) - 1u));
+}
+
+int harq_bind(crnt_ctx* ctx, const crnt_tb_params& t, int64_t* off) {
+  std::lock_guard<std::mutex> lk(ctx->harq_mu);
+  HarqPool& h = ctx->harq;
+  if (!h.arena) {
+    const uint64_t bytes = (uint64_t)ctx->cfg.harq_slots * kSoftSlot;
+    if (bytes > ctx->cfg.mem_budget) return CRNT_ENOMEM;
+    if (cudaMalloc(&h.arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h.arena = nullptr;
+      return CRNT_ENOMEM;
+    }
+    h.slots = ctx->cfg.harq_slots;
+    for (uint32_t i = 0; i < h.slots; i++) h.free_list.push_back(h.slots - 1 - i);
+  }
+  auto key = std::make_tuple(t.cell, t.ue, t.harq_pid);
+  auto it = h.keys.find(key);
+  uint32_t slot;
+  if (it != h.keys.end()) {
+    slot = it->second;
+  } else {
+    if (!t.new_data) return CRNT_ENOTFOUND;
+    if (h.free_list.empty()) return CRNT_EAGAIN;
+    slot = h.free_list.back();
+    h.free_list.pop_back();
+    h.keys[key] = slot;
+  }
+  *off = (int64_t)slot * kSoftSlot;
+  return CRNT_OK;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
 }  // namespace
 
-struct HarqPool {
-  int8_t* arena = nullptr;
-  uint32_t slots = 0;
-  std::map<std::tuple<uint32_t, uint32_t, uint32_t>, uint32_t> keys;
-  std::vector<uint32_t> free_list;
-};
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
-struct crnt_ctx {
-  int device = 0;
-  crnt_config cfg{};
-  int num_sms = 0;
-  uint32_t* xpowA = nullptr;
-  uint32_t* xpowB = nullptr;
-  HarqPool harq;
-  std::mutex mu;  // guards harq and the staging buffers
-  DevBuf stage_in, stage_out;
-  cudaStream_t stream = nullptr;
-  // serving
-  struct Serving* serving = nullptr;
-};
+int validate(const crnt_tb_params& t, lte::Seg* seg) {
+  if (t.A < 16 || t.A > 75376 || (t.A & 7)) return CRNT_EINVAL;
+  if (t.Qm != 2 && t.Qm != 4 && t.Qm != 6) return CRNT_EINVAL;
+  if (t.NL != 1 && t.NL != 2) return CRNT_EINVAL;
+  if (t.rv > 3 || t.max_iter < 1 || t.max_iter > 16) return CRNT_EINVAL;
+  if (t.G == 0 || t.G % (t.Qm * t.NL)) return CRNT_EINVAL;
+  if (!lte::segment((int)t.A + 24, seg) || seg->C > CRNT_MAX_CB) return CRNT_EINVAL;
+  if (lte::e_r((int)t.G, t.Qm, t.NL, seg->C, 0) < 1) return CRNT_EINVAL;
+  return CRNT_OK;
+}
 
-struct crnt_plan {
-  crnt_ctx* ctx = nullptr;
-  std::vector<crnt_tb_params> tbs;
-  std::vector<CbDesc> cbs;        // sorted (work-item order)
-  std::vector<int> cb_tb, cb_r;   // sorted index -> (tb, r)
-  std::vector<TbDesc> tdesc;
-  std::vector<WorkItem> items;
-  std::vector<lte::Seg> segs;
-  std::vector<uint16_t> p_used;
-  crnt_plan_info info{};
-  int smem = 0;
-  // device
-  void* d_desc = nullptr;   // cbs | tbs | items
-  void* d_scratch = nullptr;
-  size_t scratch_zero = 0;  // bytes to clear before each launch
-  DecParams prm{};
-  // host staging for results
-  uint8_t* h_res = nullptr;  // pinned: cb_iters | cb_ok | tb_ok
-  size_t res_bytes = 0;
-  ~crnt_plan() {
-    if (d_desc) cudaFree(d_desc);
-    if (d_scratch) cudaFree(d_scratch);
-    if (h_res) cudaFreeHost(h_res);
+int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
+               cudaStream_t stream) {
+  pl->ctx = ctx;
+  pl->tbs.assign(tbs, tbs + n);
+  pl->segs.assign(n, lte::Seg{});
+  pl->p_used.assign(n, 0);
+  pl->tdesc.assign(n, TbDesc{});
+  pl->cbs.clear();
+  pl->cb_tb.clear();
+  pl->cb_r.clear();
+  pl->items.clear();
+  std::vector<CbDesc> all;
+  std::vector<int> all_tb, all_r;
+  all.reserve(n * 4);
+  int64_t llr_off = 0, out_off = 0, dbg_off = 0;
+  uint64_t steps = 0, info_bits = 0;
+  for (uint32_t t = 0; t < n; t++) {
+    const crnt_tb_params& tp = tbs[t];
+    lte::Seg& s = pl->segs[t];
+    int rc = validate(tp, &s);
+    if (rc) return rc;
+    int64_t soft_base = -1;
+    if (tp.flags & CRNT_F_HARQ) {
+      rc = harq_bind(ctx, tp, &soft_base);
+      if (rc) return rc;
+    }
+    TbDesc& td = pl->tdesc[t];
+    td.out_off = out_off;
+    td.A = (int)tp.A;
+    td.C = s.C;
+    td.cb0 = (int)all.size();
+    pl->p_used[t] = (uint16_t)clamp_p(s.Kp, tp.P);
+    const int B = (int)tp.A + 24;
+    int pay_off = 0, eoff = 0, soff = 0;
+    for (int r = 0; r < s.C; r++) {
+      CbDesc d;
+      memset(&d, 0, sizeof d);
+      const int K = lte::cb_k(s, r);
+      const int F = r == 0 ? s.F : 0;
+      const int Pr = clamp_p(K, tp.P);
+      const int W = (K + Pr - 1) / Pr;
+      d.K = K;
+      d.F = F;
+      d.E = lte::e_r((int)tp.G, tp.Qm, tp.NL, s.C, r);
+      d.k0 = lte::k0(K, tp.rv);
+      d.W = W;
+      d.P = (K + W - 1) / W;
+      if (!find_divider(W, K + 4, &d.divM, &d.divS)) return CRNT_EINVAL;
+      const int ki = lte::index_of(K);
+      d.f1 = lte::kF1[ki];
+      d.f2 = lte::kF2[ki];
+      d.f2x2 = (int)((2ll * d.f2) % K);
+      d.f2sub = (int)((2ll * kSub * d.f2) % K);
+      d.f2jump = (int)((2ll * kSub * kSub * d.f2) % K);
+      d.R = lte::rows(K);
+      d.ND = 32 * d.R - (K + 4);
+      d.Nv = 3 * (K + 4) - 2 * F;
+      if (((d.ND + F) >> 5) + 1 > d.R) return CRNT_EINVAL;
+      rm_masks(d.ND, F, &d.maskB, &d.mask2);
+      d.rank0 = rank_of_k0(K, F, tp.rv, d.maskB, d.mask2);
+      d.tb = (int)t;
+      d.r = r;
+      d.llr_off = llr_off + eoff;
+      d.soft_off = soft_base >= 0 ? soft_base + soff : -1;
+      d.pay_bits = K - F - s.L;
+      d.pay_off = pay_off;
+      d.n_after = B - pay_off - d.pay_bits;
+      d.dbg_off = (int32_t)dbg_off;
+      d.crc_b = s.C > 1;
+      d.max_iter = tp.max_iter;
+      d.early_stop = tp.early_stop ? 1 : 0;
+      d.new_data = tp.new_data ? 1 : 0;
+      pay_off += d.pay_bits;
+      eoff += d.E;
+      soff += lte::ncb(K);
+      dbg_off += K + 4;
+      steps += K;
+      all.push_back(d);
+      all_tb.push_back((int)t);
+      all_r.push_back(r);
+    }
+    if (eoff != (int)tp.G || pay_off != B) return CRNT_EINVAL;
+    llr_off += tp.G;
+    out_off += tp.A / 8;
+    info_bits += tp.A;
   }
-};
+  // ---- work items: CBs of equal (K, P) share a CTA; longest work first
+  std::vector<int> order(all.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const CbDesc &a = all[x], &b = all[y];
+    const int ca = a.W * a.max_iter, cb = b.W * b.max_iter;
+    if (ca != cb) return ca > cb;
+    if (a.K != b.K) return a.K > b.K;
+    return a.P > b.P;
+  });
+  pl->cbs.reserve(all.size());
+  size_t i = 0;
+  int max_slot_bytes = 0;
+  while (i < order.size()) {
+    const CbDesc& h = all[order[i]];
+    const int slot = align16(dec_cb_smem(h.K, h.P, h.W));
+    if (slot > kSmemBudget) return CRNT_EINVAL;
+    const int gmax = std::max(1, std::min(kThreads / h.P, kSmemBudget / slot));
+    WorkItem wi;
+    wi.cb0 = (int)pl->cbs.size();
+    wi.n = 0;
+    wi.smem_per_cb = slot;
+    wi.pad0 = 0;
+    while (i < order.size() && wi.n < gmax) {
+      const CbDesc& c = all[order[i]];
+      if (c.K != h.K || c.P != h.P) break;
+      pl->cbs.push_back(c);
+      pl->cb_tb.push_back(all_tb[order[i]]);
+      pl->cb_r.push_back(all_r[order[i]]);
+      wi.n++;
+      i++;
+    }
+    max_slot_bytes = std::max(max_slot_bytes, wi.n * slot);
+    pl->items.push_back(wi);
+  }
+  pl->smem = 2048 + max_slot_bytes;
+  static std::mutex occ_mu;
+  static std::map<int, int> occ_cache;  // dynamic smem -> resident CTAs per SM
+  int per_sm;
+  {
+    std::lock_guard<std::mutex> lk(occ_mu);
+    auto it = occ_cache.find(pl->smem);
+    if (it == occ_cache.end()) it = occ_cache.emplace(pl->smem, decode_occupancy(pl->smem)).first;
+    per_sm = it->second;
+  }
+  if (per_sm < 1) return CRNT_EDEVICE;
+  const int grid = std::min<int>((int)pl->items.size(), per_sm * ctx->num_sms);
 
-// ------------------------------------------------------------------ API
+  crnt_plan_info& inf = pl->info;
+  inf.n_tb = n;
+  inf.n_cb = (uint32_t)pl->cbs.size();
+  inf.llr_bytes = (uint64_t)llr_off;
+  inf.out_bytes = (uint64_t)out_off;
+  inf.info_bits = info_bits;
+  inf.trellis_steps = steps;
+  inf.dbg_elems = (uint64_t)dbg_off;
+  inf.n_items = (uint32_t)pl->items.size();
+  inf.grid = (uint32_t)grid;
+
+  // ---- descriptors: pinned staging -> device (async on `stream`)
+  const size_t ncb = pl->cbs.size();
+  const size_t b_cbs = sizeof(CbDesc) * ncb, b_tbs = sizeof(TbDesc) * n,
+               b_items = sizeof(WorkItem) * pl->items.size();
+  const size_t off_tbs = al256(b_cbs), off_items = off_tbs + al256(b_tbs);
+  pl->desc_bytes = off_items + b_items;
+  const size_t s_state = 256, s_done = al256(4 * n), s_crc = al256(8 * n);
+  pl->scratch_zero = s_state + s_done + s_crc;
+  pl->res_bytes = 2 * ncb + n;
+  // the previous upload from h_desc must have completed before it is reused
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return CRNT_EDEVICE;
+  if (!pl->d_desc.ensure(pl->desc_bytes) || !pl->h_desc.ensure(pl->desc_bytes) ||
+      !pl->d_scratch.ensure(pl->scratch_zero + pl->res_bytes) || !pl->h_res.ensure(pl->res_bytes))
+    return CRNT_ENOMEM;
+  uint8_t* h = (uint8_t*)pl->h_desc.p;
+  memcpy(h, pl->cbs.data(), b_cbs);
+  memcpy(h + off_tbs, pl->tdesc.data(), b_tbs);
+  memcpy(h + off_items, pl->items.data(), b_items);
+  if (cudaMemcpyAsync(pl->d_desc.p, h, pl->desc_bytes, cudaMemcpyHostToDevice, stream) !=
+      cudaSuccess)
+    return CRNT_EDEVICE;
+  uint8_t* sc = (uint8_t*)pl->d_scratch.p;
+  DecParams& p = pl->prm;
+  memset(&p, 0, sizeof p);
+  p.cbs = (const CbDesc*)pl->d_desc.p;
+  p.tbs = (const TbDesc*)((uint8_t*)pl->d_desc.p + off_tbs);
+  p.items = (const WorkItem*)((uint8_t*)pl->d_desc.p + off_items);
+  p.n_items = (int)pl->items.size();
+  p.n_cbs = (int)ncb;
+  p.n_tbs = (int)n;
+  p.state = (DecState*)sc;
+  p.tb_done = (int32_t*)(sc + s_state);
+  p.tb_crc = (uint32_t*)(sc + s_state + s_done);
+  p.cb_iters = sc + pl->scratch_zero;
+  p.cb_ok = p.cb_iters + ncb;
+  p.tb_ok = p.cb_ok + ncb;
+  p.xpowA = ctx->xpowA;
+  p.xpowB = ctx->xpowB;
+  return CRNT_OK;
+}
+
+int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
+                int16_t* dbg_ext, uint8_t* dbg_hard) {
+  DecParams p = pl->prm;
+  p.llr = llr;
+  p.out = out;
+  p.soft = pl->ctx->harq.arena;
+  p.dbg_d = dbg_d;
+  p.dbg_ext = dbg_ext;
+  p.dbg_hard = dbg_hard;
+  if (cudaMemsetAsync(pl->d_scratch.p, 0, pl->scratch_zero, s) != cudaSuccess) return CRNT_EDEVICE;
+  if (launch_decode(p, (int)pl->info.grid, pl->smem, s) != cudaSuccess) return CRNT_EDEVICE;
+  return CRNT_OK;
+}
+
+int plan_fetch_results(crnt_plan* pl, cudaStream_t s) {
+  if (cudaMemcpyAsync(pl->h_res.p, pl->prm.cb_iters, pl->res_bytes, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return CRNT_EDEVICE;
+  return CRNT_OK;
+}
+
+void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res) {
+  const size_t ncb = pl->cbs.size();
+  const uint32_t n = pl->info.n_tb;
+  const uint8_t* h = (const uint8_t*)pl->h_res.p;
+  for (uint32_t t = 0; t < n; t++) {
+    crnt_tb_result& r = res[t];
+    memset(&r, 0, sizeof r);
+    const lte::Seg& sg = pl->segs[t];
+    r.status = CRNT_OK;
+    r.C = (uint8_t)sg.C;
+    r.K_plus = (uint16_t)sg.Kp;
+    r.K_minus = (uint16_t)sg.Km;
+    r.F = (uint16_t)sg.F;
+    r.P_used = pl->p_used[t];
+    r.tb_crc_ok = h[2 * ncb + t];
+  }
+  for (size_t i = 0; i < ncb; i++) {
+    crnt_tb_result& r = res[pl->cb_tb[i]];
+    r.cb_iters[pl->cb_r[i]] = h[i];
+    r.cb_crc_ok[pl->cb_r[i]] = h[ncb + i];
+  }
+}
+
+}  // namespace crnt
+
+// ------------------------------------------------------------------ C ABI
 extern "C" {
 
 int crnt_version(void) { return CRNT_VERSION; }
@@ -270,13 +501,15 @@ int crnt_create(crnt_ctx** out, const crnt_config* cfg) {
   return CRNT_OK;
 }
 
-static void serving_stop(crnt_ctx*) {}
-
 int crnt_destroy(crnt_ctx* ctx) {
   if (!ctx) return CRNT_EINVAL;
   cudaSetDevice(ctx->device);
   serving_stop(ctx);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  delete ctx->cached;
+  ctx->cached = nullptr;
+  ctx->stage_in.release();
+  ctx->stage_out.release();
   if (ctx->xpowA) cudaFree(ctx->xpowA);
   if (ctx->xpowB) cudaFree(ctx->xpowB);
   if (ctx->harq.arena) cudaFree(ctx->harq.arena);
@@ -285,39 +518,9 @@ int crnt_destroy(crnt_ctx* ctx) {
   return CRNT_OK;
 }
 
-static int harq_bind(crnt_ctx* ctx, const crnt_tb_params& t, int64_t* off) {
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  HarqPool& h = ctx->harq;
-  if (!h.arena) {
-    const uint64_t bytes = (uint64_t)ctx->cfg.harq_slots * kSoftSlot;
-    if (bytes > ctx->cfg.mem_budget) return CRNT_ENOMEM;
-    if (cudaMalloc(&h.arena, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      h.arena = nullptr;
-      return CRNT_ENOMEM;
-    }
-    h.slots = ctx->cfg.harq_slots;
-    for (uint32_t i = 0; i < h.slots; i++) h.free_list.push_back(h.slots - 1 - i);
-  }
-  auto key = std::make_tuple(t.cell, t.ue, t.harq_pid);
-  auto it = h.keys.find(key);
-  uint32_t slot;
-  if (it != h.keys.end()) {
-    slot = it->second;
-  } else {
-    if (!t.new_data) return CRNT_ENOTFOUND;
-    if (h.free_list.empty()) return CRNT_EAGAIN;
-    slot = h.free_list.back();
-    h.free_list.pop_back();
-    h.keys[key] = slot;
-  }
-  *off = (int64_t)slot * kSoftSlot;
-  return CRNT_OK;
-}
-
 int crnt_harq_release(crnt_ctx* ctx, uint32_t cell, uint32_t ue, uint32_t harq_pid) {
   if (!ctx) return CRNT_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::mutex> lk(ctx->harq_mu);
   auto it = ctx->harq.keys.find(std::make_tuple(cell, ue, harq_pid));
   if (it == ctx->harq.keys.end()) return CRNT_ENOTFOUND;
   ctx->harq.free_list.push_back(it->second);
@@ -330,206 +533,10 @@ int crnt_plan_create(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_
   *out = nullptr;
   std::unique_ptr<crnt_plan> pl(new (std::nothrow) crnt_plan);
   if (!pl) return CRNT_ENOMEM;
-  pl->ctx = ctx;
-  pl->tbs.assign(tbs, tbs + n);
-  pl->segs.resize(n);
-  pl->p_used.resize(n);
-  pl->tdesc.resize(n);
-  std::vector<CbDesc> all;  // TB order
-  std::vector<int> all_tb, all_r;
-  int64_t llr_off = 0, out_off = 0, dbg_off = 0;
-  uint64_t steps = 0, info_bits = 0;
-  std::map<std::pair<int, int>, std::pair<int, int>> divcache;
-  for (uint32_t t = 0; t < n; t++) {
-    const crnt_tb_params& tp = tbs[t];
-    lte::Seg& s = pl->segs[t];
-    int rc = validate(tp, &s);
-    if (rc) return rc;
-    int64_t soft_base = -1;
-    if (tp.flags & CRNT_F_HARQ) {
-      rc = harq_bind(ctx, tp, &soft_base);
-      if (rc) return rc;
-    }
-    TbDesc& td = pl->tdesc[t];
-    td.out_off = out_off;
-    td.A = (int)tp.A;
-    td.C = s.C;
-    td.cb0 = (int)all.size();
-    pl->p_used[t] = (uint16_t)clamp_p(s.Kp, tp.P);
-    const int B = (int)tp.A + 24;
-    int pay_off = 0, eoff = 0, soff = 0;
-    for (int r = 0; r < s.C; r++) {
-      CbDesc d;
-      memset(&d, 0, sizeof d);
-      const int K = lte::cb_k(s, r);
-      const int F = r == 0 ? s.F : 0;
-      const int Pr = clamp_p(K, tp.P);
-      const int W = (K + Pr - 1) / Pr;
-      d.K = K;
-      d.F = F;
-      d.E = lte::e_r((int)tp.G, tp.Qm, tp.NL, s.C, r);
-      d.k0 = lte::k0(K, tp.rv);
-      d.W = W;
-      d.P = (K + W - 1) / W;
-      auto key = std::make_pair(K, W);
-      auto dc = divcache.find(key);
-      if (dc == divcache.end()) {
-        int M, sh;
-        if (!find_divider(W, K + 4, &M, &sh)) return CRNT_EINVAL;
-        dc = divcache.emplace(key, std::make_pair(M, sh)).first;
-      }
-      d.divM = dc->second.first;
-      d.divS = dc->second.second;
-      const int ki = lte::index_of(K);
-      d.f1 = lte::kF1[ki];
-      d.f2 = lte::kF2[ki];
-      d.f2x2 = (int)((2ll * d.f2) % K);
-      d.f2sub = (int)((2ll * kSub * d.f2) % K);
-      d.f2jump = (int)((2ll * kSub * kSub * d.f2) % K);
-      d.R = lte::rows(K);
-      d.ND = 32 * d.R - (K + 4);
-      d.Nv = 3 * (K + 4) - 2 * F;
-      const int X = d.ND + F;
-      if ((X >> 5) + 1 > d.R) return CRNT_EINVAL;
-      uint32_t mb = 0, m2 = 0;
-      for (int c = 0; c < 32; c++) {
-        const int pc = lte::bitrev5(c);
-        if (pc < (X & 31)) mb |= 1u << c;
-        if (pc < d.ND - 1) m2 |= 1u << c;
-      }
-      d.maskB = mb;
-      d.mask2 = m2;
-      int rank0 = 0;
-      for (int w = 0; w < d.k0; w++) rank0 += lte::w_non_null(K, F, w) ? 1 : 0;
-      d.rank0 = rank0;
-      d.tb = (int)t;
-      d.r = r;
-      d.llr_off = llr_off + eoff;
-      d.soft_off = soft_base >= 0 ? soft_base + soff : -1;
-      d.pay_bits = K - F - s.L;
-      d.pay_off = pay_off;
-      d.n_after = B - pay_off - d.pay_bits;
-      d.dbg_off = (int32_t)dbg_off;
-      d.crc_b = s.C > 1;
-      d.max_iter = tp.max_iter;
-      d.early_stop = tp.early_stop ? 1 : 0;
-      d.new_data = tp.new_data ? 1 : 0;
-      pay_off += d.pay_bits;
-      eoff += d.E;
-      soff += lte::ncb(K);
-      dbg_off += K + 4;
-      steps += K;
-      all.push_back(d);
-      all_tb.push_back((int)t);
-      all_r.push_back(r);
-    }
-    if (eoff != (int)tp.G || pay_off != B) return CRNT_EINVAL;
-    llr_off += tp.G;
-    out_off += tp.A / 8;
-    info_bits += tp.A;
-  }
-  // ---- work items: group CBs of equal (K, P), longest work first
-  std::vector<int> order(all.size());
-  for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const CbDesc &a = all[x], &b = all[y];
-    const int ca = a.W * a.max_iter, cb = b.W * b.max_iter;
-    if (ca != cb) return ca > cb;
-    if (a.K != b.K) return a.K > b.K;
-    return a.P > b.P;
-  });
-  pl->cbs.reserve(all.size());
-  std::vector<std::pair<int, WorkItem>> items;  // (cost, item)
-  size_t i = 0;
-  int max_slot_bytes = 0;
-  while (i < order.size()) {
-    const CbDesc& h = all[order[i]];
-    const int slot = align16(dec_cb_smem(h.K, h.P, h.W));
-    if (slot > kSmemBudget) return CRNT_EINVAL;
-    const int gmax = std::max(1, std::min(kThreads / h.P, kSmemBudget / slot));
-    WorkItem wi;
-    wi.cb0 = (int)pl->cbs.size();
-    wi.n = 0;
-    wi.smem_per_cb = slot;
-    wi.pad0 = 0;
-    while (i < order.size() && wi.n < gmax) {
-      const CbDesc& c = all[order[i]];
-      if (c.K != h.K || c.P != h.P) break;
-      pl->cbs.push_back(c);
-      pl->cb_tb.push_back(all_tb[order[i]]);
-      pl->cb_r.push_back(all_r[order[i]]);
-      wi.n++;
-      i++;
-    }
-    max_slot_bytes = std::max(max_slot_bytes, wi.n * slot);
-    items.push_back(std::make_pair(h.W * h.max_iter, wi));
-  }
-  for (auto& it : items) pl->items.push_back(it.second);
-  pl->smem = 2048 + max_slot_bytes;
-
   cudaSetDevice(ctx->device);
-  const int per_sm = decode_occupancy(pl->smem);
-  if (per_sm < 1) return CRNT_EDEVICE;
-  const int grid = std::min<int>((int)pl->items.size(), per_sm * ctx->num_sms);
-
-  crnt_plan_info& inf = pl->info;
-  inf.n_tb = n;
-  inf.n_cb = (uint32_t)pl->cbs.size();
-  inf.llr_bytes = (uint64_t)llr_off;
-  inf.out_bytes = (uint64_t)out_off;
-  inf.info_bits = info_bits;
-  inf.trellis_steps = steps;
-  inf.dbg_elems = (uint64_t)dbg_off;
-  inf.n_items = (uint32_t)pl->items.size();
-  inf.grid = (uint32_t)grid;
-
-  // ---- device buffers
-  const size_t ncb = pl->cbs.size();
-  const size_t b_cbs = sizeof(CbDesc) * ncb, b_tbs = sizeof(TbDesc) * n,
-               b_items = sizeof(WorkItem) * pl->items.size();
-  const size_t off_tbs = (b_cbs + 255) & ~size_t(255);
-  const size_t off_items = off_tbs + ((b_tbs + 255) & ~size_t(255));
-  const size_t desc_bytes = off_items + b_items;
-  if (cudaMalloc(&pl->d_desc, desc_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return CRNT_ENOMEM;
-  }
-  std::vector<uint8_t> host(desc_bytes, 0);
-  memcpy(host.data(), pl->cbs.data(), b_cbs);
-  memcpy(host.data() + off_tbs, pl->tdesc.data(), b_tbs);
-  memcpy(host.data() + off_items, pl->items.data(), b_items);
-  if (cudaMemcpy(pl->d_desc, host.data(), desc_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
-    return CRNT_EDEVICE;
-  // scratch: state | tb_done | tb_crc (zeroed each launch) | cb_iters | cb_ok | tb_ok
-  const size_t s_state = 256, s_done = ((4 * n + 255) & ~size_t(255)),
-               s_crc = ((8 * n + 255) & ~size_t(255));
-  pl->scratch_zero = s_state + s_done + s_crc;
-  pl->res_bytes = 2 * ncb + n;
-  if (cudaMalloc(&pl->d_scratch, pl->scratch_zero + pl->res_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return CRNT_ENOMEM;
-  }
-  if (cudaMallocHost((void**)&pl->h_res, pl->res_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return CRNT_ENOMEM;
-  }
-  uint8_t* sc = (uint8_t*)pl->d_scratch;
-  DecParams& p = pl->prm;
-  p.cbs = (const CbDesc*)pl->d_desc;
-  p.tbs = (const TbDesc*)((uint8_t*)pl->d_desc + off_tbs);
-  p.items = (const WorkItem*)((uint8_t*)pl->d_desc + off_items);
-  p.n_items = (int)pl->items.size();
-  p.n_cbs = (int)ncb;
-  p.n_tbs = (int)n;
-  p.soft = ctx->harq.arena;
-  p.state = (DecState*)sc;
-  p.tb_done = (int32_t*)(sc + s_state);
-  p.tb_crc = (uint32_t*)(sc + s_state + s_done);
-  p.cb_iters = sc + pl->scratch_zero;
-  p.cb_ok = p.cb_iters + ncb;
-  p.tb_ok = p.cb_ok + ncb;
-  p.xpowA = ctx->xpowA;
-  p.xpowB = ctx->xpowB;
+  int rc = plan_build(ctx, tbs, n, pl.get(), ctx->stream);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = CRNT_EDEVICE;
+  if (rc) return rc;
   *out = pl.release();
   return CRNT_OK;
 }
@@ -544,17 +551,7 @@ int crnt_plan_launch_debug(crnt_plan* plan, const int8_t* llr, uint8_t* out, voi
                            int8_t* dbg_d, int16_t* dbg_ext, uint8_t* dbg_hard) {
   if (!plan || !llr || !out) return CRNT_EINVAL;
   if ((dbg_ext == nullptr) != (dbg_hard == nullptr)) return CRNT_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
-  DecParams p = plan->prm;
-  p.llr = llr;
-  p.out = out;
-  p.soft = plan->ctx->harq.arena;
-  p.dbg_d = dbg_d;
-  p.dbg_ext = dbg_ext;
-  p.dbg_hard = dbg_hard;
-  if (cudaMemsetAsync(plan->d_scratch, 0, plan->scratch_zero, s) != cudaSuccess) return CRNT_EDEVICE;
-  if (launch_decode(p, (int)plan->info.grid, plan->smem, s) != cudaSuccess) return CRNT_EDEVICE;
-  return CRNT_OK;
+  return plan_launch(plan, llr, out, (cudaStream_t)stream, dbg_d, dbg_ext, dbg_hard);
 }
 
 int crnt_plan_launch(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream) {
@@ -564,29 +561,9 @@ int crnt_plan_launch(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* str
 int crnt_plan_results(crnt_plan* plan, crnt_tb_result* res, void* stream) {
   if (!plan || !res) return CRNT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(plan->h_res, plan->prm.cb_iters, plan->res_bytes, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  if (plan_fetch_results(plan, s) != CRNT_OK || cudaStreamSynchronize(s) != cudaSuccess)
     return CRNT_EDEVICE;
-  const size_t ncb = plan->cbs.size();
-  const uint32_t n = plan->info.n_tb;
-  for (uint32_t t = 0; t < n; t++) {
-    crnt_tb_result& r = res[t];
-    memset(&r, 0, sizeof r);
-    const lte::Seg& sg = plan->segs[t];
-    r.status = CRNT_OK;
-    r.C = (uint8_t)sg.C;
-    r.K_plus = (uint16_t)sg.Kp;
-    r.K_minus = (uint16_t)sg.Km;
-    r.F = (uint16_t)sg.F;
-    r.P_used = plan->p_used[t];
-    r.tb_crc_ok = plan->h_res[2 * ncb + t];
-  }
-  for (size_t i = 0; i < ncb; i++) {
-    crnt_tb_result& r = res[plan->cb_tb[i]];
-    r.cb_iters[plan->cb_r[i]] = plan->h_res[i];
-    r.cb_crc_ok[plan->cb_r[i]] = plan->h_res[ncb + i];
-  }
+  plan_fill_results(plan, res);
   return CRNT_OK;
 }
 
@@ -601,34 +578,38 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
                       uint8_t* out, crnt_tb_result* res) {
   if (!ctx || !tbs || !llr || !out || !res || n == 0) return CRNT_EINVAL;
   cudaSetDevice(ctx->device);
-  crnt_plan* plan = nullptr;
-  int rc = crnt_plan_create(ctx, tbs, n, &plan);
-  if (rc) return rc;
   const bool llr_dev = is_device_ptr(llr), out_dev = is_device_ptr(out);
-  std::unique_lock<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::mutex> lk(ctx->stage_mu);
+  cudaStream_t s = ctx->stream;
+  if (!ctx->cached) {
+    ctx->cached = new (std::nothrow) crnt_plan;
+    if (!ctx->cached) return CRNT_ENOMEM;
+  }
+  crnt_plan* plan = ctx->cached;
+  int rc = plan_build(ctx, tbs, n, plan, s);
+  if (rc) return rc;
   const int8_t* d_llr = llr;
   uint8_t* d_out = out;
-  cudaStream_t s = ctx->stream;
-  rc = CRNT_OK;
   if (!llr_dev) {
-    if (ctx->stage_in.ensure(plan->info.llr_bytes) != cudaSuccess ||
-        cudaMemcpyAsync(ctx->stage_in.p, llr, plan->info.llr_bytes, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
-      rc = CRNT_EDEVICE;
+    if (!ctx->stage_in.ensure(plan->info.llr_bytes)) return CRNT_ENOMEM;
+    if (cudaMemcpyAsync(ctx->stage_in.p, llr, plan->info.llr_bytes, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return CRNT_EDEVICE;
     d_llr = (const int8_t*)ctx->stage_in.p;
   }
-  if (!rc && !out_dev) {
-    if (ctx->stage_out.ensure(plan->info.out_bytes) != cudaSuccess) rc = CRNT_EDEVICE;
+  if (!out_dev) {
+    if (!ctx->stage_out.ensure(plan->info.out_bytes)) return CRNT_ENOMEM;
     d_out = (uint8_t*)ctx->stage_out.p;
   }
-  if (!rc) rc = crnt_plan_launch(plan, d_llr, d_out, s);
-  if (!rc && !out_dev &&
+  rc = plan_launch(plan, d_llr, d_out, s, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  if (!out_dev &&
       cudaMemcpyAsync(out, d_out, plan->info.out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    rc = CRNT_EDEVICE;
-  if (!rc) rc = crnt_plan_results(plan, res, s);
-  lk.unlock();
-  crnt_plan_destroy(plan);
-  return rc;
+    return CRNT_EDEVICE;
+  if (plan_fetch_results(plan, s) != CRNT_OK || cudaStreamSynchronize(s) != cudaSuccess)
+    return CRNT_EDEVICE;
+  plan_fill_results(plan, res);
+  return CRNT_OK;
 }
 
 int crnt_decode_tb(crnt_ctx* ctx, const int8_t* llr, const crnt_tb_params* tb, uint8_t* out,
@@ -660,10 +641,9 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
       c.E = lte::e_r((int)tbs[t].G, tbs[t].Qm, tbs[t].NL, s.C, r);
       c.R = lte::rows(K);
       c.ND = 32 * c.R - (K + 4);
-      const int k0 = lte::k0(K, tbs[t].rv);
-      int rank0 = 0;
-      for (int w = 0; w < k0; w++) rank0 += lte::w_non_null(K, c.F, w) ? 1 : 0;
-      c.rank0 = rank0;
+      uint32_t mb, m2;
+      rm_masks(c.ND, c.F, &mb, &m2);
+      c.rank0 = rank_of_k0(K, c.F, tbs[t].rv, mb, m2);
       const int ki = lte::index_of(K);
       c.f1 = lte::kF1[ki];
       c.f2 = lte::kF2[ki];
@@ -678,15 +658,14 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
     }
     ioff += tbs[t].A / 8;
   }
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::mutex> lk(ctx->stage_mu);
   cudaStream_t st = ctx->stream;
   const size_t b_cbs = sizeof(EncCb) * cbs.size(), b_off = 8 * n, b_A = 4 * n;
-  const size_t o_off = (b_cbs + 255) & ~size_t(255), o_A = o_off + ((b_off + 255) & ~size_t(255));
-  const size_t o_bits = o_A + ((b_A + 255) & ~size_t(255));
+  const size_t o_off = al256(b_cbs), o_A = o_off + al256(b_off), o_bits = o_A + al256(b_A);
   const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(e_out);
   const size_t total = o_bits + (bits_dev ? 0 : (size_t)ioff);
-  if (ctx->stage_in.ensure(total) != cudaSuccess) return CRNT_ENOMEM;
-  if (!out_dev && ctx->stage_out.ensure((size_t)eoff) != cudaSuccess) return CRNT_ENOMEM;
+  if (!ctx->stage_in.ensure(total)) return CRNT_ENOMEM;
+  if (!out_dev && !ctx->stage_out.ensure((size_t)eoff)) return CRNT_ENOMEM;
   std::vector<uint8_t> host(o_bits, 0);
   memcpy(host.data(), cbs.data(), b_cbs);
   memcpy(host.data() + o_off, in_off.data(), b_off);
@@ -716,10 +695,5 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
 int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb, uint8_t* e_out) {
   return crnt_encode_batch(ctx, tb, 1, bits, e_out);
 }
-
-int crnt_submit(crnt_ctx*, const crnt_tb_params*, const int8_t* const*, uint32_t, uint64_t*) {
-  return CRNT_EINVAL;
-}
-int crnt_poll(crnt_ctx*, crnt_tb_result*, const uint8_t**, uint32_t, uint32_t) { return CRNT_EINVAL; }
 
 }  // extern "C"

@@ -1,0 +1,109 @@
+// runtime.h -- host runtime objects shared by the C ABI (crnt_api.cu) and
+// the serving loop (serve.cu): the context, reusable batch plans, and the
+// HARQ soft-buffer pool.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/crnt.h"
+#include "crnt_internal.h"
+#include "lte_params.h"
+
+namespace crnt {
+
+// Grow-only device or pinned host buffer.
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+  bool host = false;
+  Buf() = default;
+  explicit Buf(bool pinned_host) : host(pinned_host) {}
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) host ? cudaFreeHost(p) : cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  bool ensure(size_t bytes) {
+    if (bytes <= n) return true;
+    release();
+    const size_t want = bytes + bytes / 4 + 4096;
+    cudaError_t e = host ? cudaMallocHost(&p, want) : cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    n = want;
+    return true;
+  }
+};
+
+struct HarqPool {
+  int8_t* arena = nullptr;
+  uint32_t slots = 0;
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t>, uint32_t> keys;
+  std::vector<uint32_t> free_list;
+};
+
+struct Serving;
+
+}  // namespace crnt
+
+struct crnt_ctx {
+  int device = 0;
+  crnt_config cfg{};
+  int num_sms = 0;
+  uint32_t* xpowA = nullptr;
+  uint32_t* xpowB = nullptr;
+  crnt::HarqPool harq;
+  std::mutex harq_mu;     // guards harq
+  std::mutex stage_mu;    // guards the staging buffers and the cached plan
+  crnt::Buf stage_in, stage_out;
+  crnt_plan* cached = nullptr;  // plan reused by crnt_decode_batch
+  cudaStream_t stream = nullptr;
+  crnt::Serving* serving = nullptr;
+  std::mutex serving_mu;
+};
+
+// A planned batch.  Its buffers are grow-only, so re-planning a plan object
+// (plan_build) allocates nothing once it has seen a batch as large.
+struct crnt_plan {
+  crnt_ctx* ctx = nullptr;
+  std::vector<crnt_tb_params> tbs;
+  std::vector<crnt::CbDesc> cbs;     // sorted (work-item order)
+  std::vector<int> cb_tb, cb_r;      // sorted index -> (tb, r)
+  std::vector<crnt::TbDesc> tdesc;
+  std::vector<crnt::WorkItem> items;
+  std::vector<crnt::lte::Seg> segs;
+  std::vector<uint16_t> p_used;
+  crnt_plan_info info{};
+  int smem = 0;
+  crnt::Buf d_desc, d_scratch;       // device: descriptors | per-launch scratch
+  crnt::Buf h_desc{true}, h_res{true};  // pinned: descriptor staging | results
+  size_t desc_bytes = 0, scratch_zero = 0, res_bytes = 0;
+  crnt::DecParams prm{};
+};
+
+namespace crnt {
+// Host planning + descriptor upload on `stream` (asynchronous when the plan's
+// buffers are already large enough; allocates otherwise).
+int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
+               cudaStream_t stream);
+int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
+                int16_t* dbg_ext, uint8_t* dbg_hard);
+// Enqueue the D2H copy of the per-CB / per-TB results into h_res.
+int plan_fetch_results(crnt_plan* pl, cudaStream_t s);
+// Fill res[n] from h_res (after the stream has passed plan_fetch_results).
+void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res);
+int validate(const crnt_tb_params& t, lte::Seg* seg);
+void serving_stop(crnt_ctx* ctx);
+int64_t now_ns();
+}  // namespace crnt
