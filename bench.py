@@ -392,14 +392,14 @@ def subframe_latency(crnt, ctx, dev):
             "what": "device time of one 20 MHz subframe decode (13 CBs, early stop)"}
 
 
-def serving_leg(crnt, dev, seed, cells_list=(2, 4, 8, 12, 16, 24, 32), seconds=1.5):
+def serving_leg(crnt, dev, seed, cells_list=(4, 8, 12, 16, 20, 24, 28, 32), seconds=1.5):
     """Serving loop under cell load: every cell submits one subframe (8 UEs,
     TB mix of the TTI workload) per 1 ms period with a random phase and
     +-200 us jitter; ~10 % of TBs are HARQ retransmissions (rv 2) combined in
     the device-resident soft buffers.  Latency = completion - arrival time.
     Returns per cell count p50/p99 latency, deadline-miss fraction and the
     largest cell count whose p99 stays within 1 ms."""
-    import torch  # noqa: F401
+    import ctypes
     ues = 8
     maxc = max(cells_list)
     shapes = synth.tti_batch(seed + 99, n_tb=maxc * ues)
@@ -412,11 +412,24 @@ def serving_leg(crnt, dev, seed, cells_list=(2, 4, 8, 12, 16, 24, 32), seconds=1
         ctx.encode_batch(tbs, pay, coded)
         llr_all = channel(shapes, coded, seed + 5)
         offs = np.cumsum([0] + [s["G"] for s in shapes])
-        llrs = [np.ascontiguousarray(llr_all[offs[i]:offs[i + 1]]) for i in range(len(shapes))]
+        base = llr_all.ctypes.data
+        # per cell: prebuilt parameter / pointer / ticket arrays
+        cell_par, cell_ptr, cell_tk, cell_A = [], [], [], []
+        for c in range(maxc):
+            par = crnt.params_array([dict(tbs[c * ues + u], cell=c, ue=u, flags=crnt.F_HARQ)
+                                     for u in range(ues)])
+            ptr = (ctypes.c_void_p * ues)(*[base + int(offs[c * ues + u]) for u in range(ues)])
+            cell_par.append(par)
+            cell_ptr.append(ptr)
+            cell_tk.append((ctypes.c_uint64 * ues)())
+            cell_A.append([tbs[c * ues + u]["A"] for u in range(ues)])
+        res = (crnt.TbResult * 4096)()
+        bits = (ctypes.c_void_p * 4096)()
         rng_u = synth.uniform01(seed, 77, 1 << 20)
+        ku = 0
         for cells in cells_list:
-            phase = [float(rng_u[c]) * 1e6 for c in range(cells)]  # ns within the period
-            lat, subframes, nbits, k = [], 0, 0, 0
+            phase = [float(rng_u[c]) * 1e6 for c in range(cells)]
+            lat, subframes, refused, nbits = [], 0, 0, 0
             pending = {}
             t0 = time.monotonic_ns() + 2_000_000
             t_end = t0 + int(seconds * 1e9)
@@ -426,29 +439,30 @@ def serving_leg(crnt, dev, seed, cells_list=(2, 4, 8, 12, 16, 24, 32), seconds=1
                 now = time.monotonic_ns()
                 for c in range(cells):
                     if nxt[c] <= now and nxt[c] < t_end:
-                        arr = nxt[c]
-                        batch, bl = [], []
+                        par = cell_par[c]
+                        pid = sf[c] % 8
                         for u in range(ues):
-                            i = c * ues + u
-                            pid = sf[c] % 8
-                            retx = sf[c] >= 8 and float(rng_u[(k * 7919) % len(rng_u)]) < 0.1
-                            k += 1
-                            t = dict(tbs[i], cell=c, ue=u, harq_pid=pid, flags=crnt.F_HARQ,
-                                     new_data=0 if retx else 1, rv=2 if retx else 0)
-                            batch.append(t)
-                            bl.append(llrs[i])
-                        tk = ctx.submit(batch, bl)
-                        if tk is not None:
-                            for t, x in zip(tk, batch):
-                                pending[t] = (arr, x["A"])
+                            retx = sf[c] >= 8 and float(rng_u[ku & 0xFFFFF]) < 0.1
+                            ku += 1
+                            par[u].harq_pid = pid
+                            par[u].new_data = 0 if retx else 1
+                            par[u].rv = 2 if retx else 0
+                        rc = ctx.submit_raw(par, cell_ptr[c], ues, cell_tk[c])
+                        if rc == 0:
+                            arr = nxt[c]
+                            for u in range(ues):
+                                pending[cell_tk[c][u]] = (arr, cell_A[c][u])
+                        else:
+                            refused += 1
                         subframes += 1
                         sf[c] += 1
-                        jit = (float(rng_u[(k * 104729) % len(rng_u)]) - 0.5) * 400_000
+                        jit = (float(rng_u[ku & 0xFFFFF]) - 0.5) * 400_000
+                        ku += 1
                         nxt[c] = t0 + sf[c] * 1_000_000 + int(phase[c] + jit)
-                        k += 1
-                for d, _ in ctx.poll(1024, 0):
-                    arr, A = pending.pop(d["ticket"])
-                    lat.append((d["t_done_ns"] - arr) / 1e3)
+                n = ctx.poll_raw(res, bits, 4096, 0)
+                for i in range(n):
+                    arr, A = pending.pop(res[i].ticket)
+                    lat.append((res[i].t_done_ns - arr) / 1e3)
                     nbits += A
                 if now >= t_end and not pending:
                     break
@@ -460,13 +474,17 @@ def serving_leg(crnt, dev, seed, cells_list=(2, 4, 8, 12, 16, 24, 32), seconds=1
             p50 = lat[len(lat) // 2]
             p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
             rows.append({"cells": cells, "tbs": len(lat), "subframes": subframes,
-                         "p50_us": round(p50, 1), "p99_us": round(p99, 1),
+                         "refused_subframes": refused, "p50_us": round(p50, 1),
+                         "p99_us": round(p99, 1),
                          "deadline_miss": sum(1 for x in lat if x > 1000.0) / len(lat),
                          "gbit_s": nbits / seconds / 1e9})
-    ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0]
+            if p99 > 20000:
+                break  # far past saturation: larger loads only grow the queue
+    ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["refused_subframes"] == 0]
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
             "what": "continuous batching via crnt_submit/crnt_poll; 8 UEs per cell, "
-                    "1 subframe per cell per ms, +-200 us jitter, 10% HARQ retransmissions"}
+                    "1 subframe per cell per ms, +-200 us jitter, 10% HARQ retransmissions, "
+                    "latency from scheduled arrival to completion"}
 
 
 def cpu_baseline(shapes, seed):

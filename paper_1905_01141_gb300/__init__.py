@@ -248,6 +248,16 @@ class Context:
             out.append((d, data))
         return out
 
+    def submit_raw(self, params, ptrs, n, tickets):
+        """crnt_submit on prebuilt ctypes arrays (TbParams[n], c_void_p[n],
+        c_uint64[n]); returns the status code."""
+        return load().crnt_submit(self.h, params, ptrs, n, tickets)
+
+    def poll_raw(self, res, bits, max_n, timeout_us=0):
+        """crnt_poll into prebuilt arrays (TbResult[max_n], c_void_p[max_n]);
+        returns the number of results (or a negative code)."""
+        return load().crnt_poll(self.h, res, bits, max_n, timeout_us)
+
     def harq_release(self, cell, ue, pid):
         return load().crnt_harq_release(self.h, cell, ue, pid)
 

@@ -183,7 +183,7 @@ int validate(const crnt_tb_params& t, lte::Seg* seg) {
 }
 
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
-               cudaStream_t stream) {
+               cudaStream_t stream, const int64_t* llr_base) {
   pl->ctx = ctx;
   pl->tbs.assign(tbs, tbs + n);
   pl->segs.assign(n, lte::Seg{});
@@ -244,7 +244,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
       d.rank0 = rank_of_k0(K, F, tp.rv, d.maskB, d.mask2);
       d.tb = (int)t;
       d.r = r;
-      d.llr_off = llr_off + eoff;
+      d.llr_off = (llr_base ? llr_base[t] : llr_off) + eoff;
       d.soft_off = soft_base >= 0 ? soft_base + soff : -1;
       d.pay_bits = K - F - s.L;
       d.pay_off = pay_off;

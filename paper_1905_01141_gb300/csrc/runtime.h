@@ -94,9 +94,11 @@ struct crnt_plan {
 
 namespace crnt {
 // Host planning + descriptor upload on `stream` (asynchronous when the plan's
-// buffers are already large enough; allocates otherwise).
+// buffers are already large enough; allocates otherwise).  llr_base (may be
+// null): byte offset of each TB's LLRs from the LLR pointer given at launch;
+// null means the TBs' LLRs are concatenated in order.
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
-               cudaStream_t stream);
+               cudaStream_t stream, const int64_t* llr_base = nullptr);
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
                 int16_t* dbg_ext, uint8_t* dbg_hard);
 // Enqueue the D2H copy of the per-CB / per-TB results into h_res.

@@ -7,12 +7,15 @@
 // still running on other slots, so work admitted later overlaps on the
 // device with work admitted earlier.  Finished batches are harvested by
 // polling their events; results wait in a done queue for crnt_poll.
-// Admission is by in-flight TB count and by LLR bytes (the device memory a
-// request pins while queued or running); beyond either, crnt_submit returns
-// CRNT_EAGAIN.  Waits are bounded: the worker sleeps on a condition variable
+// crnt_submit copies each TB's LLRs straight into a device-resident ring
+// (one DMA per TB, completed before it returns), so the worker only plans and
+// launches.  Admission is by in-flight TB count and by space in that ring
+// (the device memory a request holds while queued or running); beyond
+// either, crnt_submit returns CRNT_EAGAIN.  Waits are bounded: the worker sleeps on a condition variable
 // with a timeout and crnt_poll honours its timeout.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -34,8 +37,49 @@ constexpr uint32_t kMaxBatchTbs = 1024;
 struct Req {
   uint64_t ticket;
   crnt_tb_params tb;
-  std::vector<int8_t> llr;
+  int64_t llr_off;   // byte offset of its LLRs in the device ring
+  uint64_t alloc;    // allocation sequence number (ring release order)
   int64_t t_submit;
+};
+
+// Ring of device memory holding the LLRs of queued and running requests,
+// released in allocation order.  Each allocation is contiguous.
+struct Ring {
+  size_t cap = 0, head = 0, tail = 0;
+  struct A {
+    size_t end;
+    bool done;
+  };
+  std::deque<A> q;
+  uint64_t first_seq = 0;  // sequence number of q.front()
+  bool alloc(size_t n, size_t* off, uint64_t* seq) {
+    if (q.empty()) head = tail = 0;
+    if (head >= tail) {  // free space: [head, cap) and [0, tail)
+      if (cap - head >= n) {
+        *off = head;
+      } else if (tail > n) {
+        *off = 0;
+      } else {
+        return false;
+      }
+    } else if (tail - head > n) {  // free space: [head, tail)
+      *off = head;
+    } else {
+      return false;
+    }
+    head = *off + n;
+    *seq = first_seq + q.size();
+    q.push_back(A{head, false});
+    return true;
+  }
+  void release(uint64_t seq) {
+    q[seq - first_seq].done = true;
+    while (!q.empty() && q.front().done) {
+      tail = q.front().end;
+      q.pop_front();
+      first_seq++;
+    }
+  }
 };
 
 struct Done {
@@ -47,8 +91,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   crnt_plan plan;
-  Buf d_llr, d_out;
-  Buf h_llr{true}, h_out{true};
+  Buf d_out;
+  Buf h_out{true};
   std::vector<Req> reqs;
   std::vector<crnt_tb_result> tmp;
   bool busy = false;
@@ -66,8 +110,12 @@ struct Serving {
   std::vector<Done> polled;  // results handed out by the last crnt_poll
   std::vector<std::unique_ptr<Slot>> slots;
   uint64_t next_ticket = 1;
-  uint64_t inflight_tbs = 0, inflight_bytes = 0;  // queued + running
+  uint64_t inflight_tbs = 0;  // queued + running
   int device_error = 0;
+  int8_t* arena = nullptr;    // device LLR ring
+  Ring ring;
+  cudaStream_t cstream = nullptr;  // submit-side copies
+  std::mutex copy_mu;
 
   void run();
   bool launch(Slot* s, std::vector<Req>&& batch);
@@ -78,25 +126,17 @@ bool Serving::launch(Slot* s, std::vector<Req>&& batch) {
   s->reqs = std::move(batch);
   const uint32_t n = (uint32_t)s->reqs.size();
   std::vector<crnt_tb_params> tbs(n);
-  size_t bytes = 0;
+  std::vector<int64_t> base(n);
   for (uint32_t i = 0; i < n; i++) {
     tbs[i] = s->reqs[i].tb;
-    bytes += s->reqs[i].llr.size();
+    base[i] = s->reqs[i].llr_off;
   }
-  if (!s->h_llr.ensure(bytes) || !s->d_llr.ensure(bytes)) return false;
-  size_t off = 0;
-  for (auto& r : s->reqs) {
-    memcpy((uint8_t*)s->h_llr.p + off, r.llr.data(), r.llr.size());
-    off += r.llr.size();
-  }
-  if (plan_build(ctx, tbs.data(), n, &s->plan, s->stream) != CRNT_OK) return false;
+  if (plan_build(ctx, tbs.data(), n, &s->plan, s->stream, base.data()) != CRNT_OK) return false;
   const size_t out_bytes = s->plan.info.out_bytes;
   if (!s->d_out.ensure(out_bytes) || !s->h_out.ensure(out_bytes)) return false;
   s->t_start = now_ns();
-  if (cudaMemcpyAsync(s->d_llr.p, s->h_llr.p, bytes, cudaMemcpyHostToDevice, s->stream) !=
-          cudaSuccess ||
-      plan_launch(&s->plan, (const int8_t*)s->d_llr.p, (uint8_t*)s->d_out.p, s->stream, nullptr,
-                  nullptr, nullptr) != CRNT_OK ||
+  if (plan_launch(&s->plan, arena, (uint8_t*)s->d_out.p, s->stream, nullptr, nullptr, nullptr) !=
+          CRNT_OK ||
       cudaMemcpyAsync(s->h_out.p, s->d_out.p, out_bytes, cudaMemcpyDeviceToHost, s->stream) !=
           cudaSuccess ||
       plan_fetch_results(&s->plan, s->stream) != CRNT_OK ||
@@ -114,7 +154,7 @@ void Serving::harvest(Slot* s, bool failed) {
     s->tmp.resize(n);
     plan_fill_results(&s->plan, s->tmp.data());
   }
-  size_t off = 0, bytes = 0;
+  size_t off = 0;
   for (uint32_t i = 0; i < n; i++) {
     Done& d = out[i];
     const Req& r = s->reqs[i];
@@ -127,7 +167,6 @@ void Serving::harvest(Slot* s, bool failed) {
       d.bits.assign(src, src + r.tb.A / 8);
     }
     off += r.tb.A / 8;
-    bytes += r.llr.size();
     d.res.ticket = r.ticket;
     d.res.t_submit_ns = (uint64_t)r.t_submit;
     d.res.t_start_ns = (uint64_t)s->t_start;
@@ -136,8 +175,8 @@ void Serving::harvest(Slot* s, bool failed) {
   {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& d : out) done.push_back(std::move(d));
+    for (auto& r : s->reqs) ring.release(r.alloc);
     inflight_tbs -= n;
-    inflight_bytes -= bytes;
   }
   s->reqs.clear();
   s->busy = false;
@@ -198,6 +237,13 @@ static Serving* serving_get(crnt_ctx* ctx) {
   if (!sv) return nullptr;
   sv->ctx = ctx;
   cudaSetDevice(ctx->device);
+  sv->ring.cap = (size_t)std::min<uint64_t>(ctx->cfg.mem_budget / 4, 1ull << 30);
+  if (cudaMalloc(&sv->arena, sv->ring.cap) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sv->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    if (sv->arena) cudaFree(sv->arena);
+    return nullptr;
+  }
   for (int i = 0; i < kSlots; i++) {
     std::unique_ptr<Slot> s(new (std::nothrow) Slot);
     if (!s || cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -229,6 +275,8 @@ void serving_stop(crnt_ctx* ctx) {
     if (s->ev) cudaEventDestroy(s->ev);
     if (s->stream) cudaStreamDestroy(s->stream);
   }
+  if (sv->cstream) cudaStreamDestroy(sv->cstream);
+  if (sv->arena) cudaFree(sv->arena);
   delete sv;
 }
 
@@ -241,7 +289,6 @@ extern "C" {
 int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* llrs, uint32_t n,
                 uint64_t* tickets_out) {
   if (!ctx || !tbs || !llrs || !tickets_out || n == 0) return CRNT_EINVAL;
-  uint64_t bytes = 0;
   for (uint32_t i = 0; i < n; i++) {
     lte::Seg s;
     int rc = validate(tbs[i], &s);
@@ -252,28 +299,48 @@ int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* l
       if (!ctx->harq.keys.count(std::make_tuple(tbs[i].cell, tbs[i].ue, tbs[i].harq_pid)))
         return CRNT_ENOTFOUND;
     }
-    bytes += tbs[i].G;
   }
   Serving* sv = serving_get(ctx);
   if (!sv) return CRNT_EDEVICE;
   const int64_t t = now_ns();
+  std::vector<Req> reqs(n);
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->device_error) return sv->device_error;
-    if (sv->inflight_tbs + n > ctx->cfg.max_inflight ||
-        sv->inflight_bytes + bytes > ctx->cfg.mem_budget / 4)
-      return CRNT_EAGAIN;
+    if (sv->inflight_tbs + n > ctx->cfg.max_inflight) return CRNT_EAGAIN;
     for (uint32_t i = 0; i < n; i++) {
-      Req r;
-      r.ticket = sv->next_ticket++;
-      r.tb = tbs[i];
-      r.llr.assign(llrs[i], llrs[i] + tbs[i].G);
-      r.t_submit = t;
-      tickets_out[i] = r.ticket;
-      sv->pending.push_back(std::move(r));
+      size_t off;
+      if (!sv->ring.alloc(tbs[i].G, &off, &reqs[i].alloc)) {
+        for (uint32_t j = 0; j < i; j++) sv->ring.release(reqs[j].alloc);
+        return CRNT_EAGAIN;
+      }
+      reqs[i].llr_off = (int64_t)off;
     }
     sv->inflight_tbs += n;
-    sv->inflight_bytes += bytes;
+  }
+  {
+    // the LLRs reach the device before the requests become visible
+    std::lock_guard<std::mutex> lk(sv->copy_mu);
+    bool ok = true;
+    for (uint32_t i = 0; i < n && ok; i++)
+      ok = cudaMemcpyAsync(sv->arena + reqs[i].llr_off, llrs[i], tbs[i].G, cudaMemcpyHostToDevice,
+                           sv->cstream) == cudaSuccess;
+    if (!ok || cudaStreamSynchronize(sv->cstream) != cudaSuccess) {
+      std::lock_guard<std::mutex> lk2(sv->mu);
+      for (uint32_t i = 0; i < n; i++) sv->ring.release(reqs[i].alloc);
+      sv->inflight_tbs -= n;
+      return CRNT_EDEVICE;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (uint32_t i = 0; i < n; i++) {
+      reqs[i].ticket = sv->next_ticket++;
+      reqs[i].tb = tbs[i];
+      reqs[i].t_submit = t;
+      tickets_out[i] = reqs[i].ticket;
+      sv->pending.push_back(std::move(reqs[i]));
+    }
   }
   sv->cv_work.notify_one();
   return CRNT_OK;
