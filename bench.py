@@ -410,9 +410,11 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 12, 16, 20, 24, 28, 32), seco
                               for t, s in enumerate(shapes)])
         coded = np.zeros(sum(s["G"] for s in shapes), dtype=np.uint8)
         ctx.encode_batch(tbs, pay, coded)
-        llr_all = channel(shapes, coded, seed + 5)
+        import torch
+        # the LLR source lives in pinned host memory, as fronthaul buffers would
+        llr_pin = torch.from_numpy(channel(shapes, coded, seed + 5)).pin_memory()
         offs = np.cumsum([0] + [s["G"] for s in shapes])
-        base = llr_all.ctypes.data
+        base = llr_pin.data_ptr()
         # per cell: prebuilt parameter / pointer / ticket arrays
         cell_par, cell_ptr, cell_tk, cell_A = [], [], [], []
         for c in range(maxc):
