@@ -20,7 +20,8 @@ on):
   * tti_batch      : cells x UEs TBs, A uniform over multiples of 8 in
                      [16, 75376], Qm in {2,4,6} and G drawn so that the code
                      rate stays <= 0.93 inside 100 PRB, SNR within +-3 dB of
-                     a capacity-based threshold for the (Qm, rate) pair.
+                     a threshold for the (Qm, rate) pair: the capacity SNR plus
+                     a gap measured for this decoder (about 10 % BLER there).
 """
 import math
 
@@ -181,6 +182,9 @@ def tti_batch(seed, n_tb=320, amin=16, amax=75376):
         G = Qm * int(math.ceil((a + 24) / (r * Qm)))
         G = min(G, 14400 * Qm)
         r_eff = (a + 24) / G
-        snr_th = 10.0 * math.log10(2.0 ** (r_eff * Qm) - 1.0) + 1.0
+        # threshold: capacity SNR plus an empirical gap of this decoder (max
+        # 6 iterations) that grows with the modulation order and at high rate
+        gap = 2.0 + 0.35 * (Qm - 2) + 10.0 * max(0.0, r_eff - 0.75)
+        snr_th = 10.0 * math.log10(2.0 ** (r_eff * Qm) - 1.0) + gap
         out.append(dict(A=a, G=G, Qm=Qm, snr_db=snr_th + 6.0 * float(snr_u[t]) - 3.0))
     return out
