@@ -123,7 +123,7 @@ __host__ __device__ inline int dec_cb_smem(int K, int P, int W) {
          + align16(4 * nwords)          // hard bits
          + 4 * P * 16                   // alpha/beta seeds of both decoders
          + P * nck * 16                 // alpha checkpoints
-         + 16;                          // per-CB flags
+         + 32;                          // per-CB flags
 }
 
 }  // namespace crnt

@@ -79,36 +79,41 @@ __device__ __forceinline__ int acs2(int x0, int c0, int x1, int c1, int S, int T
 }
 
 // Normalisation by state 0 with int16 saturation, in offset form:
-// o[s] = sat16(m[s] - m[0]) + OFF.  The subtraction runs on the FMA pipe;
-// one OR over the results detects the (rare) case where a value left
-// [0, 65535], and only then are the clamps applied -- the result equals the
-// saturating definition in every case.
+// o[s] = sat16(m[s] - m[0]) + OFF.  CHK: the exact path -- one OR over the
+// results detects a value outside [0, 65535] and only then are the clamps
+// applied.  !CHK: the caller has proved (window_fast) that no value can
+// leave the range, so the clamps could never act and are omitted.
+template <bool CHK>
 __device__ __forceinline__ void normalise(const int m[8], int o[8]) {
   const int base = OFF - m[0];
   o[0] = OFF;
 #pragma unroll
   for (int s = 1; s < 8; s++) o[s] = m[s] + base;
-  const unsigned any = (unsigned)(o[1] | o[2] | o[3] | o[4] | o[5] | o[6] | o[7]);
-  if (any > 0xFFFFu) {
+  if (CHK) {
+    const unsigned any = (unsigned)(o[1] | o[2] | o[3] | o[4] | o[5] | o[6] | o[7]);
+    if (any > 0xFFFFu) {
 #pragma unroll
-    for (int s = 1; s < 8; s++) o[s] = min(max(o[s], 0), 65535);
+      for (int s = 1; s < 8; s++) o[s] = min(max(o[s], 0), 65535);
+    }
   }
 }
 
+template <bool CHK>
 __device__ __forceinline__ void alpha_step(const int a[8], int o[8], int S, int T, int Lp) {
   int m[8];
 #pragma unroll
   for (int n = 0; n < 8; n++)
     m[n] = acs2(a[pred(n, 0)], pcode(n, 0), a[pred(n, 1)], pcode(n, 1), S, T, Lp);
-  normalise(m, o);
+  normalise<CHK>(m, o);
 }
 
+template <bool CHK>
 __device__ __forceinline__ void beta_step(int b[8], int S, int T, int Lp) {
   int m[8];
 #pragma unroll
   for (int s = 0; s < 8; s++)
     m[s] = acs2(b[nxt(s, 0)], gcode(s, 0), b[nxt(s, 1)], gcode(s, 1), S, T, Lp);
-  normalise(m, b);
+  normalise<CHK>(m, b);
 }
 
 // Terminating tail step: each state leaves on the branch that feeds a = 0.
@@ -119,37 +124,61 @@ __device__ __forceinline__ void beta_tail_step(int b[8], int Ls, int Lp) {
     const int u = ((s >> 1) ^ s) & 1;  // r2 ^ r3
     m[s] = b[nxt(s, u)] + gval(gcode(s, u), Ls, Ls + Lp, Lp);
   }
-  normalise(m, b);
+  normalise<true>(m, b);
 }
 
 __device__ __forceinline__ int max8(const int v[8]) {
   return max(__vimax3_s32(__vimax3_s32(v[0], v[1], v[2]), __vimax3_s32(v[3], v[4], v[5]), v[6]),
              v[7]);
 }
+__device__ __forceinline__ int min8(const int v[8]) {
+  return min(__vimin3_s32(__vimin3_s32(v[0], v[1], v[2]), __vimin3_s32(v[3], v[4], v[5]), v[6]),
+             v[7]);
+}
 
-// Lambda and the extrinsic of one step: returns Le, writes Lambda.  The
-// sums alpha + beta (+ Lp when the branch parity is 0) are formed on the FMA
-// pipe; the two maxima use 3-input max.  The S common to the u = 0 branches
-// is added back at the end.
+// Lambda and the extrinsic of one step: returns Le, writes Lambda.  Four
+// add-max chains over the transitions grouped by (u, parity); Lp joins the
+// parity-0 groups and S (common to u = 0) is added back at the end.
+template <bool CHK>
 __device__ __forceinline__ int app_step(const int a[8], const int b[8], int S, int Lp, int* lam_out) {
-  int v0[8], v1[8];
+  int acc[4];
+  bool first[4] = {true, true, true, true};
 #pragma unroll
   for (int s = 0; s < 8; s++)
 #pragma unroll
     for (int u = 0; u < 2; u++) {
-      const int t = a[s] + b[nxt(s, u)] + ((gcode(s, u) & 1) ? Lp : 0);
-      if (u == 0) v0[s] = t;
-      else v1[s] = t;
+      const int c = gcode(s, u);
+      const int n = nxt(s, u);
+      if (first[c]) {
+        acc[c] = a[s] + b[n];
+        first[c] = false;
+      } else {
+        acc[c] = __viaddmax_s32(a[s], b[n], acc[c]);
+      }
     }
-  const int d = max8(v0) - max8(v1);
+  const int d = __viaddmax_s32(acc[3], Lp, acc[2]) - __viaddmax_s32(acc[1], Lp, acc[0]);
   int lam = S + d;
   int le = d;
-  if (((unsigned)(lam + 32768) | (unsigned)(le + 32768)) > 0xFFFFu) {
+  if (CHK && (((unsigned)(lam + 32768) | (unsigned)(le + 32768)) > 0xFFFFu)) {
     lam = min(max(lam, -32768), 32767);
     le = min(max(lam - S, -32768), 32767);
   }
   *lam_out = lam;
   return le;
+}
+
+// Largest |metric difference| a window pass can reach, from the spreads of
+// its start metrics and the branch-metric range g >= |S| + |Lp| of every
+// step.  Between two states the metrics of the exact (unsaturated) max-plus
+// recursion differ by at most spread_start + k g after k steps and by at most
+// 3 g after 3 or more steps (every state pair is joined by exactly one
+// 3-step path of the 8-state trellis).  Lambda and Le are bounded by
+// spread_alpha + spread_beta + 2 g.  If that stays within int16, no
+// saturation can occur in the pass and the clamp-free path is exact.
+__device__ __forceinline__ bool window_fast(const int a[8], const int b[8], int g) {
+  const int sa = max8(a) - min8(a), sb = max8(b) - min8(b);
+  const int Sa = max(sa + 2 * g, 3 * g), Sb = max(sb + 2 * g, 3 * g);
+  return Sa + Sb + 2 * g <= 32767;
 }
 
 __device__ __forceinline__ int scale_ext(int le) { return (le * 3) >> 2; }
@@ -192,7 +221,7 @@ struct CbSlot {
   uint32_t* hard;
   uint4* seed;   // [4][P]: alpha dec0, alpha dec1, beta dec0, beta dec1
   uint4* ck;     // [P][nck]
-  int* flags;    // [0] done, [1] iterations, [2] crc accumulator, [3] spare
+  int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|
 };
 __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
   CbSlot s;
@@ -290,6 +319,8 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restr
     sl.flags[1] = 0;
     sl.flags[2] = 0;
     sl.flags[3] = 0;
+    sl.flags[4] = 0;
+    sl.flags[5] = 0;
   }
 }
 
@@ -332,20 +363,21 @@ __device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, 
 // Backward processing of one sub-window [j0, j0 + slen) of a window:
 // recompute forward metrics from the checkpoint into registers, then walk
 // back computing Lambda / Le and the backward metrics.  FULL: slen == kSub
-// (no per-step guards).
-template <int DEC, bool FULL>
+// (no per-step guards).  mx tracks the largest |extrinsic| written.
+template <int DEC, bool FULL, bool CHK>
 __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
-                                                int dq, int b[8]) {
+                                                int dq, int b[8], int& mx) {
   int A[kSub][8];
-  int Sv[kSub], Lv[kSub], Tv[kSub], Qv[kSub];
+  int Sv[kSub], Lv[kSub], Qv[kSub];
   unpack8(ck, A[0]);
 #pragma unroll
   for (int jj = 0; jj < kSub; jj++) {
     if (FULL || jj < slen) {
       Qv[jj] = q;
-      load_step<DEC>(w, j0 + jj, q, dq, Sv[jj], Lv[jj], Tv[jj]);
+      int t;
+      load_step<DEC>(w, j0 + jj, q, dq, Sv[jj], Lv[jj], t);
       if (jj + 1 < kSub && (FULL || jj + 1 < slen))
-        alpha_step(A[jj], A[jj + 1], Sv[jj], Sv[jj] + Lv[jj], Lv[jj]);
+        alpha_step<CHK>(A[jj], A[jj + 1], Sv[jj], Sv[jj] + Lv[jj], Lv[jj]);
     }
   }
 #pragma unroll
@@ -353,20 +385,99 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
     if (FULL || jj < slen) {
       const int S = Sv[jj], Lp = Lv[jj];
       int lam;
-      const int le = app_step(A[jj], b, S, Lp, &lam);
-      w.ext[Tv[jj]] = (int16_t)scale_ext(le);
+      const int le = app_step<CHK>(A[jj], b, S, Lp, &lam);
+      const int v = scale_ext(le);
+      mx = __vimax3_s32(mx, v, -v);
+      w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : tr_w(w, Qv[jj])] = (int16_t)v;
       if (DEC == 1 && lam < 0) {
         const int qq = Qv[jj] + w.pad;
         atomicOr(&w.hard[qq >> 5], 1u << (31 - (qq & 31)));
       }
-      beta_step(b, S, S + Lp, Lp);
+      beta_step<CHK>(b, S, S + Lp, Lp);
     }
   }
 }
 
+// Forward and backward recursions of one window (after the seeds are read).
+template <int DEC, bool CHK>
+__device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restrict__ dp,
+                                            uint4* ck, uint4* seedA, uint4* seedB, int a[8],
+                                            int b[8], int& mx) {
+  const int K = w.K, P = w.P, p = w.p, lo = w.lo, len = w.len;
+  const int f1 = dp->f1, f2 = dp->f2;
+
+  // ---- forward pass with a checkpoint every kSub steps
+  int q = 0, dq = 0;
+  if (DEC == 1) {
+    q = qpp_at(lo, f1, f2, K);
+    dq = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
+  }
+  int j0 = 0;
+  for (; j0 + kSub <= len; j0 += kSub) {
+    ck[j0 / kSub] = pack8(a);
+#pragma unroll
+    for (int jj = 0; jj < kSub; jj += 2) {
+      int S, Lp, t, o[8];
+      load_step<DEC>(w, j0 + jj, q, dq, S, Lp, t);
+      alpha_step<CHK>(a, o, S, S + Lp, Lp);
+      load_step<DEC>(w, j0 + jj + 1, q, dq, S, Lp, t);
+      alpha_step<CHK>(o, a, S, S + Lp, Lp);
+    }
+  }
+  if (j0 < len) {
+    ck[j0 / kSub] = pack8(a);
+    for (int j = j0; j < len; j++) {
+      int S, Lp, t, o[8];
+      load_step<DEC>(w, j, q, dq, S, Lp, t);
+      alpha_step<CHK>(a, o, S, S + Lp, Lp);
+#pragma unroll
+      for (int s = 0; s < 8; s++) a[s] = o[s];
+    }
+  }
+  if (p + 1 < P) seedA[p + 1] = pack8(a);
+
+  // ---- backward pass, one sub-window at a time from the end.  QPP state
+  // at the start of the last sub-window, walked backwards by kSub steps:
+  // PI(x - kSub) = PI(x) - J(x - kSub) with J(x) = kSub f1 + f2 (2 kSub x +
+  // kSub^2), J(x - kSub) = J(x) - 2 kSub^2 f2, delta(x - kSub) = delta(x) -
+  // 2 kSub f2.
+  const int nsub = (len + kSub - 1) / kSub;
+  int pis = 0, dls = 0, jmp = 0;
+  if (DEC == 1) {
+    const int is = lo + kSub * (nsub - 1);
+    pis = qpp_at(is, f1, f2, K);
+    dls = (f1 + (f2 * ((2 * is + 1) % K)) % K) % K;
+    int t = (2 * kSub * is - kSub * kSub) % K;
+    if (t < 0) t += K;
+    jmp = ((kSub * f1) % K + (f2 * t) % K) % K;
+  }
+  int sw = nsub - 1;
+  const int last_len = len - kSub * sw;
+  if (last_len < kSub) {
+    sub_window_back<DEC, false, CHK>(w, ck[sw], kSub * sw, last_len, pis, dls, b, mx);
+    if (DEC == 1) {
+      pis = modsub(pis, jmp, K);
+      dls = modsub(dls, dp->f2sub, K);
+      jmp = modsub(jmp, dp->f2jump, K);
+    }
+    sw--;
+  }
+  for (; sw >= 0; sw--) {
+    sub_window_back<DEC, true, CHK>(w, ck[sw], kSub * sw, kSub, pis, dls, b, mx);
+    if (DEC == 1) {
+      pis = modsub(pis, jmp, K);
+      dls = modsub(dls, dp->f2sub, K);
+      jmp = modsub(jmp, dp->f2jump, K);
+    }
+  }
+  if (p > 0) seedB[p - 1] = pack8(b);
+}
+
 // One SISO pass of window p of one CB.  DEC = 0: natural order (encoder 1),
 // DEC = 1: QPP order (encoder 2).  All threads of the CTA call it (run =
-// false for idle threads) because it contains barriers.
+// false for idle threads) because it contains barriers.  flags[4 + d] holds
+// the largest |extrinsic| written by the last pass of decoder d, which
+// bounds |La| for the pass that reads it.
 template <int DEC>
 __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t* base, int p,
                                           bool run, bool first) {
@@ -377,6 +488,7 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
   uint4* ck = sl.ck + p * ((W + kSub - 1) / kSub);
 
   int a[8], b[8];
+  int m_in = 0;
   if (run) {
     if (p == 0) {
       a[0] = OFF;
@@ -398,6 +510,8 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     } else {
       unpack8(seedB[p], b);
     }
+    m_in = sl.flags[5 - DEC];
+    if (p == 0) sl.flags[4 + DEC] = 0;  // written by this pass after the barrier
     if (DEC == 1) {
       const int nwords = (K + 31) / 32;
       for (int w = p; w < nwords; w += P) sl.hard[w] = 0u;
@@ -420,79 +534,17 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     w.lo = p * W;
     w.len = min(W, K - w.lo);
     w.pad = ((K + 31) / 32) * 32 - K;
-    const int lo = w.lo, len = w.len;
-    const int f1 = dp->f1, f2 = dp->f2;
-
-    // ---- forward pass with a checkpoint every kSub steps
-    int q = 0, dq = 0;
-    if (DEC == 1) {
-      q = qpp_at(lo, f1, f2, K);
-      dq = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
-    }
-    int j0 = 0;
-    for (; j0 + kSub <= len; j0 += kSub) {
-      ck[j0 / kSub] = pack8(a);
-#pragma unroll
-      for (int jj = 0; jj < kSub; jj += 2) {
-        int S, Lp, t, o[8];
-        load_step<DEC>(w, j0 + jj, q, dq, S, Lp, t);
-        alpha_step(a, o, S, S + Lp, Lp);
-        load_step<DEC>(w, j0 + jj + 1, q, dq, S, Lp, t);
-        alpha_step(o, a, S, S + Lp, Lp);
-      }
-    }
-    if (j0 < len) {
-      ck[j0 / kSub] = pack8(a);
-      for (int j = j0; j < len; j++) {
-        int S, Lp, t, o[8];
-        load_step<DEC>(w, j, q, dq, S, Lp, t);
-        alpha_step(a, o, S, S + Lp, Lp);
-#pragma unroll
-        for (int s = 0; s < 8; s++) a[s] = o[s];
-      }
-    }
-    if (p + 1 < P) seedA[p + 1] = pack8(a);
-
-    // ---- backward pass, one sub-window at a time from the end
     if (p == P - 1) {
       const int8_t* t = sl.tail + (DEC ? 6 : 0);
 #pragma unroll
       for (int j = 2; j >= 0; j--) beta_tail_step(b, t[2 * j], t[2 * j + 1]);
     }
-    const int nsub = (len + kSub - 1) / kSub;
-    // QPP state at the start of the last sub-window, walked backwards by
-    // kSub steps: PI(x - kSub) = PI(x) - J(x - kSub) with
-    // J(x) = kSub f1 + f2 (2 kSub x + kSub^2), J(x - kSub) = J(x) - 2 kSub^2 f2,
-    // delta(x - kSub) = delta(x) - 2 kSub f2.
-    int pis = 0, dls = 0, jmp = 0;
-    if (DEC == 1) {
-      const int is = lo + kSub * (nsub - 1);
-      pis = qpp_at(is, f1, f2, K);
-      dls = (f1 + (f2 * ((2 * is + 1) % K)) % K) % K;
-      int t = (2 * kSub * is - kSub * kSub) % K;
-      if (t < 0) t += K;
-      jmp = ((kSub * f1) % K + (f2 * t) % K) % K;
-    }
-    int sw = nsub - 1;
-    const int last_len = len - kSub * sw;
-    if (last_len < kSub) {
-      sub_window_back<DEC, false>(w, ck[sw], kSub * sw, last_len, pis, dls, b);
-      if (DEC == 1) {
-        pis = modsub(pis, jmp, K);
-        dls = modsub(dls, dp->f2sub, K);
-        jmp = modsub(jmp, dp->f2jump, K);
-      }
-      sw--;
-    }
-    for (; sw >= 0; sw--) {
-      sub_window_back<DEC, true>(w, ck[sw], kSub * sw, kSub, pis, dls, b);
-      if (DEC == 1) {
-        pis = modsub(pis, jmp, K);
-        dls = modsub(dls, dp->f2sub, K);
-        jmp = modsub(jmp, dp->f2jump, K);
-      }
-    }
-    if (p > 0) seedB[p - 1] = pack8(b);
+    int mx = 0;
+    if (window_fast(a, b, 254 + m_in))
+      window_pass<DEC, false>(w, dp, ck, seedA, seedB, a, b, mx);
+    else
+      window_pass<DEC, true>(w, dp, ck, seedA, seedB, a, b, mx);
+    atomicMax(&sl.flags[4 + DEC], mx);
   }
   __syncthreads();
 }
@@ -568,8 +620,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
     }
     __syncthreads();
     uint8_t* mybase = slots + (mine ? mycb : 0) * wi.smem_per_cb;
-    const CbDesc d = *dp;
-    const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
+    int* const fl = make_slot(mybase, dp->K, dp->P, dp->W).flags;
     if (prm.dbg_d) {
       for (int g = 0; g < G; g++) {
         const CbDesc& dg = cbs[g];
@@ -591,26 +642,30 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
       }
     }
 
-    // ---- phase 1: turbo iterations
+    // ---- phase 1: turbo iterations (only the flags pointer stays live
+    // across the SISO passes; descriptor fields are re-read when needed)
     const int maxit = s_maxit;
     for (int it = 1; it <= maxit; it++) {
-      const bool run = mine && sl.flags[0] == 0 && it <= d.max_iter;
+      const int my_max = mine ? (int)dp->max_iter : 0;
+      const bool run = mine && fl[0] == 0 && it <= my_max;
       const bool first = (it == 1);
       siso_pass<0>(dp, mybase, p, run, first);
       siso_pass<1>(dp, mybase, p, run, first);
-      const bool check = run && (d.early_stop || it == d.max_iter);
+      const bool check = run && (dp->early_stop || it == my_max);
       if (check) {
+        const CbDesc& d = *dp;
+        const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
         const uint32_t r = crc_share(d, sl, p, d.crc_b ? tabB : tabA, d.crc_b ? GB : GA,
                                      d.crc_b ? prm.xpowB : prm.xpowA, 0);
-        if (r) atomicXor((unsigned*)&sl.flags[2], r);
+        if (r) atomicXor((unsigned*)&fl[2], r);
       }
       __syncthreads();
       if (run && p == 0) {
-        const bool ok = check && sl.flags[2] == 0;
-        sl.flags[2] = 0;
-        if (ok || it == d.max_iter) {
-          sl.flags[0] = 1;
-          sl.flags[1] = ok ? it : d.max_iter + 1;
+        const bool ok = check && fl[2] == 0;
+        fl[2] = 0;
+        if (ok || it == my_max) {
+          fl[0] = 1;
+          fl[1] = ok ? it : my_max + 1;
           atomicSub(&s_remaining, 1);
         }
       }
@@ -619,6 +674,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
     }
 
     // ---- phase 2: results, payload bytes, TB CRC, debug copies
+    const CbDesc d = *dp;
+    const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
     const int sorted_idx = wi.cb0 + (mine ? mycb : 0);
     const bool cb_ok = mine && sl.flags[1] <= d.max_iter;
     if (mine) {
