@@ -170,6 +170,27 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
 int crnt_decode_tb(crnt_ctx* ctx, const int8_t* llr, const crnt_tb_params* tb, uint8_t* out,
                    crnt_tb_result* res);
 
+/* ---- allocation-free batched decode ------------------------------------ */
+/* No counterpart in the paper.  The same fused decode for callers that must
+ * not allocate device memory -- for example code that runs inside another
+ * framework's memory pool or between phases where allocation is forbidden --
+ * and so cannot create a context (crnt_create allocates).  Descriptors, the
+ * work queue, CRC tables and per-launch scratch live in one fixed file-scope
+ * device array of about 134 KiB held by every GPU that loads the library; no
+ * cudaMalloc, cudaFree, pinned or library allocation happens in this call.
+ * llr (device, concatenated G LLRs) in, out (device, concatenated A/8 bytes)
+ * out, res[n] (host) results; runs on `stream` (NULL = default) on the
+ * current device and returns after that stream has finished the decode.
+ * Limits: n <= 64 TBs and at most 832 code blocks in total, else
+ * CRNT_ENOMEM ("exceeds the static workspace"); no HARQ combining
+ * (CRNT_F_HARQ gives CRNT_EINVAL).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and uploads the CRC tables
+ * with synchronous copies, so make that first call before any stream
+ * capture.  Every call shares the array: calls whose GPU work overlaps (two
+ * streams, or two host threads) race on it, so do not overlap them. */
+int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, const int8_t* llr,
+                             uint8_t* out, crnt_tb_result* res, void* stream);
+
 /* ---- downlink encode (Sec. IV-B "Encoding function", Fig. 3) ------------ */
 /* Encode n TBs: CRC24A, segmentation with CRC24B and filler, turbo encode
  * (2 RSC + QPP, trellis termination), sub-block interleave and bit

@@ -98,6 +98,7 @@ SIGNATURES = {
     "crnt_submit": (ctypes.c_int, [_P, _P, _P, _U32, _P]),
     "crnt_poll": (ctypes.c_int, [_P, _P, _P, _U32, _U32]),
     "crnt_harq_release": (ctypes.c_int, [_P, _U32, _U32, _U32]),
+    "crnt_decode_batch_static": (ctypes.c_int, [_P, _U32, _P, _P, _P, _P]),
 }
 
 
@@ -160,6 +161,16 @@ def params_array(tbs):
     for i, t in enumerate(tbs):
         arr[i] = t if isinstance(t, TbParams) else make_params(**t)
     return arr
+
+
+def decode_batch_static(tbs, llr, out, stream=0):
+    """crnt_decode_batch_static: the allocation-free decode (device buffers,
+    no context); returns the results."""
+    arr = params_array(tbs)
+    res = (TbResult * len(arr))()
+    _check(load().crnt_decode_batch_static(arr, len(arr), _ptr(llr), _ptr(out), res,
+                                           stream or None), "crnt_decode_batch_static")
+    return [r.as_dict() for r in res]
 
 
 def tb_layout(tb):
