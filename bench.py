@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
+    ap.add_argument("--sweep", choices=["bler"], help="quality sweep instead of the bench line")
+    ap.add_argument("--bler-cbs", type=int, default=0,
+                    help="CBs per (K, P, Eb/N0) point (0: 1e6 for K=40, 1e5 for K=6144 "
+                         "with P>=16, 2e4 for P=4 and 1e4 for P=1)")
     return ap.parse_args()
 
 
@@ -231,6 +235,7 @@ def run_ours(args):
 
     import paper_1905_01141_gb300 as crnt
     from paper_1905_01141_gb300 import build as crnt_build
+    from paper_1905_01141_gb300 import replicas
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -241,8 +246,9 @@ def run_ours(args):
     crnt_build.build()
     ctx = crnt.Context(local)
 
-    # ---- workload: this rank's TTI (weak scaling: cells partitioned by rank)
-    shapes = tti_shapes(args.seed + 7919 * rank, args.n_tb)
+    # ---- workload: this rank's TTI (weak scaling: each rank serves its own
+    # cells -- replicas, no collective on the data path)
+    shapes = tti_shapes(replicas.rank_seed(args.seed, rank), args.n_tb)
     tbs = params(shapes)
     pay = np.concatenate([np.packbits(synth.bits(args.seed + rank, 5000 + t, s["A"]))
                           for t, s in enumerate(shapes)])
@@ -292,11 +298,7 @@ def run_ours(args):
     dev_s = sum(step_ms) / 1e3
     bits_rank = info["info_bits"] * args.steps
     if ws > 1:
-        t = torch.tensor([dev_s, float(bits_rank)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        dev_s, bits_all = float(tmax[0]), float(t[1])
+        dev_s, bits_all = replicas.reduce_time_bits(dev_s, bits_rank, device=dev)
     else:
         bits_all = float(bits_rank)
     value = bits_all / dev_s / 1e9
@@ -500,8 +502,95 @@ def cpu_baseline(shapes, seed):
                       "thread pool of %d, %.1f s" % (n, cores, secs)}
 
 
+def bler_sweep(args):
+    """Stress and quality sweep: BLER and mean iterations per (K, P, Eb/N0)
+    for single-CB TBs (A = K - 24, rate 1/3 without puncturing, BPSK), max 8
+    iterations with CRC stop, P in {1, 4, 16, 64}.  Payloads and noise are
+    drawn on the GPU (torch), encoded by the library's encoder and decoded by
+    its decoder; a small seeded subsample per point is also decoded by the
+    CPU oracle from oracle-encoded inputs and compared CB by CB."""
+    import torch
+
+    import paper_1905_01141_gb300 as crnt
+    from paper_1905_01141_gb300 import build as crnt_build
+    crnt_build.build()
+    import oracle
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed)
+    pts = []
+    ebn0s = [0.25 * i for i in range(9)]
+    with crnt.Context(0) as ctx:
+        for K in (6144, 40):
+            A, G = K - 24, 3 * (K + 4)
+            for P in (1, 4, 16, 64):
+                if args.bler_cbs:
+                    ncb = args.bler_cbs
+                elif K == 40:
+                    ncb = 1000000
+                else:
+                    ncb = {1: 10000, 4: 20000}.get(P, 100000)
+                chunk = min(ncb, 65536 if K == 40 else 4096)
+                tb = dict(A=A, G=G, Qm=2, P=P, max_iter=8, early_stop=1)
+                plan = ctx.plan([tb] * chunk)
+                for eb in ebn0s:
+                    sig2 = synth.sigma2_ebn0(eb, A / G)
+                    done = errs = undetected = 0
+                    iters = 0.0
+                    t0 = time.perf_counter()
+                    while done < ncb:
+                        bits = torch.randint(0, 2, (chunk, A), generator=gen, device=dev,
+                                             dtype=torch.uint8)
+                        w = torch.tensor([128, 64, 32, 16, 8, 4, 2, 1], dtype=torch.uint8,
+                                         device=dev)
+                        pay = (bits.view(chunk, A // 8, 8) * w).sum(-1).to(torch.uint8)
+                        coded = torch.empty(chunk * G, dtype=torch.uint8, device=dev)
+                        torch.cuda.synchronize()
+                        ctx.encode_batch([tb] * chunk, pay.reshape(-1), coded)
+                        y = (1.0 - 2.0 * coded.float()) + math.sqrt(sig2) * torch.randn(
+                            chunk * G, generator=gen, device=dev)
+                        v = 8.0 * 2.0 * y / sig2
+                        q = torch.sign(v) * torch.floor(v.abs() + 0.5)
+                        llr = q.clamp(-127, 127).to(torch.int8)
+                        out = torch.empty(chunk * A // 8, dtype=torch.uint8, device=dev)
+                        torch.cuda.synchronize()
+                        plan.launch(llr, out, torch.cuda.current_stream().cuda_stream)
+                        res = plan.results_raw(torch.cuda.current_stream().cuda_stream)
+                        ok = torch.from_numpy(res["tb_crc_ok"].astype(np.bool_)).to(dev)
+                        right = (out.view(chunk, A // 8) == pay).all(dim=1)
+                        errs += int((~right).sum())
+                        undetected += int((ok & ~right).sum())
+                        iters += float(np.minimum(res["cb_iters"][:, 0], 8).sum())
+                        done += chunk
+                    # oracle agreement on a seeded subsample at this point
+                    agree = 0
+                    nsub = 8 if K == 6144 else 32
+                    for j in range(nsub):
+                        a = synth.bits(args.seed + 17, int(eb * 100) * 1000 + j, A)
+                        e = oracle.encode_tb(a, G, Qm=2)
+                        llr_o = synth.channel_llrs(e, 1, sig2, args.seed + 17, 7000 + j)
+                        Pe = min(P, K // 8)
+                        bo, ro, _ = oracle.decode_tb(llr_o, A, G, Qm=2, P=Pe, max_iter=8)
+                        od = torch.empty(A // 8, dtype=torch.uint8, device=dev)
+                        rg = ctx.decode_batch([tb], torch.from_numpy(llr_o).to(dev), od)[0]
+                        agree += int(rg["cb_iters"] == ro["cb_iters"] and
+                                     np.array_equal(np.unpackbits(od.cpu().numpy()), bo))
+                    pts.append({"K": K, "P": P, "P_eff": min(P, K // 8), "ebn0_db": eb,
+                                "cbs": done, "bler": errs / done,
+                                "undetected": undetected, "mean_iters": iters / done,
+                                "seconds": round(time.perf_counter() - t0, 2),
+                                "oracle_agreement": "%d/%d" % (agree, nsub)})
+                    print(json.dumps(pts[-1]), flush=True)
+                plan.close()
+    print(json.dumps({"sweep": "bler", "points": pts}), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweep == "bler":
+        bler_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -295,6 +295,12 @@ class Plan:
                                                _ptr(dbg_d), _ptr(dbg_ext), _ptr(dbg_hard))
         _check(rc, "crnt_plan_launch")
 
+    def results_raw(self, stream=0):
+        """Results as a numpy structured array (fields of crnt_tb_result)."""
+        res = (TbResult * len(self.params))()
+        _check(load().crnt_plan_results(self.h, res, stream or None), "crnt_plan_results")
+        return np.ctypeslib.as_array(res)
+
     def results(self, stream=0):
         res = (TbResult * len(self.params))()
         _check(load().crnt_plan_results(self.h, res, stream or None), "crnt_plan_results")

@@ -156,3 +156,32 @@ def test_full_tti_sampled(orc, crnt_lib, ctx):
     sample = sorted(set(int(x) for x in sample))
     check_batch(orc, crnt_lib, tbs, llrs, g, sample=sample)
     assert sum(r["C"] for r in g["res"]) == g["info"]["n_cb"]
+
+
+def test_plan_launch_captured_in_cuda_graph(orc, crnt_lib, ctx):
+    # one persistent launch per TTI can be captured once and replayed
+    shapes = synth.tti_batch(seed=13, n_tb=24, amax=30000)
+    tbs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], max_iter=6, early_stop=0) for s in shapes]
+    llrs = [make_tb(orc, s["A"], s["G"], s["Qm"], 600 + i, snr=s["snr_db"])[1]
+            for i, s in enumerate(shapes)]
+    plan = ctx.plan(tbs)
+    dev = torch.device("cuda")
+    llr_d = torch.from_numpy(np.concatenate(llrs)).to(dev)
+    out_direct = torch.zeros(plan.info["out_bytes"], dtype=torch.uint8, device=dev)
+    out_graph = torch.zeros_like(out_direct)
+    s = torch.cuda.current_stream().cuda_stream
+    plan.launch(llr_d, out_direct, s)
+    want = plan.results(s)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        plan.launch(llr_d, out_graph, torch.cuda.current_stream().cuda_stream)
+    for _ in range(3):
+        out_graph.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    got = plan.results(s)
+    assert torch.equal(out_graph, out_direct)
+    assert [r["cb_iters"] for r in got] == [r["cb_iters"] for r in want]
+    plan.close()
