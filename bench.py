@@ -345,22 +345,31 @@ def run_ours(args):
 
 
 def e2e_leg(ctx, tbs, llr_h, info, args):
-    """The same metric through crnt_decode_batch with pinned host buffers:
-    planning, H2D of the LLRs, the decode, D2H of bits and results."""
+    """The same metric through the C ABI call crnt_decode_batch with pinned
+    host buffers: per step the call plans the batch, copies the LLRs to the
+    device, decodes, and copies the decoded bits and the results back.  The
+    parameter and result arrays are prebuilt C structs, as a C caller holds
+    them."""
     import torch
+
+    import paper_1905_01141_gb300 as crnt
     llr_p = torch.from_numpy(llr_h).pin_memory()
     out_p = torch.zeros(info["out_bytes"], dtype=torch.uint8).pin_memory()
-    ln, on = llr_p.numpy(), out_p.numpy()
-    ctx.decode_batch(tbs, ln, on)
+    par = crnt.params_array(tbs)
+    res = (crnt.TbResult * len(tbs))()
+    n = len(tbs)
+    lp, op = llr_p.data_ptr(), out_p.data_ptr()
+    assert ctx.decode_batch_raw(par, n, lp, op, res) == 0
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        ctx.decode_batch(tbs, ln, on)
+        rc = ctx.decode_batch_raw(par, n, lp, op, res)
     dt = (time.perf_counter() - t0) / args.e2e_steps
+    assert rc == 0
     return {"value": info["info_bits"] / dt / 1e9, "unit": "Gbit/s",
             "h2d_bytes_per_step": int(info["llr_bytes"]),
             "d2h_bytes_per_step": int(info["out_bytes"]) + 2 * int(info["n_cb"]) + len(tbs),
             "ms_per_step": dt * 1e3, "steps": args.e2e_steps,
-            "api": "crnt_decode_batch (host pinned buffers)"}
+            "api": "crnt_decode_batch (host pinned buffers, prebuilt C structs)"}
 
 
 def subframe_latency(crnt, ctx, dev):

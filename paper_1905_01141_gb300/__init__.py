@@ -259,6 +259,11 @@ class Context:
             out.append((d, data))
         return out
 
+    def decode_batch_raw(self, params, n, llr, out, res):
+        """crnt_decode_batch on prebuilt ctypes arrays (TbParams[n],
+        TbResult[n]); llr / out are addresses or arrays; returns the code."""
+        return load().crnt_decode_batch(self.h, params, n, _ptr(llr), _ptr(out), res)
+
     def submit_raw(self, params, ptrs, n, tickets):
         """crnt_submit on prebuilt ctypes arrays (TbParams[n], c_void_p[n],
         c_uint64[n]); returns the status code."""

@@ -336,8 +336,17 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   const size_t s_state = 256, s_done = al256(4 * n), s_crc = al256(8 * n);
   pl->scratch_zero = s_state + s_done + s_crc;
   pl->res_bytes = 2 * ncb + n;
-  // the previous upload from h_desc must have completed before it is reused
-  if (cudaStreamSynchronize(stream) != cudaSuccess) return CRNT_EDEVICE;
+  // The previous upload from h_desc must have completed before the staging
+  // buffer is rewritten, and no launch may still read the device buffers if
+  // they are about to grow.  Waiting on the upload's event (not the whole
+  // stream) lets LLR copies already queued on the stream keep running.
+  if (!pl->desc_ev &&
+      cudaEventCreateWithFlags(&pl->desc_ev, cudaEventDisableTiming) != cudaSuccess)
+    return CRNT_EDEVICE;
+  if (cudaEventSynchronize(pl->desc_ev) != cudaSuccess) return CRNT_EDEVICE;
+  if ((pl->desc_bytes > pl->d_desc.n || pl->scratch_zero + pl->res_bytes > pl->d_scratch.n) &&
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return CRNT_EDEVICE;
   if (!pl->d_desc.ensure(pl->desc_bytes) || !pl->h_desc.ensure(pl->desc_bytes) ||
       !pl->d_scratch.ensure(pl->scratch_zero + pl->res_bytes) || !pl->h_res.ensure(pl->res_bytes))
     return CRNT_ENOMEM;
@@ -346,7 +355,8 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   memcpy(h + off_tbs, pl->tdesc.data(), b_tbs);
   memcpy(h + off_items, pl->items.data(), b_items);
   if (cudaMemcpyAsync(pl->d_desc.p, h, pl->desc_bytes, cudaMemcpyHostToDevice, stream) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaEventRecord(pl->desc_ev, stream) != cudaSuccess)
     return CRNT_EDEVICE;
   uint8_t* sc = (uint8_t*)pl->d_scratch.p;
   DecParams& p = pl->prm;
@@ -586,17 +596,25 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
     if (!ctx->cached) return CRNT_ENOMEM;
   }
   crnt_plan* plan = ctx->cached;
-  int rc = plan_build(ctx, tbs, n, plan, s);
-  if (rc) return rc;
+  // the host LLRs start moving to the device before the host plans the batch
   const int8_t* d_llr = llr;
-  uint8_t* d_out = out;
+  uint64_t llr_bytes = 0;
+  for (uint32_t t = 0; t < n; t++) llr_bytes += tbs[t].G;
   if (!llr_dev) {
-    if (!ctx->stage_in.ensure(plan->info.llr_bytes)) return CRNT_ENOMEM;
-    if (cudaMemcpyAsync(ctx->stage_in.p, llr, plan->info.llr_bytes, cudaMemcpyHostToDevice, s) !=
+    if (ctx->stage_in.n < llr_bytes && cudaStreamSynchronize(s) != cudaSuccess)
+      return CRNT_EDEVICE;
+    if (!ctx->stage_in.ensure(llr_bytes)) return CRNT_ENOMEM;
+    if (cudaMemcpyAsync(ctx->stage_in.p, llr, llr_bytes, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
       return CRNT_EDEVICE;
     d_llr = (const int8_t*)ctx->stage_in.p;
   }
+  int rc = plan_build(ctx, tbs, n, plan, s);
+  if (rc) {
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  uint8_t* d_out = out;
   if (!out_dev) {
     if (!ctx->stage_out.ensure(plan->info.out_bytes)) return CRNT_ENOMEM;
     d_out = (uint8_t*)ctx->stage_out.p;

@@ -88,6 +88,10 @@ struct crnt_plan {
   int smem = 0;
   crnt::Buf d_desc, d_scratch;       // device: descriptors | per-launch scratch
   crnt::Buf h_desc{true}, h_res{true};  // pinned: descriptor staging | results
+  cudaEvent_t desc_ev = nullptr;     // recorded after the last descriptor upload
+  ~crnt_plan() {
+    if (desc_ev) cudaEventDestroy(desc_ev);
+  }
   size_t desc_bytes = 0, scratch_zero = 0, res_bytes = 0;
   crnt::DecParams prm{};
 };
