@@ -82,9 +82,22 @@ __device__ __forceinline__ int acs2(int x0, int c0, int x1, int c1, int S, int T
 // o[s] = sat16(m[s] - m[0]) + OFF.  CHK: the exact path -- one OR over the
 // results detects a value outside [0, 65535] and only then are the clamps
 // applied.  !CHK: the caller has proved (window_fast) that no value can
-// leave the range, so the clamps could never act and are omitted.
+// saturate, so sat16 is the identity and normalisation only subtracts a
+// per-step constant from all eight metrics.  Such a constant cancels in
+// every max-plus comparison and in Lambda (a difference of two maxima over
+// the same alpha and beta), so the clamp-free path skips it and carries
+// unnormalised int32 metrics; they are normalised only where they are
+// stored as 16-bit values (checkpoints, window seeds: pack_norm).  The
+// window_fast bound implies 8 g <= 32767, the largest metric moves by at
+// most g per step, so over at most 6144 steps the metrics stay within 2^25
+// of their start values, far inside int32.
 template <bool CHK>
 __device__ __forceinline__ void normalise(const int m[8], int o[8]) {
+  if (!CHK) {
+#pragma unroll
+    for (int s = 0; s < 8; s++) o[s] = m[s];
+    return;
+  }
   const int base = OFF - m[0];
   o[0] = OFF;
 #pragma unroll
@@ -191,6 +204,19 @@ __device__ __forceinline__ uint4 pack8(const int v[8]) {
   r.w = __byte_perm(v[6], v[7], 0x5410);
   return r;
 }
+// pack8 of normalised metrics: the exact path keeps them normalised at
+// every step; the clamp-free path normalises here, where the stored value
+// must equal the exact path's sat16(m[s] - m[0]) + OFF (no saturation by
+// the window_fast bound).
+template <bool CHK>
+__device__ __forceinline__ uint4 pack_norm(const int v[8]) {
+  if (CHK) return pack8(v);
+  int o[8];
+  const int base = OFF - v[0];
+#pragma unroll
+  for (int s = 0; s < 8; s++) o[s] = v[s] + base;
+  return pack8(o);
+}
 __device__ __forceinline__ void unpack8(uint4 r, int v[8]) {
   v[0] = r.x & 0xFFFF; v[1] = r.x >> 16;
   v[2] = r.y & 0xFFFF; v[3] = r.y >> 16;
@@ -278,18 +304,28 @@ __device__ __forceinline__ uint32_t crc_word(uint32_t r, uint32_t w, const uint3
 // LLRs e_k with k = rank - rank(k0) (mod Nv), k < E, adding them with
 // saturation to [-127, 127] onto the stored soft value (or 0 for new data),
 // and writes the result to its d-stream (and back to the soft buffer).
-__device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restrict__ llr,
+// The received LLRs e are read from `e`: the CB's LLRs in global memory, or
+// their copy staged in shared memory by stage_llrs.
+__device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
                         int8_t* __restrict__ soft_arena, int tid, int nthr) {
+  // descriptor fields in registers: the shared-memory stores below go
+  // through generic pointers and would otherwise force reloads
   const int K = d.K, F = d.F, R = d.R, E = d.E, Nv = d.Nv, rank0 = d.rank0;
+  const int P = d.P, W = d.W, divS = d.divS;
+  const unsigned divM = d.divM;
   const RmGeom g{K, F, R, d.ND, d.maskB, d.mask2};
-  const int8_t* e = llr + d.llr_off;
   int8_t* soft = d.soft_off >= 0 ? soft_arena + d.soft_off : nullptr;
   const bool combine = soft != nullptr && !d.new_data;
+  auto tr = [&](int q) {
+    const int w = (int)(((unsigned)q * divM) >> divS);
+    return (q - w * W) * P + w;
+  };
   int8_t* const streams[3] = {sl.sys, sl.par1, sl.par2};
+  // rows x = unit * R + i, walked with (unit, i) updated incrementally
   const int nrows = 64 * R;
+  int unit = tid / R, i = tid - (tid / R) * R;
+  const int du = nthr / R, di_ = nthr - du * R;
   for (int x = tid; x < nrows; x += nthr) {
-    const int unit = x / R;
-    const int i = x - unit * R;
     rm_visit(
         g, unit, i,
         [&](int p, int st, int di, int rank) {
@@ -298,22 +334,29 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restr
           int acc = combine ? soft[p] : 0;
           for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
           const int8_t v = (int8_t)acc;
-          if (di < K) streams[st][tr_idx(di, d)] = v;
+          if (di < K) streams[st][tr(di)] = v;
           else sl.tail[3 * (di - K) + st] = v;
           if (soft) soft[p] = v;
         },
         [&](int p) {
           if (soft && !combine) soft[p] = 0;
         });
+    unit += du;
+    i += di_;
+    if (i >= R) {
+      i -= R;
+      unit++;
+    }
   }
   // filler: known zero bits in the systematic stream, unknown parity 1
   for (int k = tid; k < F; k += nthr) {
-    const int t = tr_idx(k, d);
+    const int t = tr(k);
     sl.sys[t] = 127;
     sl.par1[t] = 0;
   }
-  const int tp = d.W * d.P;
-  for (int k = tid; k < tp; k += nthr) sl.ext[k] = 0;
+  const int tp = W * P;
+  uint4* ext16 = (uint4*)sl.ext;  // the ext area is 16-byte aligned and padded
+  for (int k = tid; k < (2 * tp + 15) / 16; k += nthr) ext16[k] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     sl.flags[0] = 0;
     sl.flags[1] = 0;
@@ -321,6 +364,53 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* __restr
     sl.flags[3] = 0;
     sl.flags[4] = 0;
     sl.flags[5] = 0;
+  }
+}
+
+// Copy of the CB's E received LLRs into the slot's seed + checkpoint area,
+// which the first SISO pass writes before reading.  Bulk 16-byte loads, all
+// issued before any is consumed, replace the de-rate-matcher's scattered
+// dependent byte loads from global memory.  The copy keeps the global
+// address modulo 16 (byte k at stage + (e & 15) + k) so that the 16-byte
+// body is aligned on both sides; the head and tail bytes are copied singly
+// and no byte outside [e, e + E) is read.  llr_src gives the pointer the
+// de-rate-matcher reads: the staged copy, or the global LLRs when E does not
+// fit (heavy repetition; stage_llrs then copies nothing).
+__device__ __forceinline__ const int8_t* llr_src(const CbDesc& d, const CbSlot& sl,
+                                                 const int8_t* llr) {
+  const int8_t* e = llr + d.llr_off;
+  const int cap = 16 * d.P * (4 + (d.W + kSub - 1) / kSub);
+  if (d.E + 15 > cap) return e;
+  return (const int8_t*)sl.seed + ((uintptr_t)e & 15u);
+}
+__device__ void stage_llrs(const CbDesc& d, const CbSlot& sl, const int8_t* __restrict__ llr,
+                           int tid, int nthr) {
+  const int8_t* e = llr + d.llr_off;
+  const int E = d.E;
+  const int8_t* src = llr_src(d, sl, llr);
+  if (src == e) return;
+  const int s0 = (int)((uintptr_t)e & 15u);
+  int8_t* st = (int8_t*)sl.seed + s0;
+  const int head = min(E, (16 - s0) & 15);
+  const int n16 = (E - head) >> 4;
+  const int tail0 = head + 16 * n16;
+  for (int k = tid; k < head; k += nthr) st[k] = e[k];
+  for (int k = tail0 + tid; k < E; k += nthr) st[k] = e[k];
+  const int4* gsrc = (const int4*)(e + head);
+  int4* sdst = (int4*)(st + head);
+  constexpr int kBatch = 1;
+  for (int i0 = tid; i0 < n16; i0 += kBatch * nthr) {
+    int4 v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      const int i = i0 + u * nthr;
+      if (i < n16) v[u] = __ldg(gsrc + i);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      const int i = i0 + u * nthr;
+      if (i < n16) sdst[i] = v[u];
+    }
   }
 }
 
@@ -334,6 +424,7 @@ struct Win {
   int K, P, W, divM, divS;  // geometry (tr_idx)
   int f2x2;                 // QPP first-difference step
   int p, lo, len, pad;
+  bool hard_on;             // DEC 1: form the hard decisions
 };
 
 __device__ __forceinline__ int tr_w(const Win& w, int q) {
@@ -363,7 +454,9 @@ __device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, 
 // Backward processing of one sub-window [j0, j0 + slen) of a window:
 // recompute forward metrics from the checkpoint into registers, then walk
 // back computing Lambda / Le and the backward metrics.  FULL: slen == kSub
-// (no per-step guards).  mx tracks the largest |extrinsic| written.
+// (no per-step guards).  mx tracks the largest |extrinsic| written.  With
+// w.hard_on (DEC 1 only) the hard decisions sign(Lambda) are also recorded
+// at the natural positions.
 template <int DEC, bool FULL, bool CHK>
 __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
                                                 int dq, int b[8], int& mx) {
@@ -389,9 +482,9 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
       const int v = scale_ext(le);
       mx = __vimax3_s32(mx, v, -v);
       w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : tr_w(w, Qv[jj])] = (int16_t)v;
-      if (DEC == 1 && lam < 0) {
+      if (DEC == 1 && w.hard_on) {  // branch-free: ORs a zero when lam >= 0
         const int qq = Qv[jj] + w.pad;
-        atomicOr(&w.hard[qq >> 5], 1u << (31 - (qq & 31)));
+        atomicOr(&w.hard[qq >> 5], ((unsigned)lam >> 31) << (31 - (qq & 31)));
       }
       beta_step<CHK>(b, S, S + Lp, Lp);
     }
@@ -405,6 +498,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
                                             int b[8], int& mx) {
   const int K = w.K, P = w.P, p = w.p, lo = w.lo, len = w.len;
   const int f1 = dp->f1, f2 = dp->f2;
+  const int f2sub = DEC ? dp->f2sub : 0, f2jump = DEC ? dp->f2jump : 0;
 
   // ---- forward pass with a checkpoint every kSub steps
   int q = 0, dq = 0;
@@ -414,7 +508,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
   }
   int j0 = 0;
   for (; j0 + kSub <= len; j0 += kSub) {
-    ck[j0 / kSub] = pack8(a);
+    ck[j0 / kSub] = pack_norm<CHK>(a);
 #pragma unroll
     for (int jj = 0; jj < kSub; jj += 2) {
       int S, Lp, t, o[8];
@@ -425,7 +519,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     }
   }
   if (j0 < len) {
-    ck[j0 / kSub] = pack8(a);
+    ck[j0 / kSub] = pack_norm<CHK>(a);
     for (int j = j0; j < len; j++) {
       int S, Lp, t, o[8];
       load_step<DEC>(w, j, q, dq, S, Lp, t);
@@ -434,7 +528,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
       for (int s = 0; s < 8; s++) a[s] = o[s];
     }
   }
-  if (p + 1 < P) seedA[p + 1] = pack8(a);
+  if (p + 1 < P) seedA[p + 1] = pack_norm<CHK>(a);
 
   // ---- backward pass, one sub-window at a time from the end.  QPP state
   // at the start of the last sub-window, walked backwards by kSub steps:
@@ -457,8 +551,8 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     sub_window_back<DEC, false, CHK>(w, ck[sw], kSub * sw, last_len, pis, dls, b, mx);
     if (DEC == 1) {
       pis = modsub(pis, jmp, K);
-      dls = modsub(dls, dp->f2sub, K);
-      jmp = modsub(jmp, dp->f2jump, K);
+      dls = modsub(dls, f2sub, K);
+      jmp = modsub(jmp, f2jump, K);
     }
     sw--;
   }
@@ -466,21 +560,23 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     sub_window_back<DEC, true, CHK>(w, ck[sw], kSub * sw, kSub, pis, dls, b, mx);
     if (DEC == 1) {
       pis = modsub(pis, jmp, K);
-      dls = modsub(dls, dp->f2sub, K);
-      jmp = modsub(jmp, dp->f2jump, K);
+      dls = modsub(dls, f2sub, K);
+      jmp = modsub(jmp, f2jump, K);
     }
   }
-  if (p > 0) seedB[p - 1] = pack8(b);
+  if (p > 0) seedB[p - 1] = pack_norm<CHK>(b);
 }
 
 // One SISO pass of window p of one CB.  DEC = 0: natural order (encoder 1),
 // DEC = 1: QPP order (encoder 2).  All threads of the CTA call it (run =
 // false for idle threads) because it contains barriers.  flags[4 + d] holds
 // the largest |extrinsic| written by the last pass of decoder d, which
-// bounds |La| for the pass that reads it.
+// bounds |La| for the pass that reads it.  hard (DEC 1): the hard decisions
+// of this iteration are used (a CRC check follows); otherwise they are not
+// formed, since the next iteration overwrites them unread.
 template <int DEC>
 __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t* base, int p,
-                                          bool run, bool first) {
+                                          bool run, bool first, bool hard) {
   const int K = dp->K, P = dp->P, W = dp->W;
   const CbSlot sl = make_slot(base, K, P, W);
   uint4* seedA = sl.seed + DEC * P;
@@ -512,7 +608,7 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     }
     m_in = sl.flags[5 - DEC];
     if (p == 0) sl.flags[4 + DEC] = 0;  // written by this pass after the barrier
-    if (DEC == 1) {
+    if (DEC == 1 && hard) {
       const int nwords = (K + 31) / 32;
       for (int w = p; w < nwords; w += P) sl.hard[w] = 0u;
     }
@@ -524,6 +620,7 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     w.par = DEC ? sl.par2 : sl.par1;
     w.ext = sl.ext;
     w.hard = sl.hard;
+    w.hard_on = hard;
     w.K = K;
     w.P = P;
     w.W = W;
@@ -606,11 +703,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
     const bool mine = mycb < G;
     const CbDesc* dp = cbs + (mine ? mycb : 0);
 
-    // ---- phase 0: de-rate-matching of every CB of the item
+    // ---- phase 0: de-rate-matching of every CB of the item (LLRs staged
+    // in shared memory first)
     for (int g = 0; g < G; g++) {
       const CbDesc& dg = cbs[g];
       const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
-      derm_cb(dg, sg, prm.llr, prm.soft, tid, kThreads);
+      stage_llrs(dg, sg, prm.llr, tid, kThreads);
+    }
+    __syncthreads();
+    for (int g = 0; g < G; g++) {
+      const CbDesc& dg = cbs[g];
+      const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
+      derm_cb(dg, sg, llr_src(dg, sg, prm.llr), prm.soft, tid, kThreads);
     }
     if (tid == 0) {
       s_remaining = G;
@@ -649,9 +753,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
       const int my_max = mine ? (int)dp->max_iter : 0;
       const bool run = mine && fl[0] == 0 && it <= my_max;
       const bool first = (it == 1);
-      siso_pass<0>(dp, mybase, p, run, first);
-      siso_pass<1>(dp, mybase, p, run, first);
+      siso_pass<0>(dp, mybase, p, run, first, false);
       const bool check = run && (dp->early_stop || it == my_max);
+      siso_pass<1>(dp, mybase, p, run, first, check);
       if (check) {
         const CbDesc& d = *dp;
         const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
