@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdint>
 #include <cstring>
@@ -59,31 +60,28 @@ std::vector<uint32_t> xpow_table(uint32_t g, int n) {
 }
 
 // Exact division q / W as (q * M) >> s for 0 <= q < qmax, verified
-// exhaustively; cached per (W, qmax).
+// exhaustively over q < 8192 (every K + 4 <= 6148 is below that bound), so one
+// divider per W serves every CB; kept in a lock-free table filled on first use
+// (racing threads compute and store the same value).
 bool find_divider(int W, int qmax, int* M, int* s) {
-  static std::mutex mu;
-  static std::map<std::pair<int, int>, std::pair<int, int>> cache;
-  std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_pair(W, qmax);
-  auto it = cache.find(key);
-  if (it != cache.end()) {
-    *M = it->second.first;
-    *s = it->second.second;
-    return true;
-  }
-  for (int sh = 0; sh < 32; sh++) {
-    const uint64_t m = ((1ull << sh) + W - 1) / W;
-    if (m * (uint64_t)qmax >= (1ull << 32)) break;
-    bool ok = true;
-    for (int q = 0; q < qmax && ok; q++) ok = (int)((q * m) >> sh) == q / W;
-    if (ok) {
-      cache[key] = std::make_pair((int)m, sh);
-      *M = (int)m;
-      *s = sh;
-      return true;
+  constexpr int kQ = 8192;
+  static std::atomic<uint64_t> table[lte::kZ + 1];
+  if (W < 1 || W > lte::kZ || qmax > kQ) return false;
+  uint64_t v = table[W].load(std::memory_order_relaxed);
+  if (!v) {
+    for (int sh = 0; sh < 32 && !v; sh++) {
+      const uint64_t m = ((1ull << sh) + W - 1) / W;
+      if (m * (uint64_t)kQ >= (1ull << 32)) break;
+      bool ok = true;
+      for (int q = 0; q < kQ && ok; q++) ok = (int)((q * m) >> sh) == q / W;
+      if (ok) v = (m << 8) | (uint64_t)sh | (1ull << 63);
     }
+    if (!v) return false;
+    table[W].store(v, std::memory_order_relaxed);
   }
-  return false;
+  *M = (int)((v & ~(1ull << 63)) >> 8);
+  *s = (int)(v & 0xFF);
+  return true;
 }
 
 // Window count for a CB of size K: the caller's P clamped to [1, K/8] and
@@ -104,17 +102,30 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Column masks of the circular-buffer rank formula (see rm_geom.cuh).
+// Column masks of the circular-buffer rank formula (see rm_geom.cuh): bit c
+// of maskB is [P(c) < (ND + F) mod 32], bit c of mask2 is [P(c) < ND - 1],
+// with P the bit-reversal column permutation.  kColsBelow[x] holds the
+// columns c with P(c) < x.
+struct ColsBelow {
+  uint32_t m[33];
+  constexpr ColsBelow() : m() {
+    for (int x = 0; x <= 32; x++) {
+      uint32_t v = 0;
+      for (int c = 0; c < 32; c++) {
+        int pc = 0;
+        for (int i = 0; i < 5; i++) pc |= ((c >> i) & 1) << (4 - i);
+        if (pc < x) v |= 1u << c;
+      }
+      m[x] = v;
+    }
+  }
+};
+constexpr ColsBelow kColsBelow{};
+
 void rm_masks(int ND, int F, uint32_t* maskB, uint32_t* mask2) {
   const int X = ND + F;
-  uint32_t mb = 0, m2 = 0;
-  for (int c = 0; c < 32; c++) {
-    const int pc = lte::bitrev5(c);
-    if (pc < (X & 31)) mb |= 1u << c;
-    if (pc < ND - 1) m2 |= 1u << c;
-  }
-  *maskB = mb;
-  *mask2 = m2;
+  *maskB = kColsBelow.m[X & 31];
+  *mask2 = ND >= 1 ? kColsBelow.m[ND - 1 < 32 ? ND - 1 : 32] : 0u;
 }
 
 // Non-NULL positions before k0.  k0 = R (24 rv + 2) always starts a column:
@@ -182,127 +193,239 @@ int validate(const crnt_tb_params& t, lte::Seg* seg) {
   return CRNT_OK;
 }
 
+namespace {
+
+bool make_tmpl(int K, int Preq, KTmpl* t) {
+  const int ki = lte::index_of(K);
+  if (ki < 0) return false;
+  const int Pr = clamp_p(K, Preq);
+  t->K = K;
+  t->W = (K + Pr - 1) / Pr;
+  t->P = (K + t->W - 1) / t->W;
+  if (!find_divider(t->W, K + 4, &t->divM, &t->divS)) return false;
+  t->f1 = lte::kF1[ki];
+  t->f2 = lte::kF2[ki];
+  t->f2x2 = (int)((2ll * t->f2) % K);
+  t->f2sub = (int)((2ll * kSub * t->f2) % K);
+  t->f2jump = (int)((2ll * kSub * kSub * t->f2) % K);
+  t->R = lte::rows(K);
+  t->ND = 32 * t->R - (K + 4);
+  t->ncb = lte::ncb(K);
+  t->slot = align16(dec_cb_smem(K, t->P, t->W));
+  rm_masks(t->ND, 0, &t->maskB0, &t->mask2);
+  for (int rv = 0; rv < 4; rv++) t->rank0[rv] = rank_of_k0(K, 0, rv, t->maskB0, t->mask2);
+  return true;
+}
+
+// Templates of the autotuned window count (P request 0), filled on first use.
+const KTmpl* auto_tmpl(int K) {
+  static std::mutex mu;
+  static KTmpl table[lte::kNumK];
+  static std::atomic<int> ready[lte::kNumK];
+  const int ki = lte::index_of(K);
+  if (ki < 0) return nullptr;
+  if (!ready[ki].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[ki].load(std::memory_order_relaxed)) {
+      if (!make_tmpl(K, 0, &table[ki])) return nullptr;
+      ready[ki].store(1, std::memory_order_release);
+    }
+  }
+  return &table[ki];
+}
+
+}  // namespace
+
+// Two passes.  Pass 1 validates every TB, fixes its offsets and the sort key
+// of each CB; pass 2 writes the CB descriptors in sorted (work-item) order
+// straight into the pinned staging buffer, from closed forms of the per-CB
+// offsets inside a TB.
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
                cudaStream_t stream, const int64_t* llr_base) {
   pl->ctx = ctx;
   pl->tbs.assign(tbs, tbs + n);
-  pl->segs.assign(n, lte::Seg{});
-  pl->p_used.assign(n, 0);
-  pl->tdesc.assign(n, TbDesc{});
-  pl->cbs.clear();
-  pl->cb_tb.clear();
-  pl->cb_r.clear();
+  pl->segs.resize(n);
+  pl->p_used.resize(n);
+  pl->tdesc.resize(n);
+  pl->pre.resize(n);
+  pl->keyed.clear();
+  pl->owner.clear();
   pl->items.clear();
-  std::vector<CbDesc> all;
-  std::vector<int> all_tb, all_r;
-  all.reserve(n * 4);
   int64_t llr_off = 0, out_off = 0, dbg_off = 0;
   uint64_t steps = 0, info_bits = 0;
+  uint32_t ncb = 0;
   for (uint32_t t = 0; t < n; t++) {
     const crnt_tb_params& tp = tbs[t];
     lte::Seg& s = pl->segs[t];
     int rc = validate(tp, &s);
     if (rc) return rc;
-    int64_t soft_base = -1;
+    TbPre& pr = pl->pre[t];
+    pr.soft = -1;
     if (tp.flags & CRNT_F_HARQ) {
-      rc = harq_bind(ctx, tp, &soft_base);
+      rc = harq_bind(ctx, tp, &pr.soft);
       if (rc) return rc;
     }
+    for (int h = 0; h < 2; h++) {
+      const int K = h ? s.Kp : s.Km;
+      KTmpl& tm = h ? pr.tp : pr.tm;
+      if (h == 0 && s.Cm == 0) continue;
+      if (tp.P == 0) {
+        const KTmpl* a = auto_tmpl(K);
+        if (!a) return CRNT_EINVAL;
+        tm = *a;
+      } else if (!make_tmpl(K, tp.P, &tm)) {
+        return CRNT_EINVAL;
+      }
+      if (tm.slot > kSmemBudget) return CRNT_EINVAL;
+    }
+    if (((pr.tp.ND + s.F) >> 5) + 1 > pr.tp.R ||
+        (s.Cm && ((pr.tm.ND + s.F) >> 5) + 1 > pr.tm.R))
+      return CRNT_EINVAL;
+    const int Gp = (int)tp.G / (tp.NL * tp.Qm);
+    pr.n_lo = s.C - Gp % s.C;
+    pr.E_lo = tp.NL * tp.Qm * (Gp / s.C);
+    pr.E_hi = tp.NL * tp.Qm * ((Gp + s.C - 1) / s.C);
+    pr.llr = llr_base ? llr_base[t] : llr_off;
+    pr.dbg = dbg_off;
+    pr.cb0 = ncb;
     TbDesc& td = pl->tdesc[t];
     td.out_off = out_off;
     td.A = (int)tp.A;
     td.C = s.C;
-    td.cb0 = (int)all.size();
-    pl->p_used[t] = (uint16_t)clamp_p(s.Kp, tp.P);
-    const int B = (int)tp.A + 24;
-    int pay_off = 0, eoff = 0, soff = 0;
+    td.cb0 = (int)ncb;
+    td.pad0 = 0;
+    pl->p_used[t] = (uint16_t)pr.tp.P;
     for (int r = 0; r < s.C; r++) {
-      CbDesc d;
-      memset(&d, 0, sizeof d);
-      const int K = lte::cb_k(s, r);
-      const int F = r == 0 ? s.F : 0;
-      const int Pr = clamp_p(K, tp.P);
-      const int W = (K + Pr - 1) / Pr;
-      d.K = K;
-      d.F = F;
-      d.E = lte::e_r((int)tp.G, tp.Qm, tp.NL, s.C, r);
-      d.k0 = lte::k0(K, tp.rv);
-      d.W = W;
-      d.P = (K + W - 1) / W;
-      if (!find_divider(W, K + 4, &d.divM, &d.divS)) return CRNT_EINVAL;
-      const int ki = lte::index_of(K);
-      d.f1 = lte::kF1[ki];
-      d.f2 = lte::kF2[ki];
-      d.f2x2 = (int)((2ll * d.f2) % K);
-      d.f2sub = (int)((2ll * kSub * d.f2) % K);
-      d.f2jump = (int)((2ll * kSub * kSub * d.f2) % K);
-      d.R = lte::rows(K);
-      d.ND = 32 * d.R - (K + 4);
-      d.Nv = 3 * (K + 4) - 2 * F;
-      if (((d.ND + F) >> 5) + 1 > d.R) return CRNT_EINVAL;
-      rm_masks(d.ND, F, &d.maskB, &d.mask2);
-      d.rank0 = rank_of_k0(K, F, tp.rv, d.maskB, d.mask2);
-      d.tb = (int)t;
-      d.r = r;
-      d.llr_off = (llr_base ? llr_base[t] : llr_off) + eoff;
-      d.soft_off = soft_base >= 0 ? soft_base + soff : -1;
-      d.pay_bits = K - F - s.L;
-      d.pay_off = pay_off;
-      d.n_after = B - pay_off - d.pay_bits;
-      d.dbg_off = (int32_t)dbg_off;
-      d.crc_b = s.C > 1;
-      d.max_iter = tp.max_iter;
-      d.early_stop = tp.early_stop ? 1 : 0;
-      d.new_data = tp.new_data ? 1 : 0;
-      pay_off += d.pay_bits;
-      eoff += d.E;
-      soff += lte::ncb(K);
-      dbg_off += K + 4;
-      steps += K;
-      all.push_back(d);
-      all_tb.push_back((int)t);
-      all_r.push_back(r);
+      const KTmpl& tm = r < s.Cm ? pr.tm : pr.tp;
+      const uint64_t cost = (uint64_t)(tm.W * tp.max_iter);  // < 2^17
+      // descending W max_iter, then K, then P; ascending (t, r) -- one
+      // integer sorted ascending
+      pl->keyed.push_back(((0x1FFFFull - cost) << 46) | ((uint64_t)(0x1FFF - tm.K) << 33) |
+                          ((uint64_t)(0xFF - tm.P) << 25) | (uint64_t)(ncb + r));
+      pl->owner.push_back(t);
+      dbg_off += tm.K + 4;
+      steps += tm.K;
     }
-    if (eoff != (int)tp.G || pay_off != B) return CRNT_EINVAL;
+    ncb += s.C;
+    if (ncb >= (1u << 25)) return CRNT_EINVAL;
     llr_off += tp.G;
     out_off += tp.A / 8;
     info_bits += tp.A;
   }
-  // ---- work items: CBs of equal (K, P) share a CTA; longest work first
-  std::vector<int> order(all.size());
-  for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const CbDesc &a = all[x], &b = all[y];
-    const int ca = a.W * a.max_iter, cb = b.W * b.max_iter;
-    if (ca != cb) return ca > cb;
-    if (a.K != b.K) return a.K > b.K;
-    return a.P > b.P;
-  });
-  pl->cbs.reserve(all.size());
-  size_t i = 0;
+  std::sort(pl->keyed.begin(), pl->keyed.end());
+
+  // ---- buffers: descriptors | zeroed per-launch state | work items
+  const size_t b_cbs = sizeof(CbDesc) * ncb, b_tbs = sizeof(TbDesc) * n;
+  const size_t off_tbs = al256(b_cbs), off_zero = off_tbs + al256(b_tbs);
+  const size_t s_state = 256, s_done = al256(4 * n), s_crc = al256(8 * n);
+  pl->zero_off = off_zero;
+  pl->scratch_zero = s_state + s_done + s_crc;
+  const size_t off_items = off_zero + pl->scratch_zero;
+  const size_t max_desc = off_items + sizeof(WorkItem) * ncb;
+  pl->res_bytes = 2 * (size_t)ncb + n;
+  // The previous upload from h_desc must have completed before the staging
+  // buffer is rewritten, and no launch may still read the device buffers if
+  // they are about to grow.  Waiting on the upload's event (not the whole
+  // stream) lets LLR copies already queued on the stream keep running.
+  if (!pl->desc_ev &&
+      cudaEventCreateWithFlags(&pl->desc_ev, cudaEventDisableTiming) != cudaSuccess)
+    return CRNT_EDEVICE;
+  if (pl->upload_pending && cudaEventSynchronize(pl->desc_ev) != cudaSuccess)
+    return CRNT_EDEVICE;
+  pl->upload_pending = false;
+  if ((max_desc > pl->d_desc.n || pl->res_bytes > pl->d_scratch.n) &&
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return CRNT_EDEVICE;
+  if (!pl->d_desc.ensure(max_desc) || !pl->h_desc.ensure(max_desc) ||
+      !pl->d_scratch.ensure(pl->res_bytes) || !pl->h_res.ensure(pl->res_bytes))
+    return CRNT_ENOMEM;
+  uint8_t* h = (uint8_t*)pl->h_desc.p;
+  CbDesc* hc = (CbDesc*)h;
+  WorkItem* hi = (WorkItem*)(h + off_items);
+  pl->cb_tb.resize(ncb);
+  pl->cb_r.resize(ncb);
+
+  // ---- pass 2: descriptors in sorted order, grouped into work items of
+  // equal (K, P), as many CBs as the CTA's threads and shared memory allow
   int max_slot_bytes = 0;
-  while (i < order.size()) {
-    const CbDesc& h = all[order[i]];
-    const int slot = align16(dec_cb_smem(h.K, h.P, h.W));
-    if (slot > kSmemBudget) return CRNT_EINVAL;
-    const int gmax = std::max(1, std::min(kThreads / h.P, kSmemBudget / slot));
-    WorkItem wi;
-    wi.cb0 = (int)pl->cbs.size();
-    wi.n = 0;
-    wi.smem_per_cb = slot;
-    wi.pad0 = 0;
-    while (i < order.size() && wi.n < gmax) {
-      const CbDesc& c = all[order[i]];
-      if (c.K != h.K || c.P != h.P) break;
-      pl->cbs.push_back(c);
-      pl->cb_tb.push_back(all_tb[order[i]]);
-      pl->cb_r.push_back(all_r[order[i]]);
-      wi.n++;
-      i++;
+  WorkItem wi{0, 0, 0, 0};
+  int gmax = 0, iK = -1, iP = -1;
+  for (uint32_t i = 0; i < ncb; i++) {
+    const uint32_t g = (uint32_t)(pl->keyed[i] & 0x1FFFFFF);
+    const uint32_t t = pl->owner[g];
+    const crnt_tb_params& tp = tbs[t];
+    const lte::Seg& s = pl->segs[t];
+    const TbPre& pr = pl->pre[t];
+    const int r = (int)(g - pr.cb0);
+    const KTmpl& tm = r < s.Cm ? pr.tm : pr.tp;
+    const int F = r == 0 ? s.F : 0;
+    const int nm = std::min(r, s.Cm), np = r - nm;  // earlier CBs of size K-, K+
+    const int sumK = nm * s.Km + np * s.Kp;
+    const int sumNcb = nm * (s.Cm ? pr.tm.ncb : 0) + np * pr.tp.ncb;
+    const int eoff = r <= pr.n_lo ? r * pr.E_lo : pr.n_lo * pr.E_lo + (r - pr.n_lo) * pr.E_hi;
+    const int pay_off = sumK - (r > 0 ? s.F : 0) - r * s.L;
+    CbDesc& d = hc[i];
+    d.K = tm.K;
+    d.F = F;
+    d.E = r < pr.n_lo ? pr.E_lo : pr.E_hi;
+    d.k0 = lte::k0(tm.K, tp.rv);
+    d.P = tm.P;
+    d.W = tm.W;
+    d.divM = tm.divM;
+    d.divS = tm.divS;
+    d.f1 = tm.f1;
+    d.f2 = tm.f2;
+    d.f2x2 = tm.f2x2;
+    d.f2sub = tm.f2sub;
+    d.f2jump = tm.f2jump;
+    d.R = tm.R;
+    d.ND = tm.ND;
+    d.Nv = 3 * (tm.K + 4) - 2 * F;
+    if (F == 0) {
+      d.maskB = tm.maskB0;
+      d.mask2 = tm.mask2;
+      d.rank0 = tm.rank0[tp.rv];
+    } else {
+      rm_masks(tm.ND, F, &d.maskB, &d.mask2);
+      d.rank0 = rank_of_k0(tm.K, F, tp.rv, d.maskB, d.mask2);
     }
-    max_slot_bytes = std::max(max_slot_bytes, wi.n * slot);
+    d.tb = (int)t;
+    d.r = r;
+    d.llr_off = pr.llr + eoff;
+    d.soft_off = pr.soft >= 0 ? pr.soft + sumNcb : -1;
+    d.pay_bits = tm.K - F - s.L;
+    d.pay_off = pay_off;
+    d.n_after = ((int)tp.A + 24) - pay_off - d.pay_bits;
+    d.dbg_off = (int32_t)(pr.dbg + sumK + 4 * r);
+    d.crc_b = s.C > 1;
+    d.max_iter = tp.max_iter;
+    d.early_stop = tp.early_stop ? 1 : 0;
+    d.new_data = tp.new_data ? 1 : 0;
+    memset(d.pad0, 0, sizeof d.pad0);
+    pl->cb_tb[i] = (int)t;
+    pl->cb_r[i] = r;
+    if (wi.n == 0 || wi.n >= gmax || d.K != iK || d.P != iP) {
+      if (wi.n) {
+        max_slot_bytes = std::max(max_slot_bytes, wi.n * wi.smem_per_cb);
+        hi[pl->items.size()] = wi;
+        pl->items.push_back(wi);
+      }
+      wi.cb0 = (int)i;
+      wi.n = 0;
+      wi.smem_per_cb = tm.slot;
+      wi.pad0 = 0;
+      gmax = std::max(1, std::min(kThreads / tm.P, kSmemBudget / tm.slot));
+      iK = d.K;
+      iP = d.P;
+    }
+    wi.n++;
+  }
+  if (wi.n) {
+    max_slot_bytes = std::max(max_slot_bytes, wi.n * wi.smem_per_cb);
+    hi[pl->items.size()] = wi;
     pl->items.push_back(wi);
   }
+  pl->n_cb = ncb;
   pl->smem = 2048 + max_slot_bytes;
   static std::mutex occ_mu;
   static std::map<int, int> occ_cache;  // dynamic smem -> resident CTAs per SM
@@ -318,7 +441,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
 
   crnt_plan_info& inf = pl->info;
   inf.n_tb = n;
-  inf.n_cb = (uint32_t)pl->cbs.size();
+  inf.n_cb = ncb;
   inf.llr_bytes = (uint64_t)llr_off;
   inf.out_bytes = (uint64_t)out_off;
   inf.info_bits = info_bits;
@@ -327,50 +450,31 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   inf.n_items = (uint32_t)pl->items.size();
   inf.grid = (uint32_t)grid;
 
-  // ---- descriptors: pinned staging -> device (async on `stream`)
-  const size_t ncb = pl->cbs.size();
-  const size_t b_cbs = sizeof(CbDesc) * ncb, b_tbs = sizeof(TbDesc) * n,
-               b_items = sizeof(WorkItem) * pl->items.size();
-  const size_t off_tbs = al256(b_cbs), off_items = off_tbs + al256(b_tbs);
-  pl->desc_bytes = off_items + b_items;
-  const size_t s_state = 256, s_done = al256(4 * n), s_crc = al256(8 * n);
-  pl->scratch_zero = s_state + s_done + s_crc;
-  pl->res_bytes = 2 * ncb + n;
-  // The previous upload from h_desc must have completed before the staging
-  // buffer is rewritten, and no launch may still read the device buffers if
-  // they are about to grow.  Waiting on the upload's event (not the whole
-  // stream) lets LLR copies already queued on the stream keep running.
-  if (!pl->desc_ev &&
-      cudaEventCreateWithFlags(&pl->desc_ev, cudaEventDisableTiming) != cudaSuccess)
-    return CRNT_EDEVICE;
-  if (cudaEventSynchronize(pl->desc_ev) != cudaSuccess) return CRNT_EDEVICE;
-  if ((pl->desc_bytes > pl->d_desc.n || pl->scratch_zero + pl->res_bytes > pl->d_scratch.n) &&
-      cudaStreamSynchronize(stream) != cudaSuccess)
-    return CRNT_EDEVICE;
-  if (!pl->d_desc.ensure(pl->desc_bytes) || !pl->h_desc.ensure(pl->desc_bytes) ||
-      !pl->d_scratch.ensure(pl->scratch_zero + pl->res_bytes) || !pl->h_res.ensure(pl->res_bytes))
-    return CRNT_ENOMEM;
-  uint8_t* h = (uint8_t*)pl->h_desc.p;
-  memcpy(h, pl->cbs.data(), b_cbs);
+  // ---- upload: descriptors, TB table, zeroed state and work items in one
+  // copy (asynchronous on `stream`)
   memcpy(h + off_tbs, pl->tdesc.data(), b_tbs);
-  memcpy(h + off_items, pl->items.data(), b_items);
+  memset(h + off_zero, 0, pl->scratch_zero);
+  pl->desc_bytes = off_items + sizeof(WorkItem) * pl->items.size();
   if (cudaMemcpyAsync(pl->d_desc.p, h, pl->desc_bytes, cudaMemcpyHostToDevice, stream) !=
           cudaSuccess ||
       cudaEventRecord(pl->desc_ev, stream) != cudaSuccess)
     return CRNT_EDEVICE;
+  pl->upload_pending = true;
+  pl->state_fresh = true;
+  uint8_t* dd = (uint8_t*)pl->d_desc.p;
   uint8_t* sc = (uint8_t*)pl->d_scratch.p;
   DecParams& p = pl->prm;
   memset(&p, 0, sizeof p);
-  p.cbs = (const CbDesc*)pl->d_desc.p;
-  p.tbs = (const TbDesc*)((uint8_t*)pl->d_desc.p + off_tbs);
-  p.items = (const WorkItem*)((uint8_t*)pl->d_desc.p + off_items);
+  p.cbs = (const CbDesc*)dd;
+  p.tbs = (const TbDesc*)(dd + off_tbs);
+  p.items = (const WorkItem*)(dd + off_items);
   p.n_items = (int)pl->items.size();
   p.n_cbs = (int)ncb;
   p.n_tbs = (int)n;
-  p.state = (DecState*)sc;
-  p.tb_done = (int32_t*)(sc + s_state);
-  p.tb_crc = (uint32_t*)(sc + s_state + s_done);
-  p.cb_iters = sc + pl->scratch_zero;
+  p.state = (DecState*)(dd + off_zero);
+  p.tb_done = (int32_t*)(dd + off_zero + s_state);
+  p.tb_crc = (uint32_t*)(dd + off_zero + s_state + s_done);
+  p.cb_iters = sc;
   p.cb_ok = p.cb_iters + ncb;
   p.tb_ok = p.cb_ok + ncb;
   p.xpowA = ctx->xpowA;
@@ -379,7 +483,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
 }
 
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
-                int16_t* dbg_ext, uint8_t* dbg_hard) {
+                int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded) {
   DecParams p = pl->prm;
   p.llr = llr;
   p.out = out;
@@ -387,7 +491,13 @@ int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, 
   p.dbg_d = dbg_d;
   p.dbg_ext = dbg_ext;
   p.dbg_hard = dbg_hard;
-  if (cudaMemsetAsync(pl->d_scratch.p, 0, pl->scratch_zero, s) != cudaSuccess) return CRNT_EDEVICE;
+  // the queue head and the TB accumulators start at zero: the upload of
+  // plan_build wrote zeros, a later launch of the same plan clears them
+  if (!(state_uploaded && pl->state_fresh) &&
+      cudaMemsetAsync((uint8_t*)pl->d_desc.p + pl->zero_off, 0, pl->scratch_zero, s) !=
+          cudaSuccess)
+    return CRNT_EDEVICE;
+  pl->state_fresh = false;
   if (launch_decode(p, (int)pl->info.grid, pl->smem, s) != cudaSuccess) return CRNT_EDEVICE;
   return CRNT_OK;
 }
@@ -400,7 +510,7 @@ int plan_fetch_results(crnt_plan* pl, cudaStream_t s) {
 }
 
 void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res) {
-  const size_t ncb = pl->cbs.size();
+  const size_t ncb = pl->n_cb;
   const uint32_t n = pl->info.n_tb;
   const uint8_t* h = (const uint8_t*)pl->h_res.p;
   for (uint32_t t = 0; t < n; t++) {
@@ -516,8 +626,15 @@ int crnt_destroy(crnt_ctx* ctx) {
   cudaSetDevice(ctx->device);
   serving_stop(ctx);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  delete ctx->cached;
-  ctx->cached = nullptr;
+  for (int c = 0; c < crnt_ctx::kBatchChunks; c++) {
+    if (ctx->chunk_stream[c]) {
+      cudaStreamSynchronize(ctx->chunk_stream[c]);
+      cudaStreamDestroy(ctx->chunk_stream[c]);
+    }
+    if (ctx->chunk_ev[c]) cudaEventDestroy(ctx->chunk_ev[c]);
+    delete ctx->cached[c];
+    ctx->cached[c] = nullptr;
+  }
   ctx->stage_in.release();
   ctx->stage_out.release();
   if (ctx->xpowA) cudaFree(ctx->xpowA);
@@ -590,43 +707,107 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   cudaSetDevice(ctx->device);
   const bool llr_dev = is_device_ptr(llr), out_dev = is_device_ptr(out);
   std::lock_guard<std::mutex> lk(ctx->stage_mu);
-  cudaStream_t s = ctx->stream;
-  if (!ctx->cached) {
-    ctx->cached = new (std::nothrow) crnt_plan;
-    if (!ctx->cached) return CRNT_ENOMEM;
+  constexpr int NC = crnt_ctx::kBatchChunks;
+  // Chunks of about 15 %, 40 % and 45 % of the TBs (one chunk for small
+  // batches): the device starts on the first chunk while the host plans the
+  // next ones and their LLRs are still in flight.  Chunk c runs on its own
+  // stream, so a later chunk's CTAs fill the SMs as an earlier chunk's drain.
+  uint32_t bnd[NC + 1] = {0, n, n, n};
+  int nch = 1;
+  if (n >= 24) {
+    nch = 3;
+    bnd[1] = (15 * n) / 100;
+    bnd[2] = (55 * n) / 100;
   }
-  crnt_plan* plan = ctx->cached;
-  // the host LLRs start moving to the device before the host plans the batch
+  for (int c = 0; c < nch; c++) {
+    if (!ctx->cached[c]) {
+      ctx->cached[c] = new (std::nothrow) crnt_plan;
+      if (!ctx->cached[c]) return CRNT_ENOMEM;
+    }
+    if (!ctx->chunk_stream[c] &&
+        cudaStreamCreateWithFlags(&ctx->chunk_stream[c], cudaStreamNonBlocking) != cudaSuccess)
+      return CRNT_EDEVICE;
+    if (!ctx->chunk_ev[c] &&
+        cudaEventCreateWithFlags(&ctx->chunk_ev[c], cudaEventDisableTiming) != cudaSuccess)
+      return CRNT_EDEVICE;
+  }
+  // byte offsets of each chunk's LLRs and decoded bits
+  int64_t llr_at[NC + 1] = {0, 0, 0, 0}, out_at[NC + 1] = {0, 0, 0, 0};
+  {
+    int64_t lb = 0, ob = 0;
+    int c = 0;
+    for (uint32_t t = 0; t <= n; t++) {
+      while (c <= nch && bnd[c] == t) {
+        llr_at[c] = lb;
+        out_at[c] = ob;
+        c++;
+      }
+      if (t < n) {
+        lb += tbs[t].G;
+        ob += tbs[t].A / 8;
+      }
+    }
+  }
+  // every previous call has completed (this call is synchronous), so the
+  // staging buffers can grow without waiting
   const int8_t* d_llr = llr;
-  uint64_t llr_bytes = 0;
-  for (uint32_t t = 0; t < n; t++) llr_bytes += tbs[t].G;
   if (!llr_dev) {
-    if (ctx->stage_in.n < llr_bytes && cudaStreamSynchronize(s) != cudaSuccess)
-      return CRNT_EDEVICE;
-    if (!ctx->stage_in.ensure(llr_bytes)) return CRNT_ENOMEM;
-    if (cudaMemcpyAsync(ctx->stage_in.p, llr, llr_bytes, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      return CRNT_EDEVICE;
+    if (!ctx->stage_in.ensure((size_t)llr_at[nch])) return CRNT_ENOMEM;
     d_llr = (const int8_t*)ctx->stage_in.p;
-  }
-  int rc = plan_build(ctx, tbs, n, plan, s);
-  if (rc) {
-    cudaStreamSynchronize(s);
-    return rc;
   }
   uint8_t* d_out = out;
   if (!out_dev) {
-    if (!ctx->stage_out.ensure(plan->info.out_bytes)) return CRNT_ENOMEM;
+    if (!ctx->stage_out.ensure((size_t)out_at[nch] + 16)) return CRNT_ENOMEM;
     d_out = (uint8_t*)ctx->stage_out.p;
   }
-  rc = plan_launch(plan, d_llr, d_out, s, nullptr, nullptr, nullptr);
+  // Host-to-device copies share one copy engine in issue order, so chunk c's
+  // LLRs are issued just before its planning (which they overlap) and ahead
+  // of its descriptor upload, not all at once ahead of every upload.
+  auto copy_llrs = [&](int c) {
+    const size_t bytes = (size_t)(llr_at[c + 1] - llr_at[c]);
+    if (llr_dev || bytes == 0) return true;
+    return cudaMemcpyAsync((int8_t*)ctx->stage_in.p + llr_at[c], llr + llr_at[c], bytes,
+                           cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess &&
+           cudaEventRecord(ctx->chunk_ev[c], ctx->stream) == cudaSuccess;
+  };
+  int rc = CRNT_OK;
+  int launched = 0;
+  for (int c = 0; c < nch && rc == CRNT_OK; c++) {
+    const uint32_t t0 = bnd[c], m = bnd[c + 1] - bnd[c];
+    if (m == 0) continue;
+    cudaStream_t s = ctx->chunk_stream[c];
+    crnt_plan* plan = ctx->cached[c];
+    if (!copy_llrs(c)) {
+      rc = CRNT_EDEVICE;
+      break;
+    }
+    rc = plan_build(ctx, tbs + t0, m, plan, s);
+    if (rc) break;
+    if (!llr_dev && llr_at[c + 1] > llr_at[c] &&
+        cudaStreamWaitEvent(s, ctx->chunk_ev[c], 0) != cudaSuccess) {
+      rc = CRNT_EDEVICE;
+      break;
+    }
+    rc = plan_launch(plan, d_llr + llr_at[c], d_out + out_at[c], s, nullptr, nullptr, nullptr,
+                     true);
+    if (rc) break;
+    launched = c + 1;
+    const size_t ob = (size_t)(out_at[c + 1] - out_at[c]);
+    if ((!out_dev && ob &&
+         cudaMemcpyAsync(out + out_at[c], d_out + out_at[c], ob, cudaMemcpyDeviceToHost, s) !=
+             cudaSuccess) ||
+        plan_fetch_results(plan, s) != CRNT_OK)
+      rc = CRNT_EDEVICE;
+  }
+  // wait for everything issued, also on failure, before returning
+  bool dev_ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+  for (int c = 0; c < nch; c++)
+    dev_ok = (cudaStreamSynchronize(ctx->chunk_stream[c]) == cudaSuccess) && dev_ok;
   if (rc) return rc;
-  if (!out_dev &&
-      cudaMemcpyAsync(out, d_out, plan->info.out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return CRNT_EDEVICE;
-  if (plan_fetch_results(plan, s) != CRNT_OK || cudaStreamSynchronize(s) != cudaSuccess)
-    return CRNT_EDEVICE;
-  plan_fill_results(plan, res);
+  if (!dev_ok) return CRNT_EDEVICE;
+  for (int c = 0; c < nch; c++) ctx->cached[c]->upload_pending = false;  // streams drained
+  for (int c = 0; c < launched; c++)
+    if (bnd[c + 1] > bnd[c]) plan_fill_results(ctx->cached[c], res + bnd[c]);
   return CRNT_OK;
 }
 

@@ -72,12 +72,18 @@ inline bool segment(int B, Seg* s) {
     s->C = (B + kZ - 24 - 1) / (kZ - 24);
     s->Bp = B + 24 * s->C;
   }
-  int ip = -1;
-  for (int i = 0; i < kNumK; i++)
-    if (s->C * k_of(i) >= s->Bp) {
-      ip = i;
-      break;
-    }
+  // K+ = the smallest table size with C K+ >= B', i.e. K+ >= ceil(B' / C):
+  // round that bound up to the step of its range of the K table
+  const int kmin = (s->Bp + s->C - 1) / s->C;
+  auto up = [](int x, int m) { return (x + m - 1) / m * m; };
+  int kp;
+  if (kmin <= 40) kp = 40;
+  else if (kmin <= 512) kp = up(kmin, 8);
+  else if (kmin <= 1024) kp = up(kmin < 528 ? 528 : kmin, 16);
+  else if (kmin <= 2048) kp = up(kmin < 1056 ? 1056 : kmin, 32);
+  else if (kmin <= kZ) kp = up(kmin < 2112 ? 2112 : kmin, 64);
+  else return false;
+  const int ip = index_of(kp);
   if (ip < 0) return false;
   s->Kp = k_of(ip);
   if (s->C == 1) {

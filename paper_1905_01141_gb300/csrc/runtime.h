@@ -55,6 +55,13 @@ struct HarqPool {
 
 struct Serving;
 
+// Fields of a CB descriptor fixed by (K, requested P) alone.
+struct KTmpl {
+  int32_t K, W, P, divM, divS, f1, f2, f2x2, f2sub, f2jump, R, ND, ncb, slot;
+  uint32_t maskB0, mask2;  // column masks with no filler bits
+  int32_t rank0[4];        // rank of k0 per rv with no filler bits
+};
+
 }  // namespace crnt
 
 struct crnt_ctx {
@@ -67,10 +74,24 @@ struct crnt_ctx {
   std::mutex harq_mu;     // guards harq
   std::mutex stage_mu;    // guards the staging buffers and the cached plan
   crnt::Buf stage_in, stage_out;
-  crnt_plan* cached = nullptr;  // plan reused by crnt_decode_batch
+  // crnt_decode_batch splits a batch into up to kBatchChunks chunks, each
+  // with a reused plan and its own stream, so that planning and copying a
+  // chunk overlap the decoding of the chunks before it
+  static constexpr int kBatchChunks = 3;
+  crnt_plan* cached[kBatchChunks] = {};
+  cudaStream_t chunk_stream[kBatchChunks] = {};
+  cudaEvent_t chunk_ev[kBatchChunks] = {};  // LLR copy of chunk c done
   cudaStream_t stream = nullptr;
   crnt::Serving* serving = nullptr;
   std::mutex serving_mu;
+};
+
+// Per-TB planning record (pass 1 of plan_build).
+struct TbPre {
+  int64_t llr, soft, dbg;   // TB's first LLR byte, soft-buffer base (-1), debug base
+  uint32_t cb0;             // global index of its first CB (TB order)
+  int n_lo, E_lo, E_hi;     // the first n_lo CBs get E_lo rate-matched bits, the rest E_hi
+  crnt::KTmpl tm, tp;       // descriptor templates of K- and K+
 };
 
 // A planned batch.  Its buffers are grow-only, so re-planning a plan object
@@ -78,21 +99,26 @@ struct crnt_ctx {
 struct crnt_plan {
   crnt_ctx* ctx = nullptr;
   std::vector<crnt_tb_params> tbs;
-  std::vector<crnt::CbDesc> cbs;     // sorted (work-item order)
+  std::vector<TbPre> pre;
+  std::vector<uint64_t> keyed;       // sort keys (low bits: CB index in TB order)
+  std::vector<uint32_t> owner;       // CB index in TB order -> TB
   std::vector<int> cb_tb, cb_r;      // sorted index -> (tb, r)
   std::vector<crnt::TbDesc> tdesc;
   std::vector<crnt::WorkItem> items;
   std::vector<crnt::lte::Seg> segs;
   std::vector<uint16_t> p_used;
+  uint32_t n_cb = 0;
   crnt_plan_info info{};
   int smem = 0;
-  crnt::Buf d_desc, d_scratch;       // device: descriptors | per-launch scratch
+  crnt::Buf d_desc, d_scratch;       // device: descriptors + zeroed state | results
   crnt::Buf h_desc{true}, h_res{true};  // pinned: descriptor staging | results
   cudaEvent_t desc_ev = nullptr;     // recorded after the last descriptor upload
+  bool upload_pending = false;       // desc_ev may not have completed yet
+  bool state_fresh = false;          // the zeroed state was just uploaded
   ~crnt_plan() {
     if (desc_ev) cudaEventDestroy(desc_ev);
   }
-  size_t desc_bytes = 0, scratch_zero = 0, res_bytes = 0;
+  size_t desc_bytes = 0, zero_off = 0, scratch_zero = 0, res_bytes = 0;
   crnt::DecParams prm{};
 };
 
@@ -103,8 +129,10 @@ namespace crnt {
 // null means the TBs' LLRs are concatenated in order.
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
                cudaStream_t stream, const int64_t* llr_base = nullptr);
+// state_uploaded: the caller launches right after plan_build, whose upload
+// already zeroed the per-launch state (skips one memset).
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
-                int16_t* dbg_ext, uint8_t* dbg_hard);
+                int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded = false);
 // Enqueue the D2H copy of the per-CB / per-TB results into h_res.
 int plan_fetch_results(crnt_plan* pl, cudaStream_t s);
 // Fill res[n] from h_res (after the stream has passed plan_fetch_results).

@@ -135,7 +135,8 @@ bool Serving::launch(Slot* s, std::vector<Req>&& batch) {
   const size_t out_bytes = s->plan.info.out_bytes;
   if (!s->d_out.ensure(out_bytes) || !s->h_out.ensure(out_bytes)) return false;
   s->t_start = now_ns();
-  if (plan_launch(&s->plan, arena, (uint8_t*)s->d_out.p, s->stream, nullptr, nullptr, nullptr) !=
+  if (plan_launch(&s->plan, arena, (uint8_t*)s->d_out.p, s->stream, nullptr, nullptr, nullptr,
+                  true) !=
           CRNT_OK ||
       cudaMemcpyAsync(s->h_out.p, s->d_out.p, out_bytes, cudaMemcpyDeviceToHost, s->stream) !=
           cudaSuccess ||
@@ -153,6 +154,7 @@ void Serving::harvest(Slot* s, bool failed) {
   if (!failed) {
     s->tmp.resize(n);
     plan_fill_results(&s->plan, s->tmp.data());
+    s->plan.upload_pending = false;  // the slot's event passed the upload
   }
   size_t off = 0;
   for (uint32_t i = 0; i < n; i++) {

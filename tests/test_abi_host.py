@@ -70,6 +70,18 @@ def test_tb_layout_matches_oracle(crnt_lib, orc):
         assert eoff == G
 
 
+def test_segmentation_every_tb_size(crnt_lib, orc):
+    # every TB size the library accepts (A = 16..75376, multiples of 8): the
+    # library's CB sizes and filler count equal the oracle's segmentation
+    for A in range(16, 75377, 8):
+        lay = crnt_lib.tb_layout(dict(A=A, G=6 * (3 * A + 400), Qm=6))
+        s = orc.segment(A + 24)
+        assert len(lay) == s["C"], A
+        for r, c in enumerate(lay):
+            assert c["K"] == (s["Km"] if r < s["Cm"] else s["Kp"]), (A, r)
+            assert c["F"] == (s["F"] if r == 0 else 0), (A, r)
+
+
 def test_invalid_params_rejected(crnt_lib):
     bad = [dict(A=15, G=100), dict(A=17, G=100), dict(A=75384, G=100000), dict(A=100, G=101),
            dict(A=100, G=300, Qm=3), dict(A=100, G=300, rv=4), dict(A=100, G=300, max_iter=0),
