@@ -102,6 +102,21 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Address under which kernels can use p: device and managed memory as is,
+// page-locked host memory (cudaHostAlloc / cudaHostRegister) through its
+// mapped device address -- kernels then read and write it in place over the
+// CPU-GPU link; nullptr for pageable host memory, which must be staged.
+void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return (void*)p;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  return nullptr;
+}
+
 // Column masks of the circular-buffer rank formula (see rm_geom.cuh): bit c
 // of maskB is [P(c) < (ND + F) mod 32], bit c of mask2 is [P(c) < ND - 1],
 // with P the bit-reversal column permutation.  kColsBelow[x] holds the
@@ -705,7 +720,10 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
                       uint8_t* out, crnt_tb_result* res) {
   if (!ctx || !tbs || !llr || !out || !res || n == 0) return CRNT_EINVAL;
   cudaSetDevice(ctx->device);
-  const bool llr_dev = is_device_ptr(llr), out_dev = is_device_ptr(out);
+  // device or page-locked buffers are used in place; pageable ones staged
+  const int8_t* llr_view = (const int8_t*)device_view(llr);
+  uint8_t* out_view = (uint8_t*)device_view(out);
+  const bool llr_dev = llr_view != nullptr, out_dev = out_view != nullptr;
   std::lock_guard<std::mutex> lk(ctx->stage_mu);
   constexpr int NC = crnt_ctx::kBatchChunks;
   // Chunks of about 15 %, 40 % and 45 % of the TBs (one chunk for small
@@ -750,12 +768,12 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   }
   // every previous call has completed (this call is synchronous), so the
   // staging buffers can grow without waiting
-  const int8_t* d_llr = llr;
+  const int8_t* d_llr = llr_view;
   if (!llr_dev) {
     if (!ctx->stage_in.ensure((size_t)llr_at[nch])) return CRNT_ENOMEM;
     d_llr = (const int8_t*)ctx->stage_in.p;
   }
-  uint8_t* d_out = out;
+  uint8_t* d_out = out_view;
   if (!out_dev) {
     if (!ctx->stage_out.ensure((size_t)out_at[nch] + 16)) return CRNT_ENOMEM;
     d_out = (uint8_t*)ctx->stage_out.p;

@@ -161,9 +161,10 @@ def test_full_tti_sampled(orc, crnt_lib, ctx):
 @pytest.mark.parametrize("n_tb", [23, 24, 61])
 def test_decode_batch_chunks_match_one_plan(orc, crnt_lib, ctx, n_tb):
     # crnt_decode_batch splits batches of >= 24 TBs into three chunks on
-    # their own streams; with host or device buffers every TB's bits and
-    # results equal one single-plan launch of the whole batch, which the
-    # other tests hold to the oracle
+    # their own streams; with pageable host buffers (staged), page-locked
+    # host buffers (used in place by the kernel) and device buffers every
+    # TB's bits and results equal one single-plan launch of the whole batch,
+    # which the other tests hold to the oracle
     shapes = synth.tti_batch(seed=17 + n_tb, n_tb=n_tb, amax=40000)
     specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], seed=700 + i, snr=s["snr_db"], max_iter=5,
                   early_stop=i % 2) for i, s in enumerate(shapes)]
@@ -173,14 +174,17 @@ def test_decode_batch_chunks_match_one_plan(orc, crnt_lib, ctx, n_tb):
     nbytes = sum(t["A"] // 8 for t in tbs)
     out_h = np.zeros(nbytes, dtype=np.uint8)
     res_h = ctx.decode_batch(tbs, llr, out_h)
+    out_p = torch.zeros(nbytes, dtype=torch.uint8).pin_memory()
+    res_p = ctx.decode_batch(tbs, torch.from_numpy(llr).pin_memory(), out_p)
     dev = torch.device("cuda")
     out_d = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
     res_d = ctx.decode_batch(tbs, torch.from_numpy(llr).to(dev), out_d)
     assert np.array_equal(out_h, want["out"][:nbytes])
+    assert np.array_equal(out_p.numpy(), want["out"][:nbytes])
     assert np.array_equal(out_d.cpu().numpy(), want["out"][:nbytes])
-    for r_h, r_d, w in zip(res_h, res_d, want["res"]):
-        for k in ("cb_iters", "tb_crc_ok", "C", "Kp", "P_used"):
-            assert r_h[k] == w[k] and r_d[k] == w[k], k
+    for r_h, r_p, r_d, w in zip(res_h, res_p, res_d, want["res"]):
+        for k in ("cb_iters", "cb_crc_ok", "tb_crc_ok", "C", "Kp", "P_used"):
+            assert r_h[k] == w[k] and r_p[k] == w[k] and r_d[k] == w[k], k
 
 
 def test_plan_launch_captured_in_cuda_graph(orc, crnt_lib, ctx):
