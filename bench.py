@@ -403,7 +403,8 @@ def subframe_latency(crnt, ctx, dev):
             "what": "device time of one 20 MHz subframe decode (13 CBs, early stop)"}
 
 
-def serving_leg(crnt, dev, seed, cells_list=(4, 8, 12, 16, 20, 24, 28, 32), seconds=1.5):
+def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 48, 56, 64, 80, 96),
+                seconds=1.5):
     """Serving loop under cell load: every cell submits one subframe (8 UEs,
     TB mix of the TTI workload) per 1 ms period with a random phase and
     +-200 us jitter; ~10 % of TBs are HARQ retransmissions (rv 2) combined in

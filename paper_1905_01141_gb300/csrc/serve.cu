@@ -7,10 +7,12 @@
 // still running on other slots, so work admitted later overlaps on the
 // device with work admitted earlier.  Finished batches are harvested by
 // polling their events; results wait in a done queue for crnt_poll.
-// crnt_submit copies each TB's LLRs straight into a device-resident ring
-// (one DMA per TB, completed before it returns), so the worker only plans and
-// launches.  Admission is by in-flight TB count and by space in that ring
-// (the device memory a request holds while queued or running); beyond
+// crnt_submit copies each TB's LLRs (a CPU memcpy) into a ring of
+// page-locked host memory that the decode kernel reads in place over the
+// CPU-GPU link, and the kernel writes the decoded bits straight into
+// page-locked output buffers, so neither side issues a copy: the worker only
+// plans and launches.  Admission is by in-flight TB count and by space in
+// that ring (the memory a request holds while queued or running); beyond
 // either, crnt_submit returns CRNT_EAGAIN.  Waits are bounded: the worker sleeps on a condition variable
 // with a timeout and crnt_poll honours its timeout.
 #include <cuda_runtime.h>
@@ -37,13 +39,13 @@ constexpr uint32_t kMaxBatchTbs = 1024;
 struct Req {
   uint64_t ticket;
   crnt_tb_params tb;
-  int64_t llr_off;   // byte offset of its LLRs in the device ring
+  int64_t llr_off;   // byte offset of its LLRs in the LLR ring
   uint64_t alloc;    // allocation sequence number (ring release order)
   int64_t t_submit;
 };
 
-// Ring of device memory holding the LLRs of queued and running requests,
-// released in allocation order.  Each allocation is contiguous.
+// Ring holding the LLRs of queued and running requests, released in
+// allocation order.  Each allocation is contiguous.
 struct Ring {
   size_t cap = 0, head = 0, tail = 0;
   struct A {
@@ -91,8 +93,7 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   crnt_plan plan;
-  Buf d_out;
-  Buf h_out{true};
+  Buf h_out{true};  // page-locked; the kernel writes the decoded bits here
   std::vector<Req> reqs;
   std::vector<crnt_tb_result> tmp;
   bool busy = false;
@@ -112,10 +113,9 @@ struct Serving {
   uint64_t next_ticket = 1;
   uint64_t inflight_tbs = 0;  // queued + running
   int device_error = 0;
-  int8_t* arena = nullptr;    // device LLR ring
+  int8_t* arena = nullptr;    // page-locked LLR ring (host address)
+  int8_t* arena_dev = nullptr;  // the same ring as kernels address it
   Ring ring;
-  cudaStream_t cstream = nullptr;  // submit-side copies
-  std::mutex copy_mu;
 
   void run();
   bool launch(Slot* s, std::vector<Req>&& batch);
@@ -133,13 +133,12 @@ bool Serving::launch(Slot* s, std::vector<Req>&& batch) {
   }
   if (plan_build(ctx, tbs.data(), n, &s->plan, s->stream, base.data()) != CRNT_OK) return false;
   const size_t out_bytes = s->plan.info.out_bytes;
-  if (!s->d_out.ensure(out_bytes) || !s->h_out.ensure(out_bytes)) return false;
+  if (!s->h_out.ensure(out_bytes)) return false;
+  uint8_t* out_dev = nullptr;
+  if (cudaHostGetDevicePointer((void**)&out_dev, s->h_out.p, 0) != cudaSuccess) return false;
   s->t_start = now_ns();
-  if (plan_launch(&s->plan, arena, (uint8_t*)s->d_out.p, s->stream, nullptr, nullptr, nullptr,
-                  true) !=
+  if (plan_launch(&s->plan, arena_dev, out_dev, s->stream, nullptr, nullptr, nullptr, true) !=
           CRNT_OK ||
-      cudaMemcpyAsync(s->h_out.p, s->d_out.p, out_bytes, cudaMemcpyDeviceToHost, s->stream) !=
-          cudaSuccess ||
       plan_fetch_results(&s->plan, s->stream) != CRNT_OK ||
       cudaEventRecord(s->ev, s->stream) != cudaSuccess)
     return false;
@@ -239,11 +238,11 @@ static Serving* serving_get(crnt_ctx* ctx) {
   if (!sv) return nullptr;
   sv->ctx = ctx;
   cudaSetDevice(ctx->device);
-  sv->ring.cap = (size_t)std::min<uint64_t>(ctx->cfg.mem_budget / 4, 1ull << 30);
-  if (cudaMalloc(&sv->arena, sv->ring.cap) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&sv->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+  sv->ring.cap = (size_t)std::min<uint64_t>(ctx->cfg.mem_budget / 8, 256ull << 20);
+  if (cudaHostAlloc((void**)&sv->arena, sv->ring.cap, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&sv->arena_dev, sv->arena, 0) != cudaSuccess) {
     cudaGetLastError();
-    if (sv->arena) cudaFree(sv->arena);
+    if (sv->arena) cudaFreeHost(sv->arena);
     return nullptr;
   }
   for (int i = 0; i < kSlots; i++) {
@@ -277,8 +276,7 @@ void serving_stop(crnt_ctx* ctx) {
     if (s->ev) cudaEventDestroy(s->ev);
     if (s->stream) cudaStreamDestroy(s->stream);
   }
-  if (sv->cstream) cudaStreamDestroy(sv->cstream);
-  if (sv->arena) cudaFree(sv->arena);
+  if (sv->arena) cudaFreeHost(sv->arena);
   delete sv;
 }
 
@@ -320,20 +318,9 @@ int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* l
     }
     sv->inflight_tbs += n;
   }
-  {
-    // the LLRs reach the device before the requests become visible
-    std::lock_guard<std::mutex> lk(sv->copy_mu);
-    bool ok = true;
-    for (uint32_t i = 0; i < n && ok; i++)
-      ok = cudaMemcpyAsync(sv->arena + reqs[i].llr_off, llrs[i], tbs[i].G, cudaMemcpyHostToDevice,
-                           sv->cstream) == cudaSuccess;
-    if (!ok || cudaStreamSynchronize(sv->cstream) != cudaSuccess) {
-      std::lock_guard<std::mutex> lk2(sv->mu);
-      for (uint32_t i = 0; i < n; i++) sv->ring.release(reqs[i].alloc);
-      sv->inflight_tbs -= n;
-      return CRNT_EDEVICE;
-    }
-  }
+  // the LLRs are in the ring before the requests become visible (the
+  // worker's launch, which reads them, follows the publication below)
+  for (uint32_t i = 0; i < n; i++) memcpy(sv->arena + reqs[i].llr_off, llrs[i], tbs[i].G);
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     for (uint32_t i = 0; i < n; i++) {
