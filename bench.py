@@ -334,6 +334,8 @@ def run_ours(args):
         line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
         line["serving"] = serving_leg(crnt, dev, args.seed)
+        line["single_cb"] = single_cb_config(crnt, ctx, dev)
+        line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(shapes, args.seed)
     plan.close()
@@ -507,9 +509,87 @@ def cpu_baseline(shapes, seed):
     oracle, items = oracle_sample_decoder(shapes[:96], seed)
     with cf.ThreadPoolExecutor(max_workers=cores) as pool:
         bits, secs, n, _ = oracle_run(oracle, items, 15.0, pool)
+    with cf.ThreadPoolExecutor(max_workers=1) as pool:
+        bits1, secs1, n1, _ = oracle_run(oracle, items, 5.0, pool)
     return {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
             "sample": "%d TBs of the TTI workload (first 96 shapes, cycled), 6 iterations, "
-                      "thread pool of %d, %.1f s" % (n, cores, secs)}
+                      "thread pool of %d, %.1f s" % (n, cores, secs),
+            "single_core": {"value": bits1 / secs1 / 1e9, "unit": "Gbit/s",
+                            "sample": "%d TBs on one thread, %.1f s" % (n1, secs1)}}
+
+
+def single_cb_config(crnt, ctx, dev, n_batch=1024):
+    """The single-code-block configuration: A = 6120 (one K = 6144 CB),
+    rate 1/3 (E = 18444), BPSK at Eb/N0 = 1 dB, at most 6 iterations.
+    Reports the device latency of one CB alone (P = 1 and P = 128, early
+    stop on) and the throughput of a batch of n_batch such CBs with
+    different seeds (P autotuned, exactly 6 iterations)."""
+    import torch
+    A, G = 6120, 18444
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    sig = synth.sigma2_ebn0(1.0, A / G)
+    coded = np.zeros(G * n_batch, dtype=np.uint8)
+    tbs = [dict(A=A, G=G, Qm=2, P=0, max_iter=6, early_stop=0) for _ in range(n_batch)]
+    pay = np.concatenate([np.packbits(synth.bits(31, t, A)) for t in range(n_batch)])
+    ctx.encode_batch(tbs, pay, coded)
+    llr = synth.channel_llrs(coded, 1, sig, 31, 0)
+    ld = torch.from_numpy(llr).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for P in (1, 128):
+        plan = ctx.plan([dict(A=A, G=G, Qm=2, P=P, max_iter=6, early_stop=1)])
+        od = torch.zeros(A // 8, dtype=torch.uint8, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(20)]
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                a.record(stream)
+                plan.launch(ld, od, stream.cuda_stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        res = plan.results(stream.cuda_stream)
+        out["latency_P%d_us" % P] = ms[len(ms) // 2] * 1e3
+        out["iterations_P%d" % P] = res[0]["cb_iters"][0]
+        plan.close()
+    plan = ctx.plan(tbs)
+    od = torch.zeros(plan.info["out_bytes"], dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(20)]
+    with torch.cuda.stream(stream):
+        plan.launch(ld, od, stream.cuda_stream)
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            plan.launch(ld, od, stream.cuda_stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    res = plan.results(stream.cuda_stream)
+    out["batch"] = {"cbs": n_batch, "ms": ms, "gbit_s": A * n_batch / (ms * 1e-3) / 1e9,
+                    "crc_ok_fraction": sum(r["tb_crc_ok"] for r in res) / n_batch,
+                    "l2": "flushed (256 MiB write) before every timed launch"}
+    plan.close()
+    return out
+
+
+def encoder_rate(crnt, ctx, dev, tbs, pay):
+    """Downlink encoder + rate matcher (crnt_encode_batch, device buffers) on
+    the TTI workload: wall time per call, including host planning."""
+    import torch
+    pd = torch.from_numpy(pay).to(dev)
+    ed = torch.zeros(sum(t["G"] for t in tbs), dtype=torch.uint8, device=dev)
+    ctx.encode_batch(tbs, pd, ed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 50
+    for _ in range(k):
+        ctx.encode_batch(tbs, pd, ed)
+    dt = (time.perf_counter() - t0) / k
+    bits = sum(t["A"] for t in tbs)
+    return {"gbit_s": bits / dt / 1e9, "ms_per_call": dt * 1e3, "tbs": len(tbs),
+            "what": "crnt_encode_batch on the TTI workload (CRC, segmentation, turbo "
+                    "encoding, rate matching), device buffers, wall time incl. planning"}
 
 
 def bler_sweep(args):

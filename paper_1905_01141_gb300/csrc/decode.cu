@@ -225,14 +225,13 @@ __device__ __forceinline__ void unpack8(uint4 r, int v[8]) {
 }
 
 // ---------------------------------------------------------------- helpers
+// (x + y) mod K for x in [0, K), y in [0, K]: the unsigned minimum of x + y
+// (no overflow: below 2K) and x + y - K (wraps to a large unsigned value when
+// negative), as one add and one DPX add-min.  (x - y) mod K is x + (K - y).
 __device__ __forceinline__ int modadd(int x, int y, int K) {
-  const unsigned s = (unsigned)(x + y);
-  return (int)min(s, s - (unsigned)K);
+  return (int)__viaddmin_u32((unsigned)x, (unsigned)y, (unsigned)(x + y - K));
 }
-__device__ __forceinline__ int modsub(int x, int y, int K) {
-  const unsigned s = (unsigned)(x - y);
-  return (int)min(s, s + (unsigned)K);
-}
+__device__ __forceinline__ int modsub(int x, int y, int K) { return modadd(x, K - y, K); }
 __device__ __forceinline__ int qpp_at(int x, int f1, int f2, int K) {
   int t = (f2 * x) % K;
   t = (t * x) % K;
@@ -454,14 +453,16 @@ __device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, 
 // Backward processing of one sub-window [j0, j0 + slen) of a window:
 // recompute forward metrics from the checkpoint into registers, then walk
 // back computing Lambda / Le and the backward metrics.  FULL: slen == kSub
-// (no per-step guards).  mx tracks the largest |extrinsic| written.  With
+// (no per-step guards).  mx / mn track the largest / smallest extrinsic
+// written.  With
 // w.hard_on (DEC 1 only) the hard decisions sign(Lambda) are also recorded
 // at the natural positions.
 template <int DEC, bool FULL, bool CHK>
 __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
-                                                int dq, int b[8], int& mx) {
+                                                int dq, int b[8], int& mx, int& mn) {
   int A[kSub][8];
   int Sv[kSub], Lv[kSub], Qv[kSub];
+  int vprev = 0;  // extrinsics enter the max / min tracking in pairs
   unpack8(ck, A[0]);
 #pragma unroll
   for (int jj = 0; jj < kSub; jj++) {
@@ -480,7 +481,12 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
       int lam;
       const int le = app_step<CHK>(A[jj], b, S, Lp, &lam);
       const int v = scale_ext(le);
-      mx = __vimax3_s32(mx, v, -v);
+      if (jj & 1) {
+        vprev = v;
+      } else {
+        mx = __vimax3_s32(mx, vprev, v);
+        mn = __vimin3_s32(mn, vprev, v);
+      }
       w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : tr_w(w, Qv[jj])] = (int16_t)v;
       if (DEC == 1 && w.hard_on) {  // branch-free: ORs a zero when lam >= 0
         const int qq = Qv[jj] + w.pad;
@@ -495,7 +501,7 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
 template <int DEC, bool CHK>
 __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restrict__ dp,
                                             uint4* ck, uint4* seedA, uint4* seedB, int a[8],
-                                            int b[8], int& mx) {
+                                            int b[8], int& mx, int& mn) {
   const int K = w.K, P = w.P, p = w.p, lo = w.lo, len = w.len;
   const int f1 = dp->f1, f2 = dp->f2;
   const int f2sub = DEC ? dp->f2sub : 0, f2jump = DEC ? dp->f2jump : 0;
@@ -548,7 +554,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
   int sw = nsub - 1;
   const int last_len = len - kSub * sw;
   if (last_len < kSub) {
-    sub_window_back<DEC, false, CHK>(w, ck[sw], kSub * sw, last_len, pis, dls, b, mx);
+    sub_window_back<DEC, false, CHK>(w, ck[sw], kSub * sw, last_len, pis, dls, b, mx, mn);
     if (DEC == 1) {
       pis = modsub(pis, jmp, K);
       dls = modsub(dls, f2sub, K);
@@ -557,7 +563,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     sw--;
   }
   for (; sw >= 0; sw--) {
-    sub_window_back<DEC, true, CHK>(w, ck[sw], kSub * sw, kSub, pis, dls, b, mx);
+    sub_window_back<DEC, true, CHK>(w, ck[sw], kSub * sw, kSub, pis, dls, b, mx, mn);
     if (DEC == 1) {
       pis = modsub(pis, jmp, K);
       dls = modsub(dls, f2sub, K);
@@ -636,12 +642,12 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
 #pragma unroll
       for (int j = 2; j >= 0; j--) beta_tail_step(b, t[2 * j], t[2 * j + 1]);
     }
-    int mx = 0;
+    int mx = 0, mn = 0;
     if (window_fast(a, b, 254 + m_in))
-      window_pass<DEC, false>(w, dp, ck, seedA, seedB, a, b, mx);
+      window_pass<DEC, false>(w, dp, ck, seedA, seedB, a, b, mx, mn);
     else
-      window_pass<DEC, true>(w, dp, ck, seedA, seedB, a, b, mx);
-    atomicMax(&sl.flags[4 + DEC], mx);
+      window_pass<DEC, true>(w, dp, ck, seedA, seedB, a, b, mx, mn);
+    atomicMax(&sl.flags[4 + DEC], max(mx, -mn));
   }
   __syncthreads();
 }
