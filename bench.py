@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in window counts instead of the autotuned table")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
     ap.add_argument("--sweep", choices=["bler"], help="quality sweep instead of the bench line")
     ap.add_argument("--bler-cbs", type=int, default=0,
@@ -245,6 +247,18 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     crnt_build.build()
     ctx = crnt.Context(local)
+    tune = None
+    if not args.no_autotune:
+        # window counts per K picked by measurement (outside the timed region)
+        t0 = time.perf_counter()
+        table = ctx.autotune(32)
+        ks = (list(range(40, 513, 8)) + list(range(528, 1025, 16)) + list(range(1056, 2049, 32))
+              + list(range(2112, 6145, 64)))  # the 188 CB sizes, in table order
+        builtin = [max(1, min(k // 8, 128, -(-k // 48))) for k in ks]
+        tune = {"w_min": 32, "seconds": round(time.perf_counter() - t0, 2),
+                "entries_changed_from_builtin": sum(int(a != b) for a, b in zip(table, builtin)),
+                "P_at_K": {str(k): p for k, p in zip(ks, table)
+                           if k in (40, 256, 512, 1024, 2048, 4096, 5824, 5888, 6016, 6144)}}
 
     # ---- workload: this rank's TTI (weak scaling: each rank serves its own
     # cells -- replicas, no collective on the data path)
@@ -325,6 +339,7 @@ def run_ours(args):
                        "info_bits_per_step": info["info_bits"], "llr_bytes": info["llr_bytes"],
                        "work_items": info["n_items"], "grid": info["grid"],
                        "l2": "flushed (256 MiB write) before every timed step",
+                       "autotune": tune,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
             "wall_s_timed_region": t_wall, "tb_crc_ok_fraction": ok_frac,

@@ -133,6 +133,26 @@ int crnt_qpp_params(uint32_t K, uint32_t* f1, uint32_t* f2);
  * as described at crnt_tb_params; CRNT_EINVAL otherwise. */
 int crnt_tb_layout(const crnt_tb_params* tb, crnt_cb_layout* cbs, uint32_t* C);
 
+/* ---- window-count table (autotuner) ----------------------------------- */
+/* A TB that asks for P = 0 gets, for each CB size K, the window count of a
+ * process-wide table shared by every context: entry i holds P for the i-th
+ * of the CRNT_NUM_K CB sizes in increasing order (40, 48, ..., 6144); 0
+ * selects the built-in choice (windows of about 48 trellis steps).  Entries
+ * are clamped like a requested P.  The window count changes the decoded
+ * values (window seeds, Sec. IV-B parallelisation over P), so a table fixes
+ * the results of P = 0 requests; crnt_tb_layout reports it.  The paper has no
+ * tuner: its thread counts are configured by hand. */
+#define CRNT_NUM_K 188
+int crnt_tune_get(uint8_t* P_by_k, uint32_t n);       /* copies min(n, 188) entries */
+int crnt_tune_set(const uint8_t* P_by_k, uint32_t n); /* n must be 188 */
+/* Measure on ctx's GPU the batched decode throughput (6 iterations, full
+ * batches of single-CB TBs per K) of candidate window counts for every CB
+ * size, keep for each K the fastest whose windows are at least w_min
+ * trellis steps long (0 = 32; smaller windows cost BLER), install the table
+ * and copy it to P_by_k (188 entries, may be NULL).  Blocking; takes a few
+ * seconds; allocates device memory for its inputs and frees it. */
+int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k);
+
 /* ---- context ---------------------------------------------------------- */
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates the
  * HARQ soft-buffer arena lazily.  CRNT_EDEVICE if CUDA is unusable. */

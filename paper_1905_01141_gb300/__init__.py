@@ -99,6 +99,9 @@ SIGNATURES = {
     "crnt_poll": (ctypes.c_int, [_P, _P, _P, _U32, _U32]),
     "crnt_harq_release": (ctypes.c_int, [_P, _U32, _U32, _U32]),
     "crnt_decode_batch_static": (ctypes.c_int, [_P, _U32, _P, _P, _P, _P]),
+    "crnt_tune_get": (ctypes.c_int, [_P, _U32]),
+    "crnt_tune_set": (ctypes.c_int, [_P, _U32]),
+    "crnt_autotune": (ctypes.c_int, [_P, _U32, _P]),
 }
 
 
@@ -182,6 +185,22 @@ def tb_layout(tb):
     return [{k: getattr(cbs[r], k) for k in keys} for r in range(C.value)]
 
 
+NUM_K = 188
+
+
+def tune_get():
+    """The process-wide window-count table (188 entries, 0 = built-in)."""
+    t = (ctypes.c_uint8 * NUM_K)()
+    _check(load().crnt_tune_get(t, NUM_K), "crnt_tune_get")
+    return list(t)
+
+
+def tune_set(table):
+    """Install a window-count table (188 entries, 0 = built-in)."""
+    t = (ctypes.c_uint8 * NUM_K)(*table)
+    _check(load().crnt_tune_set(t, NUM_K), "crnt_tune_set")
+
+
 class Context:
     """A library context on one CUDA device."""
 
@@ -192,6 +211,12 @@ class Context:
         h = ctypes.c_void_p()
         _check(L.crnt_create(ctypes.byref(h), ctypes.byref(cfg)), "crnt_create")
         self.h = h
+
+    def autotune(self, w_min=0):
+        """crnt_autotune: measure and install the window-count table; returns it."""
+        t = (ctypes.c_uint8 * NUM_K)()
+        _check(load().crnt_autotune(self.h, w_min, t), "crnt_autotune")
+        return list(t)
 
     def close(self):
         if self.h:

@@ -84,14 +84,6 @@ bool find_divider(int W, int qmax, int* M, int* s) {
   return true;
 }
 
-// Window count for a CB of size K: the caller's P clamped to [1, K/8] and
-// [1, CRNT_MAX_P]; P = 0 picks windows of about 48 trellis steps.
-int clamp_p(int K, int P) {
-  if (P <= 0) P = (K + 47) / 48;
-  P = std::min(P, K / 8);
-  P = std::min(P, (int)CRNT_MAX_P);
-  return std::max(P, 1);
-}
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -191,6 +183,27 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Process-wide window-count table (crnt_tune_set / crnt_autotune).
+std::atomic<uint8_t> g_tuned[lte::kNumK];
+
+int tuned_p(int K) {
+  const int ki = lte::index_of(K);
+  return ki < 0 ? 0 : (int)g_tuned[ki].load(std::memory_order_relaxed);
+}
+
+// Window count for a CB of size K: the caller's P clamped to [1, K/8] and
+// [1, CRNT_MAX_P]; P = 0 takes the table's entry, else windows of about 48
+// trellis steps.
+int clamp_p(int K, int P) {
+  if (P <= 0) {
+    P = tuned_p(K);
+    if (P <= 0) P = (K + 47) / 48;
+  }
+  P = std::min(P, K / 8);
+  P = std::min(P, (int)CRNT_MAX_P);
+  return std::max(P, 1);
+}
+
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(
              std::chrono::steady_clock::now().time_since_epoch())
@@ -232,18 +245,21 @@ bool make_tmpl(int K, int Preq, KTmpl* t) {
   return true;
 }
 
-// Templates of the autotuned window count (P request 0), filled on first use.
+// Templates of the P = 0 window count (table entry or built-in), filled on
+// first use and rebuilt when the table entry changes (ready holds the window
+// count the template was built for).
 const KTmpl* auto_tmpl(int K) {
   static std::mutex mu;
   static KTmpl table[lte::kNumK];
   static std::atomic<int> ready[lte::kNumK];
   const int ki = lte::index_of(K);
   if (ki < 0) return nullptr;
-  if (!ready[ki].load(std::memory_order_acquire)) {
+  const int want = clamp_p(K, 0);
+  if (ready[ki].load(std::memory_order_acquire) != want) {
     std::lock_guard<std::mutex> lk(mu);
-    if (!ready[ki].load(std::memory_order_relaxed)) {
-      if (!make_tmpl(K, 0, &table[ki])) return nullptr;
-      ready[ki].store(1, std::memory_order_release);
+    if (ready[ki].load(std::memory_order_relaxed) != want) {
+      if (!make_tmpl(K, want, &table[ki])) return nullptr;
+      ready[ki].store(want, std::memory_order_release);
     }
   }
   return &table[ki];

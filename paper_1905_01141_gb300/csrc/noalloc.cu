@@ -68,6 +68,7 @@ uint16_t h_pused[kStaticTbs];
 uint8_t h_res[kResBytes];
 
 int clamp_windows(int K, int P) {
+  if (P <= 0) P = tuned_p(K);  // the process-wide table (a read, no allocation)
   if (P <= 0) P = (K + 47) / 48;
   P = std::min(P, K / 8);
   P = std::min(P, (int)CRNT_MAX_P);

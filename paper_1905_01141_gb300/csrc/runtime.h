@@ -138,6 +138,10 @@ int plan_fetch_results(crnt_plan* pl, cudaStream_t s);
 // Fill res[n] from h_res (after the stream has passed plan_fetch_results).
 void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res);
 int validate(const crnt_tb_params& t, lte::Seg* seg);
+// Window count of the process-wide table for CB size K (0 = built-in).
+int tuned_p(int K);
+// Window count used for CB size K when a TB requests P (0 = table / built-in).
+int clamp_p(int K, int P);
 void serving_stop(crnt_ctx* ctx);
 int64_t now_ns();
 }  // namespace crnt

@@ -1,0 +1,153 @@
+// tune.cu -- the window-count autotuner and the process-wide table it fills.
+//
+// For each of the 188 CB sizes K the tuner decodes full batches of
+// single-CB TBs (A = K - 24, rate 1/3, 6 iterations, no early stop) with a
+// few candidate window counts P and keeps the fastest whose windows are at
+// least w_min trellis steps long.  The decode work does not depend on the
+// LLR values on the clamp-free path, so the inputs are zeros.  Candidates:
+// minimum window lengths w in {w_lo, 32, 40, 48, 56, 64, 80, 96} (w_lo: the
+// shortest allowed, which also uses the most threads), each giving
+// P = floor(K / w) windows of ceil(K / P) >= w steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <vector>
+
+#include "runtime.h"
+
+namespace crnt {
+extern std::atomic<uint8_t> g_tuned[lte::kNumK];
+
+namespace {
+
+// Decode time (ms, mean of 3 launches after one warm-up) of n single-CB TBs
+// of size K with window request P.
+int time_batch(crnt_ctx* ctx, crnt_plan* plan, int K, int P, int n, int8_t* d_llr,
+               uint8_t* d_out, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  crnt_tb_params t;
+  memset(&t, 0, sizeof t);
+  t.A = (uint32_t)(K - 24);
+  t.G = (uint32_t)(3 * K + 12);
+  t.Qm = 2;
+  t.NL = 1;
+  t.P = (uint16_t)P;
+  t.max_iter = 6;
+  t.early_stop = 0;
+  t.new_data = 1;
+  std::vector<crnt_tb_params> tbs((size_t)n, t);
+  int rc = plan_build(ctx, tbs.data(), (uint32_t)n, plan, ctx->stream);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  if (plan_launch(plan, d_llr, d_out, s, nullptr, nullptr, nullptr, true) != CRNT_OK)
+    return CRNT_EDEVICE;
+  if (cudaEventRecord(e0, s) != cudaSuccess) return CRNT_EDEVICE;
+  for (int r = 0; r < 3; r++)
+    if (plan_launch(plan, d_llr, d_out, s, nullptr, nullptr, nullptr) != CRNT_OK)
+      return CRNT_EDEVICE;
+  if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+    return CRNT_EDEVICE;
+  *ms /= 3.0f;
+  return cudaStreamSynchronize(s) == cudaSuccess ? CRNT_OK : CRNT_EDEVICE;
+}
+
+}  // namespace
+}  // namespace crnt
+
+using namespace crnt;
+
+extern "C" {
+
+int crnt_tune_get(uint8_t* P_by_k, uint32_t n) {
+  if (!P_by_k) return CRNT_EINVAL;
+  for (uint32_t i = 0; i < n && i < (uint32_t)lte::kNumK; i++)
+    P_by_k[i] = g_tuned[i].load(std::memory_order_relaxed);
+  return CRNT_OK;
+}
+
+int crnt_tune_set(const uint8_t* P_by_k, uint32_t n) {
+  if (!P_by_k || n != (uint32_t)lte::kNumK) return CRNT_EINVAL;
+  for (int i = 0; i < lte::kNumK; i++) {
+    if (P_by_k[i] > CRNT_MAX_P) return CRNT_EINVAL;
+  }
+  for (int i = 0; i < lte::kNumK; i++) g_tuned[i].store(P_by_k[i], std::memory_order_relaxed);
+  return CRNT_OK;
+}
+
+int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
+  if (!ctx) return CRNT_EINVAL;
+  if (w_min == 0) w_min = 32;
+  if (w_min > (uint32_t)lte::kZ) return CRNT_EINVAL;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->stage_mu);
+  // candidates per K, and per candidate a batch of two CBs per resident
+  // thread slot (two waves of CTAs), at most 64 MiB of LLRs
+  struct Cand {
+    int K, P, n;
+    float rate;
+  };
+  std::vector<std::vector<Cand>> cands(lte::kNumK);
+  const size_t slots = (size_t)kCtasPerSm * ctx->num_sms;
+  size_t max_llr = 0, max_out = 0;
+  for (int i = 0; i < lte::kNumK; i++) {
+    const int K = lte::k_of(i);
+    const int pmax = std::max(1, std::min(K / 8, (int)CRNT_MAX_P));
+    const int w_lo = std::max((int)w_min, (K + pmax - 1) / pmax);
+    const int ws[] = {w_lo, 32, 40, 48, 56, 64, 80, 96};
+    for (int w : ws) {
+      if (w < w_lo) continue;
+      const int P = clamp_p(K, std::max(1, K / w));  // windows of >= w steps
+      bool dup = false;
+      for (const Cand& c : cands[i]) dup |= c.P == P;
+      if (dup) continue;
+      const int W = (K + P - 1) / P;
+      const int slot = align16(dec_cb_smem(K, (K + W - 1) / W, W));
+      const int g = std::max(1, std::min(kThreads / P, kSmemBudget / slot));
+      size_t n = 2 * slots * (size_t)g;
+      n = std::min(n, (size_t)(64u << 20) / (size_t)(3 * K + 12));
+      cands[i].push_back(Cand{K, P, (int)n, 0.0f});
+      max_llr = std::max(max_llr, n * (size_t)(3 * K + 12));
+      max_out = std::max(max_out, n * (size_t)((K - 24) / 8) + 16);
+    }
+  }
+  int8_t* d_llr = nullptr;
+  uint8_t* d_out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = CRNT_OK;
+  if (cudaMalloc(&d_llr, max_llr) != cudaSuccess || cudaMalloc(&d_out, max_out) != cudaSuccess ||
+      cudaMemset(d_llr, 0, max_llr) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = CRNT_ENOMEM;
+  uint8_t table[lte::kNumK];
+  memset(table, 0, sizeof table);
+  {
+    crnt_plan plan;  // re-planned per candidate; its buffers only grow
+    for (int i = 0; i < lte::kNumK && rc == CRNT_OK; i++) {
+      float best = 0.0f;
+      for (Cand& c : cands[i]) {
+        float ms = 0.0f;
+        rc = time_batch(ctx, &plan, c.K, c.P, c.n, d_llr, d_out, e0, e1, &ms);
+        if (rc) break;
+        c.rate = (float)c.n * (float)c.K / ms;
+        best = std::max(best, c.rate);
+      }
+      // the longest windows among the candidates within 1 % of the fastest
+      int pick = 0;
+      for (const Cand& c : cands[i])
+        if (c.rate >= 0.99f * best && (!pick || c.P < pick)) pick = c.P;
+      table[i] = (uint8_t)pick;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_llr) cudaFree(d_llr);
+  if (d_out) cudaFree(d_out);
+  if (rc) return rc;
+  for (int i = 0; i < lte::kNumK; i++) g_tuned[i].store(table[i], std::memory_order_relaxed);
+  if (P_by_k) memcpy(P_by_k, table, sizeof table);
+  return CRNT_OK;
+}
+
+}  // extern "C"

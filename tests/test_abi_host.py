@@ -90,3 +90,28 @@ def test_invalid_params_rejected(crnt_lib):
         with pytest.raises(crnt_lib.CrntError) as ei:
             crnt_lib.tb_layout(b)
         assert ei.value.code == crnt_lib.EINVAL
+
+
+def test_tune_table_drives_p0_windows(crnt_lib):
+    # the process-wide window table: P = 0 requests take its entry for their
+    # K (clamped like a requested P); explicit P ignores it; 0 = built-in
+    ks = [crnt_lib.tb_layout(dict(A=6120, G=18444))[0]["K"]]
+    assert ks == [6144]
+    old = crnt_lib.tune_get()
+    try:
+        t = [0] * crnt_lib.NUM_K
+        t[-1] = 100                       # K = 6144
+        t[0] = 9                          # K = 40: clamped to K / 8 = 5
+        crnt_lib.tune_set(t)
+        assert crnt_lib.tune_get() == t
+        assert crnt_lib.tb_layout(dict(A=6120, G=18444))[0]["P"] == 100
+        assert crnt_lib.tb_layout(dict(A=6120, G=18444, P=64))[0]["P"] == 64
+        assert crnt_lib.tb_layout(dict(A=16, G=132))[0]["P"] == 5
+        with pytest.raises(crnt_lib.CrntError):
+            crnt_lib.tune_set([200] * crnt_lib.NUM_K)
+        arr = (ctypes.c_uint8 * 10)()
+        assert crnt_lib.load().crnt_tune_set(arr, 10) == crnt_lib.EINVAL
+        crnt_lib.tune_set([0] * crnt_lib.NUM_K)
+        assert crnt_lib.tb_layout(dict(A=6120, G=18444))[0]["P"] == 128
+    finally:
+        crnt_lib.tune_set(old)

@@ -214,3 +214,26 @@ def test_plan_launch_captured_in_cuda_graph(orc, crnt_lib, ctx):
     assert torch.equal(out_graph, out_direct)
     assert [r["cb_iters"] for r in got] == [r["cb_iters"] for r in want]
     plan.close()
+
+
+def test_autotuned_windows_match_oracle(orc, crnt_lib, ctx):
+    # the autotuner installs a window count per K (windows of >= 32 steps
+    # where K allows); P = 0 TBs then decode with it, still bit-exact with
+    # the oracle run at the same window counts
+    old = crnt_lib.tune_get()
+    try:
+        table = ctx.autotune(32)
+        assert table == crnt_lib.tune_get()
+        ks = list(orc.k_table())
+        assert len(ks) == len(table) == 188
+        for K, P in zip(ks, table):
+            assert 1 <= P <= min(128, max(1, K // 8)), (K, P)
+            assert -(-K // P) >= min(32, K), (K, P)
+        shapes = synth.tti_batch(seed=23, n_tb=16, amax=40000)
+        specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=6, seed=800 + i,
+                      snr=s["snr_db"]) for i, s in enumerate(shapes)]
+        tbs, llrs = batch(orc, specs)
+        g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+        check_batch(orc, crnt_lib, tbs, llrs, g)
+    finally:
+        crnt_lib.tune_set(old)
