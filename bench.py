@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in window counts instead of the autotuned table")
+    ap.add_argument("--tune-table", default=None,
+                    help="load the window table from this file instead of measuring it")
+    ap.add_argument("--save-tune", default=None, help="write the window table to this file")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
     ap.add_argument("--sweep", choices=["bler"], help="quality sweep instead of the bench line")
     ap.add_argument("--bler-cbs", type=int, default=0,
@@ -249,13 +252,23 @@ def run_ours(args):
     ctx = crnt.Context(local)
     tune = None
     if not args.no_autotune:
-        # window counts per K picked by measurement (outside the timed region)
+        # window counts per K picked by measurement (outside the timed region),
+        # or a table saved by an earlier run
         t0 = time.perf_counter()
-        table = ctx.autotune(32)
+        if args.tune_table:
+            with open(args.tune_table) as f:
+                table = [int(x) for x in f.read().split()]
+            crnt.tune_set(table)
+        else:
+            table = ctx.autotune(32)
+        if args.save_tune:
+            with open(args.save_tune, "w") as f:
+                f.write(" ".join(str(x) for x in table) + "\n")
         ks = (list(range(40, 513, 8)) + list(range(528, 1025, 16)) + list(range(1056, 2049, 32))
               + list(range(2112, 6145, 64)))  # the 188 CB sizes, in table order
         builtin = [max(1, min(k // 8, 128, -(-k // 48))) for k in ks]
         tune = {"w_min": 32, "seconds": round(time.perf_counter() - t0, 2),
+                "source": args.tune_table or "crnt_autotune",
                 "entries_changed_from_builtin": sum(int(a != b) for a, b in zip(table, builtin)),
                 "P_at_K": {str(k): p for k, p in zip(ks, table)
                            if k in (40, 256, 512, 1024, 2048, 4096, 5824, 5888, 6016, 6144)}}

@@ -345,15 +345,18 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   }
   std::sort(pl->keyed.begin(), pl->keyed.end());
 
-  // ---- buffers: descriptors | zeroed per-launch state | work items
+  // ---- one device buffer: descriptors | zeroed per-launch state | results
+  // | work items.  The state (queue head, error word, TB accumulators) and
+  // the results are contiguous, so one copy brings both back.
   const size_t b_cbs = sizeof(CbDesc) * ncb, b_tbs = sizeof(TbDesc) * n;
   const size_t off_tbs = al256(b_cbs), off_zero = off_tbs + al256(b_tbs);
   const size_t s_state = 256, s_done = al256(4 * n), s_crc = al256(8 * n);
   pl->zero_off = off_zero;
   pl->scratch_zero = s_state + s_done + s_crc;
-  const size_t off_items = off_zero + pl->scratch_zero;
+  const size_t off_res = off_zero + pl->scratch_zero;
+  pl->res_bytes = (2 * (size_t)ncb + n + 15) & ~size_t(15);
+  const size_t off_items = off_res + pl->res_bytes;
   const size_t max_desc = off_items + sizeof(WorkItem) * ncb;
-  pl->res_bytes = 2 * (size_t)ncb + n;
   // The previous upload from h_desc must have completed before the staging
   // buffer is rewritten, and no launch may still read the device buffers if
   // they are about to grow.  Waiting on the upload's event (not the whole
@@ -364,11 +367,10 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   if (pl->upload_pending && cudaEventSynchronize(pl->desc_ev) != cudaSuccess)
     return CRNT_EDEVICE;
   pl->upload_pending = false;
-  if ((max_desc > pl->d_desc.n || pl->res_bytes > pl->d_scratch.n) &&
-      cudaStreamSynchronize(stream) != cudaSuccess)
+  if (max_desc > pl->d_desc.n && cudaStreamSynchronize(stream) != cudaSuccess)
     return CRNT_EDEVICE;
   if (!pl->d_desc.ensure(max_desc) || !pl->h_desc.ensure(max_desc) ||
-      !pl->d_scratch.ensure(pl->res_bytes) || !pl->h_res.ensure(pl->res_bytes))
+      !pl->h_res.ensure(pl->scratch_zero + pl->res_bytes))
     return CRNT_ENOMEM;
   uint8_t* h = (uint8_t*)pl->h_desc.p;
   CbDesc* hc = (CbDesc*)h;
@@ -493,7 +495,6 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   pl->upload_pending = true;
   pl->state_fresh = true;
   uint8_t* dd = (uint8_t*)pl->d_desc.p;
-  uint8_t* sc = (uint8_t*)pl->d_scratch.p;
   DecParams& p = pl->prm;
   memset(&p, 0, sizeof p);
   p.cbs = (const CbDesc*)dd;
@@ -505,7 +506,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   p.state = (DecState*)(dd + off_zero);
   p.tb_done = (int32_t*)(dd + off_zero + s_state);
   p.tb_crc = (uint32_t*)(dd + off_zero + s_state + s_done);
-  p.cb_iters = sc;
+  p.cb_iters = dd + off_res;
   p.cb_ok = p.cb_iters + ncb;
   p.tb_ok = p.cb_ok + ncb;
   p.xpowA = ctx->xpowA;
@@ -534,7 +535,8 @@ int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, 
 }
 
 int plan_fetch_results(crnt_plan* pl, cudaStream_t s) {
-  if (cudaMemcpyAsync(pl->h_res.p, pl->prm.cb_iters, pl->res_bytes, cudaMemcpyDeviceToHost, s) !=
+  if (cudaMemcpyAsync(pl->h_res.p, (uint8_t*)pl->d_desc.p + pl->zero_off,
+                      pl->scratch_zero + pl->res_bytes, cudaMemcpyDeviceToHost, s) !=
       cudaSuccess)
     return CRNT_EDEVICE;
   return CRNT_OK;
@@ -543,12 +545,13 @@ int plan_fetch_results(crnt_plan* pl, cudaStream_t s) {
 void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res) {
   const size_t ncb = pl->n_cb;
   const uint32_t n = pl->info.n_tb;
-  const uint8_t* h = (const uint8_t*)pl->h_res.p;
+  const int32_t err = ((const DecState*)pl->h_res.p)->err;  // a bounded device wait expired
+  const uint8_t* h = (const uint8_t*)pl->h_res.p + pl->scratch_zero;
   for (uint32_t t = 0; t < n; t++) {
     crnt_tb_result& r = res[t];
     memset(&r, 0, sizeof r);
     const lte::Seg& sg = pl->segs[t];
-    r.status = CRNT_OK;
+    r.status = err ? CRNT_ETIMEDOUT : CRNT_OK;
     r.C = (uint8_t)sg.C;
     r.K_plus = (uint16_t)sg.Kp;
     r.K_minus = (uint16_t)sg.Km;

@@ -110,8 +110,8 @@ struct crnt_plan {
   uint32_t n_cb = 0;
   crnt_plan_info info{};
   int smem = 0;
-  crnt::Buf d_desc, d_scratch;       // device: descriptors + zeroed state | results
-  crnt::Buf h_desc{true}, h_res{true};  // pinned: descriptor staging | results
+  crnt::Buf d_desc;                  // device: descriptors, zeroed state, results, items
+  crnt::Buf h_desc{true}, h_res{true};  // pinned: descriptor staging | state + results
   cudaEvent_t desc_ev = nullptr;     // recorded after the last descriptor upload
   bool upload_pending = false;       // desc_ev may not have completed yet
   bool state_fresh = false;          // the zeroed state was just uploaded
