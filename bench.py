@@ -433,7 +433,7 @@ def subframe_latency(crnt, ctx, dev):
             "what": "device time of one 20 MHz subframe decode (13 CBs, early stop)"}
 
 
-def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 48, 56, 64, 80, 96),
+def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 48, 56, 64),
                 seconds=1.5):
     """Serving loop under cell load: every cell submits one subframe (8 UEs,
     TB mix of the TTI workload) per 1 ms period with a random phase and
@@ -471,12 +471,15 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 48, 56, 64, 8
         bits = (ctypes.c_void_p * 4096)()
         rng_u = synth.uniform01(seed, 77, 1 << 20)
         ku = 0
-        for cells in cells_list:
+        # the first pass (16 cells, 0.3 s) warms the serving loop up (its
+        # page-locked ring and slot buffers are created on the first submit)
+        # and is not reported
+        for cells, secs, record in [(16, 0.3, False)] + [(c, seconds, True) for c in cells_list]:
             phase = [float(rng_u[c]) * 1e6 for c in range(cells)]
             lat, subframes, refused, nbits = [], 0, 0, 0
             pending = {}
             t0 = time.monotonic_ns() + 2_000_000
-            t_end = t0 + int(seconds * 1e9)
+            t_end = t0 + int(secs * 1e9)
             nxt = [t0 + int(phase[c]) for c in range(cells)]
             sf = [0] * cells
             while True:
@@ -513,7 +516,7 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 48, 56, 64, 8
                 if now > t_end + 5_000_000_000:
                     break
             lat.sort()
-            if not lat:
+            if not lat or not record:
                 continue
             p50 = lat[len(lat) // 2]
             p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]

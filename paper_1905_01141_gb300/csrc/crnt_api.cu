@@ -514,6 +514,14 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   return CRNT_OK;
 }
 
+bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs) {
+  const size_t zero = 256 + al256(4 * (size_t)max_tbs) + al256(8 * (size_t)max_tbs);
+  const size_t res = (2 * (size_t)max_cbs + max_tbs + 15) & ~size_t(15);
+  const size_t desc = al256(sizeof(CbDesc) * max_cbs) + al256(sizeof(TbDesc) * max_tbs) + zero +
+                      res + sizeof(WorkItem) * max_cbs;
+  return pl->d_desc.ensure(desc) && pl->h_desc.ensure(desc) && pl->h_res.ensure(zero + res);
+}
+
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
                 int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded) {
   DecParams p = pl->prm;

@@ -129,6 +129,9 @@ namespace crnt {
 // null means the TBs' LLRs are concatenated in order.
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
                cudaStream_t stream, const int64_t* llr_base = nullptr);
+// Size a plan's buffers for batches of up to max_tbs TBs and max_cbs CBs, so
+// that planning such batches later allocates nothing.
+bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs);
 // state_uploaded: the caller launches right after plan_build, whose upload
 // already zeroed the per-launch state (skips one memset).
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,

@@ -246,9 +246,13 @@ static Serving* serving_get(crnt_ctx* ctx) {
     return nullptr;
   }
   for (int i = 0; i < kSlots; i++) {
+    // buffers for the largest batch up front: no allocation (and none of the
+    // device-wide synchronisation a cudaFree implies) while serving
     std::unique_ptr<Slot> s(new (std::nothrow) Slot);
     if (!s || cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
+        !plan_reserve(&s->plan, kMaxBatchTbs, kMaxBatchTbs * CRNT_MAX_CB) ||
+        !s->h_out.ensure((size_t)kMaxBatchTbs * 4096))
       return nullptr;
     sv->slots.push_back(std::move(s));
   }
