@@ -361,7 +361,8 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
-        line["serving"] = serving_leg(crnt, dev, args.seed)
+        line["serving"] = serving_leg(crnt, dev, args.seed,
+                                      tune_table=None if args.no_autotune else crnt.tune_get())
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
         line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
         if not args.no_cpu_baseline and ws == 1:
@@ -434,101 +435,50 @@ def subframe_latency(crnt, ctx, dev):
 
 
 def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 48, 56, 64),
-                seconds=1.5):
-    """Serving loop under cell load: every cell submits one subframe (8 UEs,
-    TB mix of the TTI workload) per 1 ms period with a random phase and
-    +-200 us jitter; ~10 % of TBs are HARQ retransmissions (rv 2) combined in
-    the device-resident soft buffers.  Latency = completion - arrival time.
-    Returns per cell count p50/p99 latency, deadline-miss fraction and the
-    largest cell count whose p99 stays within 1 ms."""
-    import ctypes
+                seconds=1.5, tune_table=None):
+    """Serving loop under cell load, driven by the native open-loop load
+    generator (crnt_loadgen, a client of crnt_submit / crnt_poll): every cell
+    submits one subframe (8 UEs, TB mix of the TTI workload) per 1 ms period
+    with a random phase and +-200 us jitter; 10 % of TBs are HARQ
+    retransmissions (rv cycling 2, 3, 1, 0) combined in the device-resident
+    soft buffers.  Latency = completion - scheduled arrival.  Returns per cell
+    count p50/p99 latency, deadline-miss fraction and the largest cell count
+    whose p99 stays within 1 ms."""
+    import struct
+    import subprocess as sp
+    from paper_1905_01141_gb300 import build as crnt_build
     ues = 8
     maxc = max(cells_list)
     shapes = synth.tti_batch(seed + 99, n_tb=maxc * ues)
-    rows = []
-    with crnt.Context(dev.index or 0, max_inflight=65536) as ctx:
-        tbs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], max_iter=6, early_stop=1) for s in shapes]
-        pay = np.concatenate([np.packbits(synth.bits(seed, 7000 + t, s["A"]))
-                              for t, s in enumerate(shapes)])
-        coded = np.zeros(sum(s["G"] for s in shapes), dtype=np.uint8)
+    tbs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], max_iter=6, early_stop=1) for s in shapes]
+    pay = np.concatenate([np.packbits(synth.bits(seed, 7000 + t, s["A"]))
+                          for t, s in enumerate(shapes)])
+    coded = np.zeros(sum(s["G"] for s in shapes), dtype=np.uint8)
+    with crnt.Context(dev.index or 0) as ctx:
         ctx.encode_batch(tbs, pay, coded)
-        import torch
-        # the LLR source lives in pinned host memory, as fronthaul buffers would
-        llr_pin = torch.from_numpy(channel(shapes, coded, seed + 5)).pin_memory()
-        offs = np.cumsum([0] + [s["G"] for s in shapes])
-        base = llr_pin.data_ptr()
-        # per cell: prebuilt parameter / pointer / ticket arrays
-        cell_par, cell_ptr, cell_tk, cell_A = [], [], [], []
-        for c in range(maxc):
-            par = crnt.params_array([dict(tbs[c * ues + u], cell=c, ue=u, flags=crnt.F_HARQ)
-                                     for u in range(ues)])
-            ptr = (ctypes.c_void_p * ues)(*[base + int(offs[c * ues + u]) for u in range(ues)])
-            cell_par.append(par)
-            cell_ptr.append(ptr)
-            cell_tk.append((ctypes.c_uint64 * ues)())
-            cell_A.append([tbs[c * ues + u]["A"] for u in range(ues)])
-        res = (crnt.TbResult * 4096)()
-        bits = (ctypes.c_void_p * 4096)()
-        rng_u = synth.uniform01(seed, 77, 1 << 20)
-        ku = 0
-        # the first pass (16 cells, 0.3 s) warms the serving loop up (its
-        # page-locked ring and slot buffers are created on the first submit)
-        # and is not reported
-        for cells, secs, record in [(16, 0.3, False)] + [(c, seconds, True) for c in cells_list]:
-            phase = [float(rng_u[c]) * 1e6 for c in range(cells)]
-            lat, subframes, refused, nbits = [], 0, 0, 0
-            pending = {}
-            t0 = time.monotonic_ns() + 2_000_000
-            t_end = t0 + int(secs * 1e9)
-            nxt = [t0 + int(phase[c]) for c in range(cells)]
-            sf = [0] * cells
-            while True:
-                now = time.monotonic_ns()
-                for c in range(cells):
-                    if nxt[c] <= now and nxt[c] < t_end:
-                        par = cell_par[c]
-                        pid = sf[c] % 8
-                        for u in range(ues):
-                            retx = sf[c] >= 8 and float(rng_u[ku & 0xFFFFF]) < 0.1
-                            ku += 1
-                            par[u].harq_pid = pid
-                            par[u].new_data = 0 if retx else 1
-                            par[u].rv = 2 if retx else 0
-                        rc = ctx.submit_raw(par, cell_ptr[c], ues, cell_tk[c])
-                        if rc == 0:
-                            arr = nxt[c]
-                            for u in range(ues):
-                                pending[cell_tk[c][u]] = (arr, cell_A[c][u])
-                        else:
-                            refused += 1
-                        subframes += 1
-                        sf[c] += 1
-                        jit = (float(rng_u[ku & 0xFFFFF]) - 0.5) * 400_000
-                        ku += 1
-                        nxt[c] = t0 + sf[c] * 1_000_000 + int(phase[c] + jit)
-                n = ctx.poll_raw(res, bits, 4096, 0)
-                for i in range(n):
-                    arr, A = pending.pop(res[i].ticket)
-                    lat.append((res[i].t_done_ns - arr) / 1e3)
-                    nbits += A
-                if now >= t_end and not pending:
-                    break
-                if now > t_end + 5_000_000_000:
-                    break
-            lat.sort()
-            if not lat or not record:
-                continue
-            p50 = lat[len(lat) // 2]
-            p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
-            rows.append({"cells": cells, "tbs": len(lat), "subframes": subframes,
-                         "refused_subframes": refused, "p50_us": round(p50, 1),
-                         "p99_us": round(p99, 1),
-                         "deadline_miss": sum(1 for x in lat if x > 1000.0) / len(lat),
-                         "gbit_s": nbits / seconds / 1e9})
-            if p99 > 20000:
-                break  # far past saturation: larger loads only grow the queue
-    ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["refused_subframes"] == 0]
+    llr = channel(shapes, coded, seed + 5)
+    offs = np.cumsum([0] + [s["G"] for s in shapes])[:-1].astype(np.int64)
+    par = crnt.params_array(tbs)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "load.bin")
+        with open(path, "wb") as f:
+            f.write(struct.pack("<I", len(tbs)))
+            f.write(bytes(par))
+            f.write(offs.tobytes())
+            f.write(llr.tobytes())
+        cmd = [crnt_build.LOADGEN]
+        if tune_table is not None:
+            tpath = os.path.join(td, "tune.txt")
+            with open(tpath, "w") as f:
+                f.write(" ".join(str(x) for x in tune_table))
+            cmd += ["--tune", tpath]
+        cmd += [path, str(ues), str(seconds), "0.1", str(seed)] + [str(c) for c in cells_list]
+        out = sp.run(cmd, capture_output=True, text=True, timeout=600)
+    rows = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["refused_subframes"] == 0
+          and r["errors"] == 0]
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
+            "driver": "crnt_loadgen (native, open loop)", "rc": out.returncode,
             "what": "continuous batching via crnt_submit/crnt_poll; 8 UEs per cell, "
                     "1 subframe per cell per ms, +-200 us jitter, 10% HARQ retransmissions, "
                     "latency from scheduled arrival to completion"}

@@ -1,5 +1,7 @@
 """Build the library: every CUDA translation unit of ``csrc/`` is compiled for
-sm_103a in parallel and linked into ``_build/libcrnt.so`` (in-tree)."""
+sm_103a in parallel and linked into ``_build/libcrnt.so`` (in-tree), then the
+serving load generator ``_build/crnt_loadgen`` (a host program that uses the
+library through its C ABI) is linked against it."""
 import concurrent.futures as cf
 import os
 import subprocess
@@ -9,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcrnt.so")
+LOADGEN = os.path.join(OUT, "crnt_loadgen")
 UNITS = ["decode.cu", "encode.cu", "crnt_api.cu", "serve.cu", "noalloc.cu", "tune.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -25,7 +28,7 @@ def _deps():
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LOADGEN):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps() if os.path.exists(d))
@@ -59,6 +62,15 @@ def build(force=False, verbose=False):
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("link failed")
     os.replace(tmp, LIB)
+    # the serving load generator: a host-only client of the C ABI
+    tmp = LOADGEN + ".%d.tmp" % os.getpid()
+    cmd = [NVCC, "-O2", "-std=c++17", "-o", tmp, os.path.join(SRC, "loadgen.cpp"), "-L" + OUT,
+           "-lcrnt", "-Xlinker", "-rpath,$ORIGIN", "-Xcompiler", "-pthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("loadgen build failed")
+    os.replace(tmp, LOADGEN)
     return LIB
 
 

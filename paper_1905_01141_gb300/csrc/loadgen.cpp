@@ -1,0 +1,216 @@
+// loadgen.cpp -- open-loop cell load for the serving loop, a client of the
+// public C ABI only (crnt_submit / crnt_poll).
+//
+// Every cell sends one subframe (its UEs' TBs) per 1 ms period, at a random
+// phase plus uniform jitter, from a native submitter thread that follows the
+// arrival times; a poller thread collects results.  Latency of a TB = its
+// completion time (the library's t_done_ns, steady clock) minus its
+// scheduled arrival.  A fraction of TBs are HARQ retransmissions of the same
+// (cell, UE, process) with the redundancy version cycling 2, 3, 1, 0.
+//
+// Input file (written by the caller): uint32 n, then n crnt_tb_params, then
+// n int64 LLR offsets, then the LLR bytes.  TB u of cell c is entry
+// (c * ues + u) mod n.  Output: one JSON object per cell count on stdout.
+//
+// usage: crnt_loadgen [--tune TABLE] FILE UES SECONDS RETX_FRACTION SEED CELLS...
+// TABLE: a window-count table (188 numbers) installed with crnt_tune_set.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <queue>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/crnt.h"
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// SplitMix64 (public definition): the phases, jitter and retransmission draws
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double unit(uint64_t& s) { return (double)(splitmix(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+struct Point {
+  int cells = 0;
+  long tbs = 0, subframes = 0, refused = 0, errors = 0;
+  double p50 = 0, p99 = 0, miss = 0, gbit = 0;
+};
+
+Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
+                const std::vector<const int8_t*>& ptr, int ues, int cells, double seconds,
+                double retx, uint64_t seed) {
+  const int n = (int)par.size();
+  uint64_t rs = seed * 1000003ull + (uint64_t)cells;
+  std::vector<double> phase(cells);
+  for (int c = 0; c < cells; c++) phase[c] = unit(rs) * 1e6;
+  std::mutex mu;
+  std::unordered_map<uint64_t, std::pair<int64_t, uint32_t>> pending;  // ticket -> (arrival, A)
+  std::vector<double> lat;
+  std::atomic<bool> done_submitting{false};
+  long n_bits = 0, errors = 0;
+  const int64_t t0 = now_ns() + 2000000;
+  const int64_t t_end = t0 + (int64_t)(seconds * 1e9);
+  // poller
+  std::thread poller([&] {
+    std::vector<crnt_tb_result> res(4096);
+    std::vector<const uint8_t*> bits(4096);
+    for (;;) {
+      const int k = crnt_poll(ctx, res.data(), bits.data(), 4096, 1000);
+      if (k < 0) break;
+      std::lock_guard<std::mutex> lk(mu);
+      for (int i = 0; i < k; i++) {
+        auto it = pending.find(res[i].ticket);
+        if (it == pending.end()) continue;
+        if (res[i].status != CRNT_OK) errors++;
+        lat.push_back((double)((int64_t)res[i].t_done_ns - it->second.first) / 1e3);
+        n_bits += it->second.second;
+        pending.erase(it);
+      }
+      if (done_submitting.load() && pending.empty()) break;
+      if (now_ns() > t_end + 5000000000ll) break;
+    }
+  });
+  // submitter: arrivals in time order
+  using Ev = std::pair<int64_t, int>;  // (arrival, cell)
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> q;
+  std::vector<int> sf(cells, 0);
+  for (int c = 0; c < cells; c++) q.push(Ev{t0 + (int64_t)phase[c], c});
+  std::vector<crnt_tb_params> tb(ues);
+  std::vector<const int8_t*> lp(ues);
+  std::vector<uint64_t> tk(ues);
+  long subframes = 0, refused = 0;
+  while (!q.empty()) {
+    const Ev ev = q.top();
+    q.pop();
+    if (ev.first >= t_end) continue;
+    while (now_ns() < ev.first) {
+    }
+    const int c = ev.second;
+    const int pid = sf[c] % 8;
+    for (int u = 0; u < ues; u++) {
+      const int e = (c * ues + u) % n;
+      tb[u] = par[e];
+      lp[u] = ptr[e];
+      tb[u].cell = (uint32_t)c;
+      tb[u].ue = (uint32_t)u;
+      tb[u].harq_pid = (uint32_t)pid;
+      tb[u].flags = CRNT_F_HARQ;
+      const bool rt = sf[c] >= 8 && unit(rs) < retx;
+      static const uint8_t rv_cycle[4] = {2, 3, 1, 0};
+      tb[u].new_data = rt ? 0 : 1;
+      tb[u].rv = rt ? rv_cycle[(sf[c] / 8) % 4] : 0;
+    }
+    {
+      // tickets are registered before the poller can see their results
+      std::lock_guard<std::mutex> lk(mu);
+      const int rc = crnt_submit(ctx, tb.data(), lp.data(), (uint32_t)ues, tk.data());
+      if (rc == CRNT_OK) {
+        for (int u = 0; u < ues; u++) pending[tk[u]] = {ev.first, tb[u].A};
+      } else {
+        refused++;
+      }
+    }
+    subframes++;
+    sf[c]++;
+    const double jit = (unit(rs) - 0.5) * 400000.0;
+    q.push(Ev{t0 + (int64_t)sf[c] * 1000000 + (int64_t)(phase[c] + jit), c});
+  }
+  done_submitting.store(true);
+  poller.join();
+  Point p;
+  p.cells = cells;
+  p.subframes = subframes;
+  p.refused = refused;
+  p.errors = errors;
+  std::sort(lat.begin(), lat.end());
+  p.tbs = (long)lat.size();
+  if (!lat.empty()) {
+    p.p50 = lat[lat.size() / 2];
+    p.p99 = lat[std::min(lat.size() - 1, (size_t)(0.99 * (double)lat.size()))];
+    long miss = 0;
+    for (double x : lat) miss += x > 1000.0;
+    p.miss = (double)miss / (double)lat.size();
+  }
+  p.gbit = (double)n_bits / seconds / 1e9;
+  return p;
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc > 2 && strcmp(argv[1], "--tune") == 0) {
+    FILE* t = fopen(argv[2], "r");
+    if (!t) return 2;
+    uint8_t table[CRNT_NUM_K];
+    for (int i = 0; i < CRNT_NUM_K; i++) {
+      int v = 0;
+      if (fscanf(t, "%d", &v) != 1) return 2;
+      table[i] = (uint8_t)v;
+    }
+    fclose(t);
+    if (crnt_tune_set(table, CRNT_NUM_K) != CRNT_OK) return 2;
+    argv += 2;
+    argc -= 2;
+  }
+  if (argc < 7) {
+    fprintf(stderr, "usage: crnt_loadgen [--tune TABLE] FILE UES SECONDS RETX SEED CELLS...\n");
+    return 2;
+  }
+  FILE* f = fopen(argv[1], "rb");
+  if (!f) return 2;
+  uint32_t n = 0;
+  if (fread(&n, 4, 1, f) != 1 || n == 0) return 2;
+  std::vector<crnt_tb_params> par(n);
+  std::vector<int64_t> off(n);
+  if (fread(par.data(), sizeof(crnt_tb_params), n, f) != n || fread(off.data(), 8, n, f) != n)
+    return 2;
+  std::vector<int8_t> blob;
+  int8_t buf[1 << 16];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) blob.insert(blob.end(), buf, buf + k);
+  fclose(f);
+  std::vector<const int8_t*> ptr(n);
+  for (uint32_t i = 0; i < n; i++) ptr[i] = blob.data() + off[i];
+  const int ues = atoi(argv[2]);
+  const double seconds = atof(argv[3]), retx = atof(argv[4]);
+  const uint64_t seed = strtoull(argv[5], nullptr, 10);
+  int max_cells = 0;
+  for (int a = 6; a < argc; a++) max_cells = std::max(max_cells, atoi(argv[a]));
+  crnt_config cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.harq_slots = (uint32_t)std::max(4096, max_cells * ues * 8);
+  cfg.max_inflight = 65536;
+  crnt_ctx* ctx = nullptr;
+  if (crnt_create(&ctx, &cfg) != CRNT_OK) return 3;
+  // warm-up pass (not reported): the serving loop's buffers come up here
+  run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1);
+  for (int a = 6; a < argc; a++) {
+    const int cells = atoi(argv[a]);
+    const Point p = run_point(ctx, par, ptr, ues, cells, seconds, retx, seed);
+    printf("{\"cells\": %d, \"tbs\": %ld, \"subframes\": %ld, \"refused_subframes\": %ld, "
+           "\"errors\": %ld, \"p50_us\": %.1f, \"p99_us\": %.1f, \"deadline_miss\": %.6f, "
+           "\"gbit_s\": %.4f}\n",
+           p.cells, p.tbs, p.subframes, p.refused, p.errors, p.p50, p.p99, p.miss, p.gbit);
+    fflush(stdout);
+    if (p.p99 > 20000.0) break;  // far past saturation
+  }
+  crnt_destroy(ctx);
+  return 0;
+}

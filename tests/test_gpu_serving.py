@@ -1,6 +1,7 @@
 """Serving loop (crnt_submit / crnt_poll): continuous batching gives every
 TB the same result alone and in the mix, admission refuses work beyond the
 in-flight limit, HARQ retransmissions combine through the serving path."""
+import json
 import time
 
 import numpy as np
@@ -111,3 +112,35 @@ def test_harq_through_serving(orc, crnt_lib, ctx):
     with pytest.raises(crnt_lib.CrntError) as ei:
         ctx.submit([t2], [l2])
     assert ei.value.code == crnt_lib.ENOTFOUND
+
+
+def test_native_load_generator_runs(crnt_lib):
+    # crnt_loadgen (the bench's serving driver, a client of the C ABI) serves
+    # a light load: every submitted TB comes back without error, within 1 ms
+    import os
+    import struct
+    import subprocess
+    import tempfile
+
+    import numpy as np
+    from paper_1905_01141_gb300 import build
+    shapes = synth.tti_batch(seed=41, n_tb=16, amax=20000)
+    tbs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], max_iter=6, early_stop=1) for s in shapes]
+    llr = np.concatenate([synth.channel_llrs(np.zeros(s["G"], np.uint8), s["Qm"],
+                                             synth.sigma2_snr(30.0), 41, i)
+                          for i, s in enumerate(shapes)])
+    offs = np.cumsum([0] + [s["G"] for s in shapes])[:-1].astype(np.int64)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "load.bin")
+        with open(path, "wb") as f:
+            f.write(struct.pack("<I", len(tbs)))
+            f.write(bytes(crnt_lib.params_array(tbs)))
+            f.write(offs.tobytes())
+            f.write(llr.tobytes())
+        out = subprocess.run([build.LOADGEN, path, "8", "0.3", "0.1", "1", "2"],
+                             capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    rows = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(rows) == 1 and rows[0]["cells"] == 2
+    assert rows[0]["tbs"] >= 2 * 8 * 250 and rows[0]["errors"] == 0
+    assert rows[0]["refused_subframes"] == 0 and rows[0]["p99_us"] < 1000.0
