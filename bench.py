@@ -361,8 +361,10 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
-        line["serving"] = serving_leg(crnt, dev, args.seed,
-                                      tune_table=None if args.no_autotune else crnt.tune_get())
+        tt = None if args.no_autotune else crnt.tune_get()
+        line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
+        line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 44, 48, 52),
+                                            tune_table=tt, purge=True)
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
         line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
         if not args.no_cpu_baseline and ws == 1:
@@ -435,7 +437,7 @@ def subframe_latency(crnt, ctx, dev):
 
 
 def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 48, 56, 64),
-                seconds=1.5, tune_table=None):
+                seconds=1.5, tune_table=None, purge=False):
     """Serving loop under cell load, driven by the native open-loop load
     generator (crnt_loadgen, a client of crnt_submit / crnt_poll): every cell
     submits one subframe (8 UEs, TB mix of the TTI workload) per 1 ms period
@@ -472,6 +474,8 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 4
             with open(tpath, "w") as f:
                 f.write(" ".join(str(x) for x in tune_table))
             cmd += ["--tune", tpath]
+        if purge:
+            cmd += ["--purge"]
         cmd += [path, str(ues), str(seconds), "0.1", str(seed)] + [str(c) for c in cells_list]
         out = sp.run(cmd, capture_output=True, text=True, timeout=600)
     rows = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
@@ -479,6 +483,7 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 4
           and r["errors"] == 0]
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
             "driver": "crnt_loadgen (native, open loop)", "rc": out.returncode,
+            "purge_on_failure": purge,
             "what": "continuous batching via crnt_submit/crnt_poll; 8 UEs per cell, "
                     "1 subframe per cell per ms, +-200 us jitter, 10% HARQ retransmissions, "
                     "latency from scheduled arrival to completion"}

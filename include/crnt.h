@@ -75,10 +75,18 @@ typedef struct crnt_tb_params {
     uint8_t new_data;    /* 1: clear the HARQ soft buffer before combining */
     uint32_t cell, ue, harq_pid; /* HARQ process key (flags bit 0 set) */
     uint32_t flags;      /* bit 0 (CRNT_F_HARQ): combine into the library-owned
-                            soft buffer of (cell, ue, harq_pid) */
+                            soft buffer of (cell, ue, harq_pid); bit 1
+                            (CRNT_F_PURGE): purge on failure, see below */
 } crnt_tb_params;
 
 #define CRNT_F_HARQ 1u
+/* Purge on failure (Algorithm 2's purge of a failed TB's remaining CBs): as
+ * soon as one CB of the TB fails (max_iter iterations without a CRC pass),
+ * its other CBs stop at their next iteration boundary.  The TB result is the
+ * same (tb_crc_ok = 0); a stopped CB reports cb_iters = 0, cb_crc_ok = 0 and
+ * writes no payload bytes (they are left as they were).  Which CBs stop
+ * depends on timing; TBs that decode are never affected. */
+#define CRNT_F_PURGE 2u
 
 /* Per-TB result (80 bytes). */
 typedef struct crnt_tb_result {

@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEVICE, ENOTFOUND = 0, -1, -2, -3, -4, -
 MAX_CB = 16
 MAX_P = 128
 F_HARQ = 1
+F_PURGE = 2
 
 
 class CrntError(RuntimeError):

@@ -434,6 +434,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     d.max_iter = tp.max_iter;
     d.early_stop = tp.early_stop ? 1 : 0;
     d.new_data = tp.new_data ? 1 : 0;
+    d.purge = (tp.flags & CRNT_F_PURGE) && s.C > 1 ? 1 : 0;
     memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;
     pl->cb_r[i] = r;

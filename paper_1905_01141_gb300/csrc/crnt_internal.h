@@ -38,7 +38,8 @@ struct CbDesc {
   int32_t dbg_off;         // element offset of the CB in debug arrays
   uint8_t crc_b;           // 1: CRC24B per CB (C > 1); 0: CRC24A (C == 1)
   uint8_t max_iter, early_stop, new_data;
-  uint8_t pad0[4];
+  uint8_t purge;           // 1: stop when another CB of the TB has failed
+  uint8_t pad0[3];
 };
 
 struct TbDesc {

@@ -246,7 +246,8 @@ struct CbSlot {
   uint32_t* hard;
   uint4* seed;   // [4][P]: alpha dec0, alpha dec1, beta dec0, beta dec1
   uint4* ck;     // [P][nck]
-  int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|
+  int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|,
+                 // [6] stopped by a purge
 };
 __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
   CbSlot s;
@@ -363,6 +364,7 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     sl.flags[3] = 0;
     sl.flags[4] = 0;
     sl.flags[5] = 0;
+    sl.flags[6] = 0;
   }
 }
 
@@ -773,9 +775,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
       if (run && p == 0) {
         const bool ok = check && fl[2] == 0;
         fl[2] = 0;
+        const int tb = dp->tb;
         if (ok || it == my_max) {
           fl[0] = 1;
           fl[1] = ok ? it : my_max + 1;
+          atomicSub(&s_remaining, 1);
+          // a failed CB fails its TB: flag it now (the TB CRC step flags it
+          // again) so that purging CBs of the TB can stop
+          if (!ok && dp->crc_b) atomicOr(&prm.tb_crc[2 * tb + 1], 1u);
+        } else if (dp->purge && *(volatile uint32_t*)&prm.tb_crc[2 * tb + 1] != 0u) {
+          fl[0] = 1;
+          fl[1] = 0;
+          fl[6] = 1;
           atomicSub(&s_remaining, 1);
         }
       }
@@ -787,8 +798,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
     const CbDesc d = *dp;
     const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
     const int sorted_idx = wi.cb0 + (mine ? mycb : 0);
-    const bool cb_ok = mine && sl.flags[1] <= d.max_iter;
-    if (mine) {
+    const bool purged = mine && sl.flags[6] != 0;
+    const bool cb_ok = mine && !purged && sl.flags[1] <= d.max_iter;
+    if (mine && !purged) {
       const TbDesc tb = prm.tbs[d.tb];
       const int nw = (d.K + 31) / 32;
       const int pad = nw * 32 - d.K;

@@ -12,8 +12,9 @@
 // n int64 LLR offsets, then the LLR bytes.  TB u of cell c is entry
 // (c * ues + u) mod n.  Output: one JSON object per cell count on stdout.
 //
-// usage: crnt_loadgen [--tune TABLE] FILE UES SECONDS RETX_FRACTION SEED CELLS...
-// TABLE: a window-count table (188 numbers) installed with crnt_tune_set.
+// usage: crnt_loadgen [--tune TABLE] [--purge] FILE UES SECONDS RETX_FRACTION SEED CELLS...
+// TABLE: a window-count table (188 numbers) installed with crnt_tune_set;
+// --purge: every TB asks for purge on failure (CRNT_F_PURGE).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -55,7 +56,7 @@ struct Point {
 
 Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
                 const std::vector<const int8_t*>& ptr, int ues, int cells, double seconds,
-                double retx, uint64_t seed) {
+                double retx, uint64_t seed, uint32_t extra_flags) {
   const int n = (int)par.size();
   uint64_t rs = seed * 1000003ull + (uint64_t)cells;
   std::vector<double> phase(cells);
@@ -111,7 +112,7 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
       tb[u].cell = (uint32_t)c;
       tb[u].ue = (uint32_t)u;
       tb[u].harq_pid = (uint32_t)pid;
-      tb[u].flags = CRNT_F_HARQ;
+      tb[u].flags = CRNT_F_HARQ | extra_flags;
       const bool rt = sf[c] >= 8 && unit(rs) < retx;
       static const uint8_t rv_cycle[4] = {2, 3, 1, 0};
       tb[u].new_data = rt ? 0 : 1;
@@ -169,8 +170,15 @@ int main(int argc, char** argv) {
     argv += 2;
     argc -= 2;
   }
+  uint32_t extra_flags = 0;
+  if (argc > 1 && strcmp(argv[1], "--purge") == 0) {
+    extra_flags = CRNT_F_PURGE;
+    argv += 1;
+    argc -= 1;
+  }
   if (argc < 7) {
-    fprintf(stderr, "usage: crnt_loadgen [--tune TABLE] FILE UES SECONDS RETX SEED CELLS...\n");
+    fprintf(stderr,
+            "usage: crnt_loadgen [--tune TABLE] [--purge] FILE UES SECONDS RETX SEED CELLS...\n");
     return 2;
   }
   FILE* f = fopen(argv[1], "rb");
@@ -200,10 +208,10 @@ int main(int argc, char** argv) {
   crnt_ctx* ctx = nullptr;
   if (crnt_create(&ctx, &cfg) != CRNT_OK) return 3;
   // warm-up pass (not reported): the serving loop's buffers come up here
-  run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1);
+  run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1, extra_flags);
   for (int a = 6; a < argc; a++) {
     const int cells = atoi(argv[a]);
-    const Point p = run_point(ctx, par, ptr, ues, cells, seconds, retx, seed);
+    const Point p = run_point(ctx, par, ptr, ues, cells, seconds, retx, seed, extra_flags);
     printf("{\"cells\": %d, \"tbs\": %ld, \"subframes\": %ld, \"refused_subframes\": %ld, "
            "\"errors\": %ld, \"p50_us\": %.1f, \"p99_us\": %.1f, \"deadline_miss\": %.6f, "
            "\"gbit_s\": %.4f}\n",

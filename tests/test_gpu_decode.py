@@ -237,3 +237,34 @@ def test_autotuned_windows_match_oracle(orc, crnt_lib, ctx):
         check_batch(orc, crnt_lib, tbs, llrs, g)
     finally:
         crnt_lib.tune_set(old)
+
+
+def test_purge_on_failure(orc, crnt_lib, ctx):
+    # Purge on failure (Algorithm 2): with CRNT_F_PURGE a failed CB stops the
+    # other CBs of its TB.  Decoded TBs are bit-exact with the oracle; every
+    # failed TB still fails, and each of its CBs either matches the oracle
+    # (iterations, CRC flag) or was stopped (0 iterations, CRC not passed).
+    # Many undecodable 13-CB TBs spread their CBs over several waves of CTAs.
+    specs = []
+    for i in range(48):
+        bad = i % 2 == 0
+        specs.append(dict(A=75376, G=86400, Qm=6, max_iter=6, early_stop=1,
+                          flags=crnt_lib.F_PURGE, seed=900 + i, snr=6.0 if bad else 22.0))
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs), debug=False)
+    off = np.cumsum([0] + [t["A"] // 8 for t in tbs])
+    stopped = 0
+    for t in range(len(tbs)):
+        cbs, bits, ok, _ = oracle_tb(orc, crnt_lib, tbs[t], llrs[t])
+        r = g["res"][t]
+        assert r["tb_crc_ok"] == ok
+        if ok:
+            assert np.array_equal(np.unpackbits(g["out"][off[t]:off[t + 1]]), bits)
+            assert r["cb_iters"] == [c[3] for c in cbs]
+        for c, it, crc in zip(cbs, r["cb_iters"], r["cb_crc_ok"]):
+            if it == 0:
+                stopped += 1
+                assert not ok and not crc
+            else:
+                assert it == c[3] and crc == (c[3] <= 6)
+    print("CBs stopped by purges:", stopped)
