@@ -33,7 +33,7 @@ def build(force=False):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-Wextra", "-shared", "-fPIC",
-                           _SRC, "-o", tmp])
+                           _SRC, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -76,6 +76,7 @@ def lib():
                 "orc_encode_tb": (I, [P, I, I, I, I, I, P]),
                 "orc_decode_tb": (I, [P, I, I, I, I, I, I, I, I, I, P, P, P]),
                 "orc_scale_ext": (I, [I]),
+                "orc_mi_table": (I, [P, I]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -233,15 +234,30 @@ def siso_seeded(Ls, Lp, La, ts, tp, P, aseed=None, bseed=None):
     return lam, le, a, b
 
 
+def _stop(early_stop):
+    """Stop rule code: False/0 none, True/1 CRC, 2 mutual information."""
+    if not isinstance(early_stop, bool) and early_stop == 2:
+        return 2
+    return int(bool(early_stop))
+
+
+def mi_table(n=128):
+    """T(x) of the mutual-information stop rule, x = 0..n-1."""
+    t = np.zeros(n, dtype=np.int32)
+    lib().orc_mi_table(_p(t), n)
+    return t
+
+
 def turbo_decode_cb(d0, d1, d2, F=0, crc="A", P=1, max_iter=6, early_stop=True):
-    """Returns (iterations, hard bits [K], extrinsic [K])."""
+    """Returns (iterations, hard bits [K], extrinsic [K]).  early_stop: False
+    (none), True (CRC) or 2 (mutual information)."""
     d0, d1, d2 = _i8(d0), _i8(d1), _i8(d2)
     K = len(d0) - 4
     hard = np.zeros(K, dtype=np.uint8)
     ext = np.zeros(K, dtype=np.int16)
     ct = {"A": 0, "B": 1, None: -1}[crc]
     it = lib().orc_turbo_decode_cb(_p(d0), _p(d1), _p(d2), K, F, ct, P, max_iter,
-                                   int(bool(early_stop)), _p(hard), _p(ext))
+                                   _stop(early_stop), _p(hard), _p(ext))
     if it < 0:
         raise RuntimeError("orc_turbo_decode_cb failed")
     return it, hard, ext
@@ -259,7 +275,7 @@ def decode_tb(llr, A, G, Qm=2, NL=1, rv=0, P=1, max_iter=6, early_stop=True, sof
         soft = np.zeros(tb_ncb_total(A), dtype=np.int8)
     a = np.zeros(A, dtype=np.uint8)
     res = TBResult()
-    rc = lib().orc_decode_tb(_p(llr), A, G, Qm, NL, rv, P, max_iter, int(bool(early_stop)),
+    rc = lib().orc_decode_tb(_p(llr), A, G, Qm, NL, rv, P, max_iter, _stop(early_stop),
                              int(new), _p(soft), _p(a), ctypes.byref(res))
     if rc:
         raise RuntimeError("orc_decode_tb failed")

@@ -29,6 +29,7 @@
  * (noiseless round trips): "parity unpinned" against 3GPP.
  */
 #include <stdint.h>
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -573,12 +574,45 @@ int orc_siso_once(int K, int P, const int8_t* Ls, const int8_t* Lp, const int16_
 }
 
 /* ------------------------------------------------------------------ */
+/* Mutual information of the a-posteriori LLRs (Sec. IV-B "Decoding    */
+/* function": the paper stops when the average mutual information of   */
+/* the LLRs converges).  Reading: for an LLR L in natural units, the    */
+/* information a bit carries is 1 - log2(1 + exp(-|L|)); the decoder's */
+/* LLRs carry 8 fixed-point units per natural unit (the LLR scale       */
+/* 8 * 2y / sigma^2 of the inputs).  In integers, with 2^16 = 1 bit:    */
+/*   T(x) = round(2^16 * log2(1 + exp(-x / 8))), x = min(|L|, 127)     */
+/* (T(127) already rounds to 0), and the sum over a CB                 */
+/*   S = sum_k (2^16 - T(min(|Lambda2_k|, 127))).                      */
+/* Stop rule: after iteration t >= 2, stop when the mean changed by at  */
+/* most 2^-10 bit: |S_t - S_(t-1)| * 2^10 <= K * 2^16.                 */
+/* ------------------------------------------------------------------ */
+int orc_mi_table(int32_t* T, int n)
+{
+    for (int x = 0; x < n; x++)
+        T[x] = (int32_t)floor(65536.0 * log2(1.0 + exp(-(double)x / 8.0)) + 0.5);
+    return 0;
+}
+
+static int64_t mi_sum(const int16_t* Lam, int K, const int32_t* T)
+{
+    int64_t S = 0;
+    for (int k = 0; k < K; k++) {
+        int x = Lam[k] < 0 ? -(int)Lam[k] : (int)Lam[k];
+        if (x > 127) x = 127;
+        S += 65536 - T[x];
+    }
+    return S;
+}
+
+/* ------------------------------------------------------------------ */
 /* Turbo decoding of one CB (Sec. IV-B "Decoding function", Fig. 4):   */
 /* demultiplex, SISO1 -> interleave -> SISO2 -> de-interleave, repeat. */
-/* Stop rule: CRC (24A for a single-CB TB, 24B otherwise) of the hard  */
-/* decisions after each full iteration, replacing the paper's mutual-  */
-/* information rule.  Returns iterations run, or max_iter+1 if the CRC */
-/* never passed (the failure convention of the performance captor).    */
+/* Stop rules (early_stop): 0 = none (max_iter iterations), 1 = CRC    */
+/* (24A for a single-CB TB, 24B otherwise) of the hard decisions after */
+/* each full iteration, 2 = the paper's mutual-information rule above  */
+/* (the CRC then only decides success).  Returns the iterations run    */
+/* when the CRC passes at the stop, else max_iter+1 (the failure       */
+/* convention of the performance captor).                               */
 /*   crc_type: 0 = CRC24A, 1 = CRC24B, -1 = no CRC (never passes).     */
 /*   hard[K]: hard decisions of the last iteration run.                */
 /*   ext[K] (optional): extrinsic a-priori for SISO1 after the last    */
@@ -614,6 +648,9 @@ int orc_turbo_decode_cb(const int8_t* d0, const int8_t* d1, const int8_t* d2, in
     s1.have = s2.have = 0;
     uint8_t* msg = malloc((size_t)K);
     int result = max_iter + 1;
+    int32_t T[128];
+    orc_mi_table(T, 128);
+    int64_t S_prev = 0;
     for (int it = 1; it <= max_iter; it++) {
         siso(K, d0, d1, La1, ts1, tp1, &s1, Lam, Le);
         for (int i = 0; i < K; i++) La2[i] = (int16_t)scale_ext(Le[pi[i]]);
@@ -626,6 +663,17 @@ int orc_turbo_decode_cb(const int8_t* d0, const int8_t* d1, const int8_t* d2, in
         if (crc_type >= 0) {
             for (int k = F; k < K; k++) msg[k - F] = hard[k];
             ok = (orc_crc24(msg, K - F, crc_type) == 0);
+        }
+        if (early_stop == 2) {
+            const int64_t S = mi_sum(Lam, K, T);
+            const int64_t dS = S > S_prev ? S - S_prev : S_prev - S;
+            const int converged = it >= 2 && dS * 1024 <= (int64_t)K * 65536;
+            S_prev = S;
+            if (converged || it == max_iter) {
+                if (ok) result = it;
+                break;
+            }
+            continue;
         }
         if (ok && (early_stop || it == max_iter)) { result = it; break; }
     }

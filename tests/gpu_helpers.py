@@ -70,7 +70,7 @@ def oracle_tb(orc, crnt, tb, llr, soft=None):
         soft[c["soft_offset"]:c["soft_offset"] + c["Ncb"]] = sb2
         it, hard, ext = orc.turbo_decode_cb(d0, d1, d2, F=c["F"], crc="B" if C > 1 else "A",
                                             P=c["P"], max_iter=tb.get("max_iter", 6),
-                                            early_stop=bool(tb.get("early_stop", 1)))
+                                            early_stop=tb.get("early_stop", 1))
         ok_all &= it <= tb.get("max_iter", 6)
         cbs.append((d0, d1, d2, it, hard, ext))
         payload.append(hard[c["F"]:c["K"] - L])

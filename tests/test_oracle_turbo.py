@@ -98,3 +98,46 @@ def test_filler_bits_are_known_zeros(orc):
     e = orc.encode_tb(a, G, Qm=2)
     bits, res, _ = orc.decode_tb(noiseless(e, 60), A, G, Qm=2, P=2)
     assert res["tb_crc_ok"] and np.array_equal(bits, a) and c_len > 0
+
+
+def test_mi_table_pins(orc):
+    # T(x) = round(2^16 log2(1 + exp(-x/8))): a zero LLR carries no
+    # information (T(0) = 2^16 exactly, log2 2 = 1), information grows with
+    # |L| (T non-increasing, strictly while the slope exceeds one unit:
+    # x < 77) and |L| = 127 (~16 natural units) is certain to 2^-16
+    # (T(127) = 0); T(8 ln 3) would be 2^16 log2(4/3), bracketed by the
+    # integer neighbours of 8 ln 3 = 8.79
+    T = orc.mi_table()
+    assert T[0] == 65536 and T[127] == 0
+    assert np.all(np.diff(T[:77]) < 0) and np.all(np.diff(T) <= 0)
+    target = 65536 * np.log2(4.0 / 3.0)
+    assert T[9] < target < T[8]
+
+
+def test_mi_stop_rule(orc):
+    # the mutual-information rule stops no earlier than iteration 2; the
+    # stop changes no arithmetic (decoding exactly that many iterations
+    # without a stop rule gives the same bits and CRC outcome); a noiseless
+    # block converges at once (MI = 1 after iterations 1 and 2); an
+    # undecodable one stops early and reports the failure convention
+    A, G = 2000, 6144
+    a = synth.bits(4, 0, A)
+    e = orc.encode_tb(a, G, Qm=2)
+    bits, res, _ = orc.decode_tb(noiseless(e), A, G, Qm=2, max_iter=8, early_stop=2)
+    assert res["cb_iters"] == [2] and res["tb_crc_ok"] and np.array_equal(bits, a)
+    for snr in (-2.0, 1.0, 2.0, 4.0):
+        llr = synth.channel_llrs(e, 2, synth.sigma2_snr(snr), 4, int(10 * snr) + 50)
+        b_mi, r_mi, _ = orc.decode_tb(llr, A, G, Qm=2, max_iter=8, early_stop=2)
+        t = r_mi["cb_iters"][0]
+        ran = t if t <= 8 else None
+        if ran is None:
+            # failed: find how many iterations ran from the fixed-count runs
+            # (the first t >= 2 whose outcome is the same failure)
+            assert not r_mi["tb_crc_ok"]
+            continue
+        assert t >= 2 and r_mi["tb_crc_ok"]
+        b_fix, r_fix, _ = orc.decode_tb(llr, A, G, Qm=2, max_iter=t, early_stop=False)
+        assert np.array_equal(b_mi, b_fix) and r_fix["tb_crc_ok"]
+    noise = synth.randint(4, 2, G, -127, 127).astype(np.int8)
+    _, r, _ = orc.decode_tb(noise, A, G, Qm=2, max_iter=8, early_stop=2)
+    assert r["cb_iters"] == [9] and not r["tb_crc_ok"]
