@@ -574,15 +574,18 @@ int orc_siso_once(int K, int P, const int8_t* Ls, const int8_t* Lp, const int16_
 }
 
 /* ------------------------------------------------------------------ */
-/* Mutual information of the a-posteriori LLRs (Sec. IV-B "Decoding    */
+/* Mutual information of the exchanged LLRs (Sec. IV-B "Decoding       */
 /* function": the paper stops when the average mutual information of   */
-/* the LLRs converges).  Reading: for an LLR L in natural units, the    */
-/* information a bit carries is 1 - log2(1 + exp(-|L|)); the decoder's */
-/* LLRs carry 8 fixed-point units per natural unit (the LLR scale       */
-/* 8 * 2y / sigma^2 of the inputs).  In integers, with 2^16 = 1 bit:    */
+/* the LLRs converges, without naming which LLRs).  Reading: the        */
+/* extrinsic LLRs the decoders exchange, i.e. the a-priori La1 the next */
+/* iteration would use (scale(Le2), natural order), whose mutual        */
+/* information is what iterative-decoding convergence tracks.  For an   */
+/* LLR L in natural units a bit carries 1 - log2(1 + exp(-|L|)); the    */
+/* decoder's LLRs carry 8 fixed-point units per natural unit (the input */
+/* scale 8 * 2y / sigma^2).  In integers, with 2^16 = 1 bit:            */
 /*   T(x) = round(2^16 * log2(1 + exp(-x / 8))), x = min(|L|, 127)     */
 /* (T(127) already rounds to 0), and the sum over a CB                 */
-/*   S = sum_k (2^16 - T(min(|Lambda2_k|, 127))).                      */
+/*   S = sum_k (2^16 - T(min(|La1_k|, 127))).                          */
 /* Stop rule: after iteration t >= 2, stop when the mean changed by at  */
 /* most 2^-10 bit: |S_t - S_(t-1)| * 2^10 <= K * 2^16.                 */
 /* ------------------------------------------------------------------ */
@@ -593,11 +596,11 @@ int orc_mi_table(int32_t* T, int n)
     return 0;
 }
 
-static int64_t mi_sum(const int16_t* Lam, int K, const int32_t* T)
+static int64_t mi_sum(const int16_t* L, int K, const int32_t* T)
 {
     int64_t S = 0;
     for (int k = 0; k < K; k++) {
-        int x = Lam[k] < 0 ? -(int)Lam[k] : (int)Lam[k];
+        int x = L[k] < 0 ? -(int)L[k] : (int)L[k];
         if (x > 127) x = 127;
         S += 65536 - T[x];
     }
@@ -665,7 +668,7 @@ int orc_turbo_decode_cb(const int8_t* d0, const int8_t* d1, const int8_t* d2, in
             ok = (orc_crc24(msg, K - F, crc_type) == 0);
         }
         if (early_stop == 2) {
-            const int64_t S = mi_sum(Lam, K, T);
+            const int64_t S = mi_sum(La1, K, T);
             const int64_t dS = S > S_prev ? S - S_prev : S_prev - S;
             const int converged = it >= 2 && dS * 1024 <= (int64_t)K * 65536;
             S_prev = S;
