@@ -71,7 +71,12 @@ typedef struct crnt_tb_params {
     uint8_t NL;          /* 1 or 2 layers */
     uint8_t rv;          /* redundancy version 0..3 */
     uint8_t max_iter;    /* 1..16 turbo iterations */
-    uint8_t early_stop;  /* 1: stop each CB at its first CRC pass */
+    uint8_t early_stop;  /* stop rule per CB: 0 none (max_iter iterations),
+                            1 at its first CRC pass, 2 when the mean mutual
+                            information of the exchanged extrinsic LLRs changes
+                            by at most 2^-10 bit between iterations (the
+                            paper's rule, Sec. IV-B; the CRC then only decides
+                            success) */
     uint8_t new_data;    /* 1: clear the HARQ soft buffer before combining */
     uint32_t cell, ue, harq_pid; /* HARQ process key (flags bit 0 set) */
     uint32_t flags;      /* bit 0 (CRNT_F_HARQ): combine into the library-owned

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <chrono>
 #include <cstdint>
 #include <cstring>
@@ -214,7 +215,7 @@ int validate(const crnt_tb_params& t, lte::Seg* seg) {
   if (t.A < 16 || t.A > 75376 || (t.A & 7)) return CRNT_EINVAL;
   if (t.Qm != 2 && t.Qm != 4 && t.Qm != 6) return CRNT_EINVAL;
   if (t.NL != 1 && t.NL != 2) return CRNT_EINVAL;
-  if (t.rv > 3 || t.max_iter < 1 || t.max_iter > 16) return CRNT_EINVAL;
+  if (t.rv > 3 || t.max_iter < 1 || t.max_iter > 16 || t.early_stop > 2) return CRNT_EINVAL;
   if (t.G == 0 || t.G % (t.Qm * t.NL)) return CRNT_EINVAL;
   if (!lte::segment((int)t.A + 24, seg) || seg->C > CRNT_MAX_CB) return CRNT_EINVAL;
   if (lte::e_r((int)t.G, t.Qm, t.NL, seg->C, 0) < 1) return CRNT_EINVAL;
@@ -432,7 +433,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     d.dbg_off = (int32_t)(pr.dbg + sumK + 4 * r);
     d.crc_b = s.C > 1;
     d.max_iter = tp.max_iter;
-    d.early_stop = tp.early_stop ? 1 : 0;
+    d.early_stop = tp.early_stop;  // 0 none, 1 CRC, 2 mutual information
     d.new_data = tp.new_data ? 1 : 0;
     d.purge = (tp.flags & CRNT_F_PURGE) && s.C > 1 ? 1 : 0;
     memset(d.pad0, 0, sizeof d.pad0);
@@ -460,7 +461,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     pl->items.push_back(wi);
   }
   pl->n_cb = ncb;
-  pl->smem = 2048 + max_slot_bytes;
+  pl->smem = kSmemFixed + max_slot_bytes;
   static std::mutex occ_mu;
   static std::map<int, int> occ_cache;  // dynamic smem -> resident CTAs per SM
   int per_sm;
@@ -512,6 +513,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   p.tb_ok = p.cb_ok + ncb;
   p.xpowA = ctx->xpowA;
   p.xpowB = ctx->xpowB;
+  p.mi_tab = ctx->mi_tab;
   return CRNT_OK;
 }
 
@@ -652,10 +654,16 @@ int crnt_create(crnt_ctx** out, const crnt_config* cfg) {
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   std::vector<uint32_t> xa = xpow_table(kGA, kXpowA), xb = xpow_table(kGB, kXpowB);
+  // mutual-information stop rule: T(x) = round(2^16 log2(1 + exp(-x/8)))
+  int32_t mi[kMiTable];
+  for (int x = 0; x < kMiTable; x++)
+    mi[x] = (int32_t)std::floor(65536.0 * std::log2(1.0 + std::exp(-(double)x / 8.0)) + 0.5);
   if (cudaMalloc(&c->xpowA, 4 * kXpowA) != cudaSuccess ||
       cudaMalloc(&c->xpowB, 4 * kXpowB) != cudaSuccess ||
+      cudaMalloc(&c->mi_tab, sizeof mi) != cudaSuccess ||
       cudaMemcpy(c->xpowA, xa.data(), 4 * kXpowA, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->xpowB, xb.data(), 4 * kXpowB, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->mi_tab, mi, sizeof mi, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
     crnt_destroy(c);
     return CRNT_EDEVICE;
@@ -682,6 +690,7 @@ int crnt_destroy(crnt_ctx* ctx) {
   ctx->stage_out.release();
   if (ctx->xpowA) cudaFree(ctx->xpowA);
   if (ctx->xpowB) cudaFree(ctx->xpowB);
+  if (ctx->mi_tab) cudaFree(ctx->mi_tab);
   if (ctx->harq.arena) cudaFree(ctx->harq.arena);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

@@ -15,6 +15,11 @@ constexpr int kSmemBudget = 72 * 1024; // dynamic smem per decode CTA
 constexpr int kMaxP = kThreads;        // windows per SISO pass (one thread each)
 constexpr int kSub = 4;                // sub-window length of the alpha recompute
 constexpr int kMaxK = 6144;
+// Fixed shared memory of a decode CTA ahead of the CB slots: the CRC24A /
+// CRC24B byte tables (2 x 256 words) and the mutual-information table (128
+// words).
+constexpr int kSmemFixed = 2048 + 512;
+constexpr int kMiTable = 128;
 constexpr int kMaxCb = 16;
 
 // One code block of a batch, fixed at plan time.
@@ -79,6 +84,7 @@ struct DecParams {
   uint8_t* tb_ok;         // [n_tbs]
   const uint32_t* xpowA;  // x^(32 s) mod gCRC24A, s < 2400
   const uint32_t* xpowB;  // x^(32 s) mod gCRC24B, s < 200
+  const int32_t* mi_tab;  // [kMiTable] mutual-information table (stop rule 2)
   int8_t* dbg_d;          // optional: [sum (K+4)] x 3 d-streams per CB
   int16_t* dbg_ext;       // optional: [sum K] final extrinsic, natural order
   uint8_t* dbg_hard;      // optional: [sum K] hard decisions
@@ -124,7 +130,7 @@ __host__ __device__ inline int dec_cb_smem(int K, int P, int W) {
          + align16(4 * nwords)          // hard bits
          + 4 * P * 16                   // alpha/beta seeds of both decoders
          + P * nck * 16                 // alpha checkpoints
-         + 32;                          // per-CB flags
+         + 64;                          // per-CB flags
 }
 
 }  // namespace crnt

@@ -237,6 +237,10 @@ __device__ __forceinline__ int qpp_at(int x, int f1, int f2, int K) {
   t = (t * x) % K;
   return (t + f1 * x) % K;
 }
+// Dynamic shared memory of the decode kernel: CRC tables (2 KiB), the
+// mutual-information table, then the CB slots.
+extern __shared__ __align__(16) uint8_t smem[];
+
 struct CbSlot {
   int8_t* sys;
   int8_t* par1;
@@ -247,7 +251,8 @@ struct CbSlot {
   uint4* seed;   // [4][P]: alpha dec0, alpha dec1, beta dec0, beta dec1
   uint4* ck;     // [P][nck]
   int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|,
-                 // [6] stopped by a purge
+                 // [6] stopped by a purge, [8] / [9] mutual information of this / the
+                 // previous iteration (2^16 units per bit, summed over the CB)
 };
 __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
   CbSlot s;
@@ -365,6 +370,8 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     sl.flags[4] = 0;
     sl.flags[5] = 0;
     sl.flags[6] = 0;
+    sl.flags[8] = 0;
+    sl.flags[9] = 0;
   }
 }
 
@@ -680,15 +687,17 @@ __device__ uint32_t crc_share(const CbDesc& d, const CbSlot& sl, int p, const ui
 }
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams prm) {
-  extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_item;
   __shared__ int s_remaining;
   __shared__ int s_maxit;
   uint32_t* tabA = (uint32_t*)smem;
   uint32_t* tabB = tabA + 256;
-  uint8_t* slots = smem + 2048;
+  int* mi_tab = (int*)(smem + 2048);
+  uint8_t* slots = smem + kSmemFixed;
   const int tid = threadIdx.x;
 
+  if (prm.mi_tab)
+    for (int i = tid; i < kMiTable; i += kThreads) mi_tab[i] = __ldg(&prm.mi_tab[i]);
   for (int i = tid; i < 512; i += kThreads) {
     const uint32_t g = (i < 256) ? GA : GB;
     uint32_t r = (uint32_t)(i & 255) << 16;
@@ -770,13 +779,31 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
         const uint32_t r = crc_share(d, sl, p, d.crc_b ? tabB : tabA, d.crc_b ? GB : GA,
                                      d.crc_b ? prm.xpowB : prm.xpowA, 0);
         if (r) atomicXor((unsigned*)&fl[2], r);
+        if (d.early_stop == 2) {
+          // stop rule 2: mutual information of the a-priori LLRs the next
+          // iteration would use (the scaled extrinsics of decoder 2, held in
+          // the ext array; its padding entries are 0 and add nothing)
+          int mi = 0;
+          for (int t = p; t < d.W * d.P; t += d.P)
+            mi += 65536 - mi_tab[min(abs((int)sl.ext[t]), kMiTable - 1)];
+          atomicAdd(&fl[8], mi);
+        }
       }
       __syncthreads();
       if (run && p == 0) {
         const bool ok = check && fl[2] == 0;
         fl[2] = 0;
         const int tb = dp->tb;
-        if (ok || it == my_max) {
+        bool stop = ok || it == my_max;
+        if (dp->early_stop == 2) {
+          // mutual-information rule: stop once the mean changed by at most
+          // 2^-10 bit (from iteration 2); the CRC decides success
+          const int S = fl[8], dS = abs(S - fl[9]);
+          stop = (it >= 2 && (long long)dS * 1024 <= (long long)dp->K * 65536) || it == my_max;
+          fl[9] = S;
+          fl[8] = 0;
+        }
+        if (stop) {
           fl[0] = 1;
           fl[1] = ok ? it : my_max + 1;
           atomicSub(&s_remaining, 1);
@@ -855,7 +882,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
 
 }  // namespace
 
-int decode_max_smem() { return kSmemBudget + 2048; }
+int decode_max_smem() { return kSmemBudget + kSmemFixed; }
 
 static cudaError_t set_attr() {
   return cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

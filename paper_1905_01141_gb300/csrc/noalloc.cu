@@ -195,6 +195,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     rc = validate(tp, &sg);
     if (rc) return rc;
     if (tp.flags & CRNT_F_HARQ) return CRNT_EINVAL;  // no soft-buffer arena here
+    if (tp.early_stop > 1) return CRNT_EINVAL;       // no mutual-information table here
     if (ncb + sg.C > kStaticCbs) return CRNT_ENOMEM;
     TbDesc& td = h_tbs[t];
     memset(&td, 0, sizeof td);
@@ -286,7 +287,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     }
     max_slot = std::max(max_slot, wi.n * slot);
   }
-  const int smem = 2048 + max_slot;
+  const int smem = kSmemFixed + max_slot;
   const int per_sm = decode_occupancy(smem);
   if (per_sm < 1) return CRNT_EDEVICE;
   const int grid = std::min(nitems, per_sm * g_num_sms[dev]);

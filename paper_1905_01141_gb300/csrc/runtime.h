@@ -70,6 +70,7 @@ struct crnt_ctx {
   int num_sms = 0;
   uint32_t* xpowA = nullptr;
   uint32_t* xpowB = nullptr;
+  int32_t* mi_tab = nullptr;  // [kMiTable] table of the mutual-information stop rule
   crnt::HarqPool harq;
   std::mutex harq_mu;     // guards harq
   std::mutex stage_mu;    // guards the staging buffers and the cached plan

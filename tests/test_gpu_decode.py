@@ -268,3 +268,18 @@ def test_purge_on_failure(orc, crnt_lib, ctx):
             else:
                 assert it == c[3] and crc == (c[3] <= 6)
     print("CBs stopped by purges:", stopped)
+
+
+def test_mi_stop_rule_matches_oracle(orc, crnt_lib, ctx):
+    # stop rule 2 (the paper's mutual-information rule): per CB iterations,
+    # hard decisions, extrinsics and CRC results bit-exact with the oracle,
+    # over SNRs where blocks decode quickly, slowly or not at all
+    shapes = synth.tti_batch(seed=29, n_tb=24, amax=40000)
+    specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=8, early_stop=2, seed=950 + i,
+                  snr=s["snr_db"]) for i, s in enumerate(shapes)]
+    specs.append(dict(A=6120, G=18444, Qm=2, P=1, max_iter=8, early_stop=2, seed=990, ebn0=0.5))
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
+    iters = [it for r in g["res"] for it in r["cb_iters"]]
+    assert min(iters) >= 2 and len(set(iters)) > 2
