@@ -56,7 +56,9 @@ def parse():
                     help="load the window table from this file instead of measuring it")
     ap.add_argument("--save-tune", default=None, help="write the window table to this file")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
-    ap.add_argument("--sweep", choices=["bler"], help="quality sweep instead of the bench line")
+    ap.add_argument("--sweep", choices=["bler", "stop"],
+                    help="quality sweep instead of the bench line (stop: CRC vs mutual "
+                         "information stop rule)")
     ap.add_argument("--bler-cbs", type=int, default=0,
                     help="CBs per (K, P, Eb/N0) point (0: 1e6 for K=40, 1e5 for K=6144 "
                          "with P>=16, 2e4 for P=4 and 1e4 for P=1)")
@@ -578,13 +580,14 @@ def encoder_rate(crnt, ctx, dev, tbs, pay):
                     "encoding, rate matching), device buffers, wall time incl. planning"}
 
 
-def bler_sweep(args):
-    """Stress and quality sweep: BLER and mean iterations per (K, P, Eb/N0)
-    for single-CB TBs (A = K - 24, rate 1/3 without puncturing, BPSK), max 8
-    iterations with CRC stop, P in {1, 4, 16, 64}.  Payloads and noise are
-    drawn on the GPU (torch), encoded by the library's encoder and decoded by
-    its decoder; a small seeded subsample per point is also decoded by the
-    CPU oracle from oracle-encoded inputs and compared CB by CB."""
+def bler_sweep(args, ks=(6144, 40), ps=(1, 4, 16, 64), stops=(1,)):
+    """Stress and quality sweep: BLER and mean iterations per (K, P, Eb/N0,
+    stop rule) for single-CB TBs (A = K - 24, rate 1/3 without puncturing,
+    BPSK), max 8 iterations, P in {1, 4, 16, 64}; stop rule 1 = CRC, 2 = the
+    paper's mutual-information rule.  Payloads and noise are drawn on the GPU
+    (torch), encoded by the library's encoder and decoded by its decoder; a
+    small seeded subsample per point is also decoded by the CPU oracle from
+    oracle-encoded inputs and compared CB by CB."""
     import torch
 
     import paper_1905_01141_gb300 as crnt
@@ -598,9 +601,9 @@ def bler_sweep(args):
     pts = []
     ebn0s = [0.25 * i for i in range(9)]
     with crnt.Context(0) as ctx:
-        for K in (6144, 40):
+        for K, P, stop in [(k, p, st) for k in ks for p in ps for st in stops]:
             A, G = K - 24, 3 * (K + 4)
-            for P in (1, 4, 16, 64):
+            if True:
                 if args.bler_cbs:
                     ncb = args.bler_cbs
                 elif K == 40:
@@ -608,7 +611,7 @@ def bler_sweep(args):
                 else:
                     ncb = {1: 10000, 4: 20000}.get(P, 100000)
                 chunk = min(ncb, 65536 if K == 40 else 4096)
-                tb = dict(A=A, G=G, Qm=2, P=P, max_iter=8, early_stop=1)
+                tb = dict(A=A, G=G, Qm=2, P=P, max_iter=8, early_stop=stop)
                 plan = ctx.plan([tb] * chunk)
                 for eb in ebn0s:
                     sig2 = synth.sigma2_ebn0(eb, A / G)
@@ -637,7 +640,7 @@ def bler_sweep(args):
                         right = (out.view(chunk, A // 8) == pay).all(dim=1)
                         errs += int((~right).sum())
                         undetected += int((ok & ~right).sum())
-                        iters += float(np.minimum(res["cb_iters"][:, 0], 8).sum())
+                        iters += float(res["cb_iters_run"][:, 0].sum())
                         done += chunk
                     # oracle agreement on a seeded subsample at this point
                     agree = 0
@@ -647,12 +650,14 @@ def bler_sweep(args):
                         e = oracle.encode_tb(a, G, Qm=2)
                         llr_o = synth.channel_llrs(e, 1, sig2, args.seed + 17, 7000 + j)
                         Pe = min(P, K // 8)
-                        bo, ro, _ = oracle.decode_tb(llr_o, A, G, Qm=2, P=Pe, max_iter=8)
+                        bo, ro, _ = oracle.decode_tb(llr_o, A, G, Qm=2, P=Pe, max_iter=8,
+                                                     early_stop=stop)
                         od = torch.empty(A // 8, dtype=torch.uint8, device=dev)
                         rg = ctx.decode_batch([tb], torch.from_numpy(llr_o).to(dev), od)[0]
                         agree += int(rg["cb_iters"] == ro["cb_iters"] and
                                      np.array_equal(np.unpackbits(od.cpu().numpy()), bo))
                     pts.append({"K": K, "P": P, "P_eff": min(P, K // 8), "ebn0_db": eb,
+                                "stop": {1: "crc", 2: "mutual information"}[stop],
                                 "cbs": done, "bler": errs / done,
                                 "undetected": undetected, "mean_iters": iters / done,
                                 "seconds": round(time.perf_counter() - t0, 2),
@@ -666,6 +671,10 @@ def main():
     args = parse()
     if args.sweep == "bler":
         bler_sweep(args)
+        return
+    if args.sweep == "stop":
+        # the two stop rules side by side: BLER and mean iterations
+        bler_sweep(args, ks=(6144,), ps=(1, 16, 64), stops=(1, 2))
         return
     if args.impl == "reference":
         run_reference(args)

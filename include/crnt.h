@@ -93,7 +93,7 @@ typedef struct crnt_tb_params {
  * depends on timing; TBs that decode are never affected. */
 #define CRNT_F_PURGE 2u
 
-/* Per-TB result (80 bytes). */
+/* Per-TB result (96 bytes). */
 typedef struct crnt_tb_result {
     int32_t status;                 /* CRNT_OK or a negative code for this TB */
     uint8_t tb_crc_ok;              /* 1: every CB CRC and the TB CRC24A passed */
@@ -102,6 +102,9 @@ typedef struct crnt_tb_result {
     uint8_t cb_iters[CRNT_MAX_CB];  /* iterations run per CB; max_iter+1 = failure
                                        (the paper's loss convention, Sec. IV-B) */
     uint8_t cb_crc_ok[CRNT_MAX_CB];
+    uint8_t cb_iters_run[CRNT_MAX_CB]; /* iterations actually run per CB (a failure
+                                       under a stop rule may stop before max_iter;
+                                       a purged CB reports the ones it ran) */
     uint16_t P_used;                /* window count requested after clamping, for K+ */
     uint16_t pad0;
     uint64_t ticket;                /* serving ticket (0 elsewhere) */

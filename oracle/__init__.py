@@ -71,7 +71,7 @@ def lib():
                 "orc_windows": (I, [I, I]),
                 "orc_siso_once": (I, [I, I, P, P, P, P, P, P, P]),
                 "orc_siso_seeded": (I, [I, I, P, P, P, P, P, I, P, P, P, P]),
-                "orc_turbo_decode_cb": (I, [P, P, P, I, I, I, I, I, I, P, P]),
+                "orc_turbo_decode_cb": (I, [P, P, P, I, I, I, I, I, I, P, P, P]),
                 "orc_tb_ncb_total": (I, [I]),
                 "orc_encode_tb": (I, [P, I, I, I, I, I, P]),
                 "orc_decode_tb": (I, [P, I, I, I, I, I, I, I, I, I, P, P, P]),
@@ -248,19 +248,21 @@ def mi_table(n=128):
     return t
 
 
-def turbo_decode_cb(d0, d1, d2, F=0, crc="A", P=1, max_iter=6, early_stop=True):
-    """Returns (iterations, hard bits [K], extrinsic [K]).  early_stop: False
-    (none), True (CRC) or 2 (mutual information)."""
+def turbo_decode_cb(d0, d1, d2, F=0, crc="A", P=1, max_iter=6, early_stop=True, runs=False):
+    """Returns (iterations, hard bits [K], extrinsic [K]) -- plus the
+    iterations actually run when runs=True.  early_stop: False (none), True
+    (CRC) or 2 (mutual information)."""
     d0, d1, d2 = _i8(d0), _i8(d1), _i8(d2)
     K = len(d0) - 4
     hard = np.zeros(K, dtype=np.uint8)
     ext = np.zeros(K, dtype=np.int16)
     ct = {"A": 0, "B": 1, None: -1}[crc]
+    ran = ctypes.c_int(0)
     it = lib().orc_turbo_decode_cb(_p(d0), _p(d1), _p(d2), K, F, ct, P, max_iter,
-                                   _stop(early_stop), _p(hard), _p(ext))
+                                   _stop(early_stop), _p(hard), _p(ext), ctypes.byref(ran))
     if it < 0:
         raise RuntimeError("orc_turbo_decode_cb failed")
-    return it, hard, ext
+    return (it, hard, ext, ran.value) if runs else (it, hard, ext)
 
 
 def tb_ncb_total(A):

@@ -620,10 +620,11 @@ static int64_t mi_sum(const int16_t* L, int K, const int32_t* T)
 /*   hard[K]: hard decisions of the last iteration run.                */
 /*   ext[K] (optional): extrinsic a-priori for SISO1 after the last    */
 /*   iteration run, scale(Le2) in natural order.                       */
+/*   iters_run (optional): iterations actually run.                    */
 /* ------------------------------------------------------------------ */
 int orc_turbo_decode_cb(const int8_t* d0, const int8_t* d1, const int8_t* d2, int K, int F,
                         int crc_type, int P, int max_iter, int early_stop, uint8_t* hard,
-                        int16_t* ext)
+                        int16_t* ext, int* iters_run)
 {
     int* pi = qpp_table(K);
     if (!pi) return -1;
@@ -654,7 +655,9 @@ int orc_turbo_decode_cb(const int8_t* d0, const int8_t* d1, const int8_t* d2, in
     int32_t T[128];
     orc_mi_table(T, 128);
     int64_t S_prev = 0;
+    int ran = 0;
     for (int it = 1; it <= max_iter; it++) {
+        ran = it;
         siso(K, d0, d1, La1, ts1, tp1, &s1, Lam, Le);
         for (int i = 0; i < K; i++) La2[i] = (int16_t)scale_ext(Le[pi[i]]);
         siso(K, Ls2, d2, La2, ts2, tp2, &s2, Lam, Le);
@@ -681,6 +684,7 @@ int orc_turbo_decode_cb(const int8_t* d0, const int8_t* d1, const int8_t* d2, in
         if (ok && (early_stop || it == max_iter)) { result = it; break; }
     }
     if (ext) memcpy(ext, La1, (size_t)K * 2);
+    if (iters_run) *iters_run = ran;
     free(pi); free(Ls2); free(La1); free(La2); free(Lam); free(Le); free(msg);
     free(s1.aseed); free(s1.bseed); free(s2.aseed); free(s2.bseed);
     return result;
@@ -780,7 +784,7 @@ int orc_decode_tb(const int8_t* llr, int A, int G, int Qm, int NL, int rv, int P
         uint8_t* hard = malloc((size_t)K);
         orc_derm_cb(llr + eoff, E, K, F, rv, new_data, soft + soff, d0, d1, d2);
         int it = orc_turbo_decode_cb(d0, d1, d2, K, F, s.C == 1 ? 0 : 1, P, max_iter, early_stop,
-                                     hard, NULL);
+                                     hard, NULL, NULL);
         res->cb_iters[r] = it;
         res->cb_crc_ok[r] = (it <= max_iter);
         all_ok &= res->cb_crc_ok[r];

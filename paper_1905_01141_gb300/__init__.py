@@ -48,6 +48,7 @@ class TbResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("tb_crc_ok", ctypes.c_uint8), ("C", ctypes.c_uint8),
                 ("K_plus", ctypes.c_uint16), ("K_minus", ctypes.c_uint16), ("F", ctypes.c_uint16),
                 ("cb_iters", ctypes.c_uint8 * MAX_CB), ("cb_crc_ok", ctypes.c_uint8 * MAX_CB),
+                ("cb_iters_run", ctypes.c_uint8 * MAX_CB),
                 ("P_used", ctypes.c_uint16), ("pad0", ctypes.c_uint16),
                 ("ticket", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
                 ("t_start_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
@@ -56,7 +57,8 @@ class TbResult(ctypes.Structure):
         C = self.C
         return dict(status=self.status, tb_crc_ok=bool(self.tb_crc_ok), C=C, Kp=self.K_plus,
                     Km=self.K_minus, F=self.F, cb_iters=list(self.cb_iters[:C]),
-                    cb_crc_ok=[bool(x) for x in self.cb_crc_ok[:C]], P_used=self.P_used,
+                    cb_crc_ok=[bool(x) for x in self.cb_crc_ok[:C]],
+                    cb_iters_run=list(self.cb_iters_run[:C]), P_used=self.P_used,
                     ticket=self.ticket, t_submit_ns=self.t_submit_ns,
                     t_start_ns=self.t_start_ns, t_done_ns=self.t_done_ns)
 

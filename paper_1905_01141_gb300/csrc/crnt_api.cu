@@ -355,7 +355,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   pl->zero_off = off_zero;
   pl->scratch_zero = s_state + s_done + s_crc;
   const size_t off_res = off_zero + pl->scratch_zero;
-  pl->res_bytes = (2 * (size_t)ncb + n + 15) & ~size_t(15);
+  pl->res_bytes = (3 * (size_t)ncb + n + 15) & ~size_t(15);
   const size_t off_items = off_res + pl->res_bytes;
   const size_t max_desc = off_items + sizeof(WorkItem) * ncb;
   // The previous upload from h_desc must have completed before the staging
@@ -509,8 +509,9 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   p.tb_done = (int32_t*)(dd + off_zero + s_state);
   p.tb_crc = (uint32_t*)(dd + off_zero + s_state + s_done);
   p.cb_iters = dd + off_res;
+  p.cb_runs = p.cb_iters + 2 * (size_t)ncb;
   p.cb_ok = p.cb_iters + ncb;
-  p.tb_ok = p.cb_ok + ncb;
+  p.tb_ok = p.cb_iters + 3 * (size_t)ncb;  // cb_iters | cb_ok | cb_runs | tb_ok
   p.xpowA = ctx->xpowA;
   p.xpowB = ctx->xpowB;
   p.mi_tab = ctx->mi_tab;
@@ -519,7 +520,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
 
 bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs) {
   const size_t zero = 256 + al256(4 * (size_t)max_tbs) + al256(8 * (size_t)max_tbs);
-  const size_t res = (2 * (size_t)max_cbs + max_tbs + 15) & ~size_t(15);
+  const size_t res = (3 * (size_t)max_cbs + max_tbs + 15) & ~size_t(15);
   const size_t desc = al256(sizeof(CbDesc) * max_cbs) + al256(sizeof(TbDesc) * max_tbs) + zero +
                       res + sizeof(WorkItem) * max_cbs;
   return pl->d_desc.ensure(desc) && pl->h_desc.ensure(desc) && pl->h_res.ensure(zero + res);
@@ -568,12 +569,13 @@ void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res) {
     r.K_minus = (uint16_t)sg.Km;
     r.F = (uint16_t)sg.F;
     r.P_used = pl->p_used[t];
-    r.tb_crc_ok = h[2 * ncb + t];
+    r.tb_crc_ok = h[3 * ncb + t];
   }
   for (size_t i = 0; i < ncb; i++) {
     crnt_tb_result& r = res[pl->cb_tb[i]];
     r.cb_iters[pl->cb_r[i]] = h[i];
     r.cb_crc_ok[pl->cb_r[i]] = h[ncb + i];
+    r.cb_iters_run[pl->cb_r[i]] = h[2 * ncb + i];
   }
 }
 

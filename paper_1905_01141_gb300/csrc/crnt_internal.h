@@ -81,6 +81,7 @@ struct DecParams {
   uint32_t* tb_crc;       // [n_tbs] xor of CRC24A contributions
   uint8_t* cb_iters;      // [n_cbs] by sorted CB index
   uint8_t* cb_ok;         // [n_cbs]
+  uint8_t* cb_runs;       // [n_cbs] iterations run (may be null)
   uint8_t* tb_ok;         // [n_tbs]
   const uint32_t* xpowA;  // x^(32 s) mod gCRC24A, s < 2400
   const uint32_t* xpowB;  // x^(32 s) mod gCRC24B, s < 200

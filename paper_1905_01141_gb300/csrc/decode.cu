@@ -252,7 +252,8 @@ struct CbSlot {
   uint4* ck;     // [P][nck]
   int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|,
                  // [6] stopped by a purge, [8] / [9] mutual information of this / the
-                 // previous iteration (2^16 units per bit, summed over the CB)
+                 // previous iteration (2^16 units per bit, summed over the CB),
+                 // [10] iterations run
 };
 __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
   CbSlot s;
@@ -806,6 +807,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
         if (stop) {
           fl[0] = 1;
           fl[1] = ok ? it : my_max + 1;
+          fl[10] = it;
           atomicSub(&s_remaining, 1);
           // a failed CB fails its TB: flag it now (the TB CRC step flags it
           // again) so that purging CBs of the TB can stop
@@ -814,6 +816,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
           fl[0] = 1;
           fl[1] = 0;
           fl[6] = 1;
+          fl[10] = it;
           atomicSub(&s_remaining, 1);
         }
       }
@@ -854,6 +857,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
     __syncthreads();
     if (mine && p == 0) {
       prm.cb_iters[sorted_idx] = (uint8_t)sl.flags[1];
+      if (prm.cb_runs) prm.cb_runs[sorted_idx] = (uint8_t)sl.flags[10];
       prm.cb_ok[sorted_idx] = cb_ok ? 1 : 0;
       const TbDesc tb = prm.tbs[d.tb];
       if (tb.C == 1) {

@@ -338,6 +338,9 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
   for (int i = 0; i < ncb; i++) {
     res[h_cb_tb[i]].cb_iters[h_cb_r[i]] = h_res[i];
     res[h_cb_tb[i]].cb_crc_ok[h_cb_r[i]] = h_res[ncb + i];
+    // stop rules 0 and 1 only: a failure ran all max_iter iterations
+    const int mi = tbs[h_cb_tb[i]].max_iter;
+    res[h_cb_tb[i]].cb_iters_run[h_cb_r[i]] = (uint8_t)std::min((int)h_res[i], mi);
   }
   return CRNT_OK;
 }

@@ -48,7 +48,8 @@ def run_gpu(crnt, ctx, tbs, llr_cat, debug=True):
 def oracle_tb(orc, crnt, tb, llr, soft=None):
     """Oracle decode of one TB CB by CB, with the library's per-CB window
     counts (reported by crnt_tb_layout, which needs no GPU).  Returns per-CB
-    (d0, d1, d2, iters, hard, ext), the A payload bits, tb_ok and the soft
+    (d0, d1, d2, iters, hard, ext, iterations run), the A payload bits, tb_ok
+    and the soft
     buffer."""
     lay = crnt.tb_layout(tb)
     A, G, Qm, NL, rv = tb["A"], tb["G"], tb.get("Qm", 2), tb.get("NL", 1), tb.get("rv", 0)
@@ -68,11 +69,12 @@ def oracle_tb(orc, crnt, tb, llr, soft=None):
         else:
             d0, d1, d2, sb2 = orc.derm_cb(e, c["K"], c["F"], rv, soft=sb.copy())
         soft[c["soft_offset"]:c["soft_offset"] + c["Ncb"]] = sb2
-        it, hard, ext = orc.turbo_decode_cb(d0, d1, d2, F=c["F"], crc="B" if C > 1 else "A",
-                                            P=c["P"], max_iter=tb.get("max_iter", 6),
-                                            early_stop=tb.get("early_stop", 1))
+        it, hard, ext, ran = orc.turbo_decode_cb(d0, d1, d2, F=c["F"],
+                                                 crc="B" if C > 1 else "A", P=c["P"],
+                                                 max_iter=tb.get("max_iter", 6),
+                                                 early_stop=tb.get("early_stop", 1), runs=True)
         ok_all &= it <= tb.get("max_iter", 6)
-        cbs.append((d0, d1, d2, it, hard, ext))
+        cbs.append((d0, d1, d2, it, hard, ext, ran))
         payload.append(hard[c["F"]:c["K"] - L])
     b = np.concatenate(payload)
     tb_ok = bool(ok_all and orc.crc24(b, "A") == 0)
@@ -105,7 +107,7 @@ def check_batch(orc, crnt, tbs, llrs, g, sample=None):
         cbs, bits, tb_ok, _ = oracle_tb(orc, crnt, tb, llrs[t])
         res = g["res"][t]
         assert res["C"] == len(cbs)
-        for r, (d0, d1, d2, it, hard, ext) in enumerate(cbs):
+        for r, (d0, d1, d2, it, hard, ext, ran) in enumerate(cbs):
             K = len(hard)
             o = dbg_off[cb_index[t] + r]
             D = K + 4
@@ -119,6 +121,7 @@ def check_batch(orc, crnt, tbs, llrs, g, sample=None):
                                                   res["cb_iters"][r], it)
                 assert np.array_equal(ge, ext), ("ext", t, r, _diff(ge, ext))
             assert res["cb_iters"][r] == it, ("iters", t, r, res["cb_iters"][r], it)
+            assert res["cb_iters_run"][r] == ran, ("run", t, r, res["cb_iters_run"][r], ran)
             assert res["cb_crc_ok"][r] == (it <= tb.get("max_iter", 6)), ("cbok", t, r)
         assert res["tb_crc_ok"] == tb_ok, ("tbok", t)
         got = np.unpackbits(g["out"][out_off[t]:out_off[t + 1]])

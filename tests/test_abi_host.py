@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(crnt_lib):
 
 def test_struct_sizes(crnt_lib):
     assert ctypes.sizeof(crnt_lib.TbParams) == 32
-    assert ctypes.sizeof(crnt_lib.TbResult) == 80
+    assert ctypes.sizeof(crnt_lib.TbResult) == 96
     assert ctypes.sizeof(crnt_lib.CbLayout) == 40
     assert crnt_lib.version() == 1
     assert crnt_lib.strerror(-1) == "invalid argument"

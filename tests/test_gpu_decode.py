@@ -125,7 +125,7 @@ def test_harq_combining(orc, crnt_lib, ctx):
     g2 = run_gpu(crnt_lib, ctx, [t2], l2)
     cbs2, bits2, ok2, _ = oracle_tb(orc, crnt_lib, t2, l2, soft=soft)
     assert ok2 and g2["res"][0]["tb_crc_ok"]
-    d0, d1, d2, it, hard, ext = cbs2[0]
+    d0, d1, d2, it, hard, ext, _ = cbs2[0]
     D = len(d0)
     assert np.array_equal(g2["d"][:D], d0) and np.array_equal(g2["d"][2 * D:3 * D], d2)
     assert g2["res"][0]["cb_iters"][0] == it
