@@ -236,7 +236,8 @@ int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, const int8_t
  * (2 RSC + QPP, trellis termination), sub-block interleave and bit
  * selection from k0(rv).  bits: concatenated A/8 bytes per TB (host or
  * device); e_out: concatenated G bytes (one coded bit per byte, host or
- * device). */
+ * device).  Device and page-locked host buffers are used in place by the
+ * kernel; pageable host buffers are staged.  Blocking. */
 int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, const uint8_t* bits,
                       uint8_t* e_out);
 int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb, uint8_t* e_out);

@@ -877,19 +877,42 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
                       uint8_t* e_out) {
   if (!ctx || !tbs || !bits || !e_out || n == 0) return CRNT_EINVAL;
   cudaSetDevice(ctx->device);
-  std::vector<EncCb> cbs;
-  std::vector<int64_t> in_off(n);
-  std::vector<int32_t> As(n);
+  std::lock_guard<std::mutex> lk(ctx->stage_mu);
+  // pass 1: validate, count CBs and bytes
+  std::vector<lte::Seg>& segs = ctx->enc_segs;
+  segs.resize(n);
+  size_t ncb = 0;
   int64_t ioff = 0, eoff = 0;
   for (uint32_t t = 0; t < n; t++) {
-    lte::Seg s;
-    int rc = validate(tbs[t], &s);
+    int rc = validate(tbs[t], &segs[t]);
     if (rc) return rc;
-    in_off[t] = ioff;
-    As[t] = (int32_t)tbs[t].A;
+    ncb += (size_t)segs[t].C;
+    ioff += tbs[t].A / 8;
+    eoff += tbs[t].G;
+  }
+  // device or page-locked buffers are used in place; pageable ones staged
+  const uint8_t* bits_view = (const uint8_t*)device_view(bits);
+  uint8_t* out_view = (uint8_t*)device_view(e_out);
+  const size_t b_cbs = sizeof(EncCb) * ncb, b_off = 8 * (size_t)n, b_A = 4 * (size_t)n;
+  const size_t o_off = al256(b_cbs), o_A = o_off + al256(b_off), o_bits = o_A + al256(b_A);
+  const size_t total = o_bits + (bits_view ? 0 : (size_t)ioff);
+  if (!ctx->stage_in.ensure(total) || !ctx->enc_host.ensure(o_bits)) return CRNT_ENOMEM;
+  if (!out_view && !ctx->stage_out.ensure((size_t)eoff)) return CRNT_ENOMEM;
+  // pass 2: descriptors straight into page-locked staging
+  uint8_t* h = (uint8_t*)ctx->enc_host.p;
+  EncCb* hc = (EncCb*)h;
+  int64_t* h_off = (int64_t*)(h + o_off);
+  int32_t* h_A = (int32_t*)(h + o_A);
+  size_t k = 0;
+  ioff = 0;
+  eoff = 0;
+  for (uint32_t t = 0; t < n; t++) {
+    const lte::Seg& s = segs[t];
+    h_off[t] = ioff;
+    h_A[t] = (int32_t)tbs[t].A;
     int pay_off = 0;
     for (int r = 0; r < s.C; r++) {
-      EncCb c;
+      EncCb& c = hc[k++];
       memset(&c, 0, sizeof c);
       const int K = lte::cb_k(s, r);
       c.K = K;
@@ -910,38 +933,26 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
       c.e_off = eoff;
       pay_off += c.pay_bits;
       eoff += c.E;
-      cbs.push_back(c);
     }
     ioff += tbs[t].A / 8;
   }
-  std::lock_guard<std::mutex> lk(ctx->stage_mu);
   cudaStream_t st = ctx->stream;
-  const size_t b_cbs = sizeof(EncCb) * cbs.size(), b_off = 8 * n, b_A = 4 * n;
-  const size_t o_off = al256(b_cbs), o_A = o_off + al256(b_off), o_bits = o_A + al256(b_A);
-  const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(e_out);
-  const size_t total = o_bits + (bits_dev ? 0 : (size_t)ioff);
-  if (!ctx->stage_in.ensure(total)) return CRNT_ENOMEM;
-  if (!out_dev && !ctx->stage_out.ensure((size_t)eoff)) return CRNT_ENOMEM;
-  std::vector<uint8_t> host(o_bits, 0);
-  memcpy(host.data(), cbs.data(), b_cbs);
-  memcpy(host.data() + o_off, in_off.data(), b_off);
-  memcpy(host.data() + o_A, As.data(), b_A);
   uint8_t* base = (uint8_t*)ctx->stage_in.p;
-  if (cudaMemcpyAsync(base, host.data(), o_bits, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(base, h, o_bits, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return CRNT_EDEVICE;
-  if (!bits_dev &&
+  if (!bits_view &&
       cudaMemcpyAsync(base + o_bits, bits, (size_t)ioff, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return CRNT_EDEVICE;
   EncParams p;
   p.cbs = (const EncCb*)base;
   p.tb_in_off = (const int64_t*)(base + o_off);
   p.tb_A = (const int32_t*)(base + o_A);
-  p.tb_bits = bits_dev ? bits : base + o_bits;
-  p.e_out = out_dev ? e_out : (uint8_t*)ctx->stage_out.p;
+  p.tb_bits = bits_view ? bits_view : base + o_bits;
+  p.e_out = out_view ? out_view : (uint8_t*)ctx->stage_out.p;
   p.xpowA = ctx->xpowA;
   p.xpowB = ctx->xpowB;
-  if (launch_encode(p, (int)cbs.size(), st) != cudaSuccess) return CRNT_EDEVICE;
-  if (!out_dev &&
+  if (launch_encode(p, (int)ncb, st) != cudaSuccess) return CRNT_EDEVICE;
+  if (!out_view &&
       cudaMemcpyAsync(e_out, p.e_out, (size_t)eoff, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return CRNT_EDEVICE;
   if (cudaStreamSynchronize(st) != cudaSuccess) return CRNT_EDEVICE;

@@ -75,6 +75,8 @@ struct crnt_ctx {
   std::mutex harq_mu;     // guards harq
   std::mutex stage_mu;    // guards the staging buffers and the cached plan
   crnt::Buf stage_in, stage_out;
+  crnt::Buf enc_host{true};             // page-locked encoder descriptor staging
+  std::vector<crnt::lte::Seg> enc_segs;  // encoder planning scratch
   // crnt_decode_batch splits a batch into up to kBatchChunks chunks, each
   // with a reused plan and its own stream, so that planning and copying a
   // chunk overlap the decoding of the chunks before it
