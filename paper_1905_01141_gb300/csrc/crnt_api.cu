@@ -86,15 +86,6 @@ bool find_divider(int W, int qmax, int* M, int* s) {
 }
 
 
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // Address under which kernels can use p: device and managed memory as is,
 // page-locked host memory (cudaHostAlloc / cudaHostRegister) through its
 // mapped device address -- kernels then read and write it in place over the
