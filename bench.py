@@ -367,6 +367,9 @@ def run_ours(args):
         line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
         line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 44, 48, 52),
                                             tune_table=tt, purge=True)
+        line["serving_poisson"] = serving_leg(crnt, dev, args.seed,
+                                              cells_list=(24, 32, 36, 40, 44, 48),
+                                              tune_table=tt, poisson=True)
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
         line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
         if not args.no_cpu_baseline and ws == 1:
@@ -439,7 +442,7 @@ def subframe_latency(crnt, ctx, dev):
 
 
 def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 48, 56, 64),
-                seconds=1.5, tune_table=None, purge=False):
+                seconds=1.5, tune_table=None, purge=False, poisson=False):
     """Serving loop under cell load, driven by the native open-loop load
     generator (crnt_loadgen, a client of crnt_submit / crnt_poll): every cell
     submits one subframe (8 UEs, TB mix of the TTI workload) per 1 ms period
@@ -478,6 +481,8 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 4
             cmd += ["--tune", tpath]
         if purge:
             cmd += ["--purge"]
+        if poisson:
+            cmd += ["--poisson"]
         cmd += [path, str(ues), str(seconds), "0.1", str(seed)] + [str(c) for c in cells_list]
         out = sp.run(cmd, capture_output=True, text=True, timeout=600)
     rows = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
@@ -486,6 +491,8 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 4
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
             "driver": "crnt_loadgen (native, open loop)", "rc": out.returncode,
             "purge_on_failure": purge,
+            "arrivals": "exponential, mean 1 ms per cell" if poisson
+                        else "1 ms period, random phase, +-200 us jitter",
             "what": "continuous batching via crnt_submit/crnt_poll; 8 UEs per cell, "
                     "1 subframe per cell per ms, +-200 us jitter, 10% HARQ retransmissions, "
                     "latency from scheduled arrival to completion"}

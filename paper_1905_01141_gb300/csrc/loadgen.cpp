@@ -12,9 +12,12 @@
 // n int64 LLR offsets, then the LLR bytes.  TB u of cell c is entry
 // (c * ues + u) mod n.  Output: one JSON object per cell count on stdout.
 //
-// usage: crnt_loadgen [--tune TABLE] [--purge] FILE UES SECONDS RETX_FRACTION SEED CELLS...
+// usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] FILE UES SECONDS RETX_FRACTION SEED
+//                     CELLS...
 // TABLE: a window-count table (188 numbers) installed with crnt_tune_set;
-// --purge: every TB asks for purge on failure (CRNT_F_PURGE).
+// --purge: every TB asks for purge on failure (CRNT_F_PURGE);
+// --poisson: exponential inter-arrival times of mean 1 ms per cell instead of
+// the 1 ms period with jitter.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -56,7 +59,7 @@ struct Point {
 
 Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
                 const std::vector<const int8_t*>& ptr, int ues, int cells, double seconds,
-                double retx, uint64_t seed, uint32_t extra_flags) {
+                double retx, uint64_t seed, uint32_t extra_flags, bool poisson) {
   const int n = (int)par.size();
   uint64_t rs = seed * 1000003ull + (uint64_t)cells;
   std::vector<double> phase(cells);
@@ -130,8 +133,13 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
     }
     subframes++;
     sf[c]++;
-    const double jit = (unit(rs) - 0.5) * 400000.0;
-    q.push(Ev{t0 + (int64_t)sf[c] * 1000000 + (int64_t)(phase[c] + jit), c});
+    if (poisson) {
+      const double gap = -std::log(1.0 - unit(rs)) * 1e6;  // exponential, mean 1 ms
+      q.push(Ev{ev.first + (int64_t)gap, c});
+    } else {
+      const double jit = (unit(rs) - 0.5) * 400000.0;
+      q.push(Ev{t0 + (int64_t)sf[c] * 1000000 + (int64_t)(phase[c] + jit), c});
+    }
   }
   done_submitting.store(true);
   poller.join();
@@ -171,14 +179,22 @@ int main(int argc, char** argv) {
     argc -= 2;
   }
   uint32_t extra_flags = 0;
-  if (argc > 1 && strcmp(argv[1], "--purge") == 0) {
-    extra_flags = CRNT_F_PURGE;
+  bool poisson = false;
+  for (;;) {
+    if (argc > 1 && strcmp(argv[1], "--purge") == 0) {
+      extra_flags = CRNT_F_PURGE;
+    } else if (argc > 1 && strcmp(argv[1], "--poisson") == 0) {
+      poisson = true;
+    } else {
+      break;
+    }
     argv += 1;
     argc -= 1;
   }
   if (argc < 7) {
     fprintf(stderr,
-            "usage: crnt_loadgen [--tune TABLE] [--purge] FILE UES SECONDS RETX SEED CELLS...\n");
+            "usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] FILE UES SECONDS RETX SEED "
+            "CELLS...\n");
     return 2;
   }
   FILE* f = fopen(argv[1], "rb");
@@ -208,10 +224,12 @@ int main(int argc, char** argv) {
   crnt_ctx* ctx = nullptr;
   if (crnt_create(&ctx, &cfg) != CRNT_OK) return 3;
   // warm-up pass (not reported): the serving loop's buffers come up here
-  run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1, extra_flags);
+  run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1, extra_flags,
+            poisson);
   for (int a = 6; a < argc; a++) {
     const int cells = atoi(argv[a]);
-    const Point p = run_point(ctx, par, ptr, ues, cells, seconds, retx, seed, extra_flags);
+    const Point p =
+        run_point(ctx, par, ptr, ues, cells, seconds, retx, seed, extra_flags, poisson);
     printf("{\"cells\": %d, \"tbs\": %ld, \"subframes\": %ld, \"refused_subframes\": %ld, "
            "\"errors\": %ld, \"p50_us\": %.1f, \"p99_us\": %.1f, \"deadline_miss\": %.6f, "
            "\"gbit_s\": %.4f}\n",
