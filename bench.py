@@ -56,7 +56,7 @@ def parse():
                     help="load the window table from this file instead of measuring it")
     ap.add_argument("--save-tune", default=None, help="write the window table to this file")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
-    ap.add_argument("--sweep", choices=["bler", "stop"],
+    ap.add_argument("--sweep", choices=["bler", "stop", "peak"],
                     help="quality sweep instead of the bench line (stop: CRC vs mutual "
                          "information stop rule)")
     ap.add_argument("--bler-cbs", type=int, default=0,
@@ -674,10 +674,34 @@ def bler_sweep(args, ks=(6144, 40), ps=(1, 4, 16, 64), stops=(1,)):
     print(json.dumps({"sweep": "bler", "points": pts}), flush=True)
 
 
+def int_issue_peaks():
+    """Issue rates (warp-instructions per SM clock) of the decoder's integer
+    instruction kinds, measured by crnt_int_issue_probe; with 32 lanes per
+    warp-instruction they give the lanes per SM clock of the ALU-issue
+    roofline."""
+    import ctypes
+
+    import paper_1905_01141_gb300 as crnt
+    from paper_1905_01141_gb300 import build as crnt_build
+    crnt_build.build()
+    L = crnt.load()
+    names = ["dpx_addmax_s32", "dpx_addmax_s16x2", "imad_s32", "dpx_s32_and_imad_1to1"]
+    out = {}
+    for k, name in enumerate(names):
+        v = ctypes.c_double()
+        rc = L.crnt_int_issue_probe(0, k, ctypes.byref(v))
+        out[name] = {"warp_instr_per_clk_per_sm": round(v.value, 3) if rc == 0 else None,
+                     "int_lanes_per_clk_per_sm": round(32 * v.value, 1) if rc == 0 else None}
+    print(json.dumps({"sweep": "int_issue_peak", "probe": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.sweep == "bler":
         bler_sweep(args)
+        return
+    if args.sweep == "peak":
+        int_issue_peaks()
         return
     if args.sweep == "stop":
         # the two stop rules side by side: BLER and mean iterations

@@ -169,6 +169,15 @@ int crnt_tune_set(const uint8_t* P_by_k, uint32_t n); /* n must be 188 */
  * seconds; allocates device memory for its inputs and frees it. */
 int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k);
 
+/* ---- measurement ------------------------------------------------------ */
+/* Issue rate of one integer instruction kind on `device`, in warp-
+ * instructions per SM clock, from a fully resident probe kernel with 8
+ * independent chains per thread (clock64 timing): kind 0 = DPX add-max
+ * s32 (the trellis ACS instruction), 1 = DPX add-max s16x2, 2 = 32-bit
+ * multiply-add, 3 = kinds 0 and 2 interleaved 1:1.  Grounds the decode
+ * kernel's ALU-issue roofline; the paper has no counterpart. */
+int crnt_int_issue_probe(int device, int kind, double* warp_instr_per_clk_per_sm);
+
 /* ---- context ---------------------------------------------------------- */
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates the
  * HARQ soft-buffer arena lazily.  CRNT_EDEVICE if CUDA is unusable. */

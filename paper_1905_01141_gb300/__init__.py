@@ -105,6 +105,7 @@ SIGNATURES = {
     "crnt_tune_get": (ctypes.c_int, [_P, _U32]),
     "crnt_tune_set": (ctypes.c_int, [_P, _U32]),
     "crnt_autotune": (ctypes.c_int, [_P, _U32, _P]),
+    "crnt_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P]),
 }
 
 

@@ -12,7 +12,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcrnt.so")
 LOADGEN = os.path.join(OUT, "crnt_loadgen")
-UNITS = ["decode.cu", "encode.cu", "crnt_api.cu", "serve.cu", "noalloc.cu", "tune.cu"]
+UNITS = ["decode.cu", "encode.cu", "crnt_api.cu", "serve.cu", "noalloc.cu", "tune.cu",
+         "peak.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v"]
