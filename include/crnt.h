@@ -255,7 +255,10 @@ int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb,
 /* Submit n TBs whose LLRs are host buffers llrs[i] (G_i bytes each).  The
  * LLRs are copied before return.  Work starts on the device as soon as
  * in-flight capacity and memory allow; tickets_out[i] receives a ticket.
- * CRNT_EAGAIN when admission is refused (nothing of the call is queued). */
+ * CRNT_EAGAIN when admission is refused (nothing of the call is queued).
+ * TBs that share a HARQ key (cell, ue, harq_pid) must not be in flight at
+ * the same time (a retransmission is submitted after the previous
+ * transmission's result was polled, as the HARQ round trip implies). */
 int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* llrs, uint32_t n,
                 uint64_t* tickets_out);
 /* Collect up to max finished TBs, waiting at most timeout_us for the first.
