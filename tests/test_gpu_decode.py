@@ -283,3 +283,22 @@ def test_mi_stop_rule_matches_oracle(orc, crnt_lib, ctx):
     check_batch(orc, crnt_lib, tbs, llrs, g)
     iters = [it for r in g["res"] for it in r["cb_iters"]]
     assert min(iters) >= 2 and len(set(iters)) > 2
+
+
+def test_int_issue_probe(crnt_lib):
+    # the issue-rate probe behind the roofline: every kind reports a rate
+    # between 1 and 4 warp-instructions per SM clock (4 schedulers); DPX
+    # add-max reaches at least 1.5 (two per clock on this GPU)
+    import ctypes
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L = crnt_lib.load()
+    rates = []
+    for kind in range(4):
+        v = ctypes.c_double()
+        assert L.crnt_int_issue_probe(0, kind, ctypes.byref(v)) == 0
+        rates.append(v.value)
+    assert all(1.0 <= r <= 4.0 for r in rates), rates
+    assert rates[0] >= 1.5
+    v = ctypes.c_double()
+    assert L.crnt_int_issue_probe(0, 4, ctypes.byref(v)) == crnt_lib.EINVAL
