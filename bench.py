@@ -506,11 +506,19 @@ def cpu_baseline(shapes, seed):
         bits, secs, n, _ = oracle_run(oracle, items, 15.0, pool)
     with cf.ThreadPoolExecutor(max_workers=1) as pool:
         bits1, secs1, n1, _ = oracle_run(oracle, items, 5.0, pool)
+    # one 20 MHz subframe (TBS 75376, 13 CBs, 64QAM, early stop) on one thread
+    A, G = 75376, 86400
+    e = oracle.encode_tb(synth.bits(77, 0, A), G, Qm=6)
+    llr = synth.channel_llrs(e, 6, synth.sigma2_snr(20.0), 77, 0)
+    t0 = time.perf_counter()
+    oracle.decode_tb(llr, A, G, Qm=6, P=122, max_iter=6, early_stop=True)
+    sub_ms = (time.perf_counter() - t0) * 1e3
     return {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
             "sample": "%d TBs of the TTI workload (first 96 shapes, cycled), 6 iterations, "
                       "thread pool of %d, %.1f s" % (n, cores, secs),
             "single_core": {"value": bits1 / secs1 / 1e9, "unit": "Gbit/s",
-                            "sample": "%d TBs on one thread, %.1f s" % (n1, secs1)}}
+                            "sample": "%d TBs on one thread, %.1f s" % (n1, secs1)},
+            "subframe_ms_one_thread": sub_ms}
 
 
 def single_cb_config(crnt, ctx, dev, n_batch=1024):
