@@ -489,7 +489,7 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 4
     ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["refused_subframes"] == 0
           and r["errors"] == 0]
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
-            "driver": "crnt_loadgen (native, open loop)", "rc": out.returncode,
+            "load_generator": "crnt_loadgen (native, open loop)", "rc": out.returncode,
             "purge_on_failure": purge,
             "arrivals": "exponential, mean 1 ms per cell" if poisson
                         else "1 ms period, random phase, +-200 us jitter",

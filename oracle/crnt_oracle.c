@@ -22,7 +22,7 @@
  *   LLRs        : L = log P(b=0)/P(b=1); BPSK 0 -> +1; hard bit = (L < 0).
  *
  * Parity status: the QPP (f1,f2) values below are restated from TS 36.212
- * Table 5.1.3-3, which is not available to this build.  Each row is checked
+ * Table 5.1.3-3, which this repository does not contain.  Each row is checked
  * to be a permutation, but conformance of the values to 3GPP is
  * "parity unpinned".  The tail-bit multiplexing order (TS 36.212 Sec.
  * 5.1.3.2.2) is likewise restated, checked only for self-consistency

@@ -115,7 +115,7 @@ def test_harq_through_serving(orc, crnt_lib, ctx):
 
 
 def test_native_load_generator_runs(crnt_lib):
-    # crnt_loadgen (the bench's serving driver, a client of the C ABI) serves
+    # crnt_loadgen (the bench's serving load generator, a C-ABI client) serves
     # a light load: every submitted TB comes back without error or refusal
     # (the latency figures are the bench's; here only a loose bound)
     import os
