@@ -48,6 +48,11 @@ def test_encode_matches_oracle(orc, crnt_lib, ctx):
     ctx.encode_batch(tbs, bd, ed)
     torch.cuda.synchronize()
     assert np.array_equal(ed.cpu().numpy(), want)
+    # page-locked host buffers, read and written in place by the kernel
+    bp = torch.from_numpy(bits).pin_memory()
+    ep = torch.zeros(len(want), dtype=torch.uint8).pin_memory()
+    ctx.encode_batch(tbs, bp, ep)
+    assert np.array_equal(ep.numpy(), want)
 
 
 def test_encode_decode_round_trip(crnt_lib, ctx):
