@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncParams prm) {
   __shared__ uint32_t tabA[256], tabB[256];
   __shared__ uint16_t rtab[8][256];  // (end state << 8) | parity byte
   __shared__ uint8_t cbits[kMaxK];   // CB bits (0/1)
+  __shared__ uint8_t cbits2[kMaxK];  // the same bits in QPP order (input of encoder 2)
   __shared__ uint8_t zpar[2][kMaxK]; // parity of encoder 1 / 2
   __shared__ uint8_t tail[12];
   __shared__ uint8_t zs[2][kEncThreads], st0[2][kEncThreads + 1];
@@ -139,18 +140,29 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncParams prm) {
   const int cpb = (nbytes + kEncThreads - 1) / kEncThreads;  // bytes per chunk
   const int j0 = tid * cpb, j1 = min(nbytes, j0 + cpb);
   const int f1 = d.f1, f2 = d.f2;
-  // interleaved input byte j of encoder 2: bits c[PI(8j + q)]
-  auto in_byte = [&](int enc, int j) -> int {
-    int v = 0;
-    if (enc == 0) {
-      for (int q = 0; q < 8; q++) v = (v << 1) | cbits[8 * j + q];
-    } else {
-      for (int q = 0; q < 8; q++) {
-        const int i = 8 * j + q;
-        const int pi = (int)(((long long)f1 * i + (long long)f2 * i % K * i) % K);
-        v = (v << 1) | cbits[pi];
+  // encoder 2 input c'[i] = c[PI(i)], PI(i) = (f1 i + f2 i^2) mod K: each
+  // thread walks its own bit range with the first differences
+  // PI(i+1) = PI(i) + D(i), D(i+1) = D(i) + 2 f2 (mod K)
+  {
+    const int i0 = 8 * j0, i1 = 8 * j1;
+    if (i0 < i1) {
+      int pi = (int)(((long long)f1 * i0 + (long long)f2 * i0 % K * i0) % K);
+      int dl = (int)(((long long)f1 + (long long)f2 * (2 * i0 + 1)) % K);
+      const int f2x2 = (int)((2ll * f2) % K);
+      for (int i = i0; i < i1; i++) {
+        cbits2[i] = cbits[pi];
+        pi += dl;
+        if (pi >= K) pi -= K;
+        dl += f2x2;
+        if (dl >= K) dl -= K;
       }
     }
+  }
+  __syncthreads();
+  auto in_byte = [&](int enc, int j) -> int {
+    const uint8_t* c = enc == 0 ? cbits : cbits2;
+    int v = 0;
+    for (int q = 0; q < 8; q++) v = (v << 1) | c[8 * j + q];
     return v;
   };
   for (int enc = 0; enc < 2; enc++) {
@@ -209,9 +221,10 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncParams prm) {
   const int R = d.R, E = d.E;
   const int Nv = 3 * (K + 4) - 2 * F;
   uint8_t* out = prm.e_out + d.e_off;
+  // rows x = unit * R + i, walked with (unit, i) updated incrementally
+  int unit = tid / R, i = tid - (tid / R) * R;
+  const int du = kEncThreads / R, di_ = kEncThreads - du * R;
   for (int x = tid; x < 64 * R; x += kEncThreads) {
-    const int unit = x / R;
-    const int i = x - unit * R;
     rm_visit(
         gg, unit, i,
         [&](int p, int st, int di, int rank) {
@@ -224,6 +237,12 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncParams prm) {
           for (; k < E; k += Nv) out[k] = v;
         },
         [&](int) {});
+    unit += du;
+    i += di_;
+    if (i >= R) {
+      i -= R;
+      unit++;
+    }
   }
 }
 
