@@ -412,33 +412,41 @@ def e2e_leg(ctx, tbs, llr_h, info, args):
 
 def subframe_latency(crnt, ctx, dev):
     """Device latency of one 20 MHz uplink subframe (TBS 75376 -> 13 CBs of
-    K = 5824, G = 86400, 64QAM at 18..22 dB, early stop on, P autotuned)."""
+    K = 5824, G = 86400, 64QAM at 18..22 dB, early stop on): 30 subframes with
+    the autotuned window count, and 10 each at P = 1, 8 and 32."""
     import torch
-    lat = []
     stream = torch.cuda.Stream(device=dev)
-    for i in range(30):
-        A, G = 75376, 86400
-        tb = [dict(A=A, G=G, Qm=6, P=0, max_iter=6, early_stop=1)]
-        pay = np.packbits(synth.bits(77, i, A))
-        coded = np.zeros(G, dtype=np.uint8)
-        ctx.encode_batch(tb, pay, coded)
-        llr = synth.channel_llrs(coded, 6, synth.sigma2_snr(18.0 + 4.0 * (i % 5) / 4), 77, i)
-        plan = ctx.plan(tb)
-        ld = torch.from_numpy(llr).to(dev)
-        od = torch.zeros(A // 8, dtype=torch.uint8, device=dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            plan.launch(ld, od, stream.cuda_stream)
-            e0.record(stream)
-            plan.launch(ld, od, stream.cuda_stream)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        lat.append(e0.elapsed_time(e1) * 1e3)
-        plan.close()
-    lat.sort()
-    return {"p50_us": lat[len(lat) // 2], "p99_us": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "max_us": lat[-1], "n": len(lat),
-            "what": "device time of one 20 MHz subframe decode (13 CBs, early stop)"}
+    A, G = 75376, 86400
+
+    def run(P, n):
+        lat = []
+        for i in range(n):
+            tb = [dict(A=A, G=G, Qm=6, P=P, max_iter=6, early_stop=1)]
+            pay = np.packbits(synth.bits(77, i, A))
+            coded = np.zeros(G, dtype=np.uint8)
+            ctx.encode_batch(tb, pay, coded)
+            llr = synth.channel_llrs(coded, 6, synth.sigma2_snr(18.0 + 4.0 * (i % 5) / 4), 77, i)
+            plan = ctx.plan(tb)
+            ld = torch.from_numpy(llr).to(dev)
+            od = torch.zeros(A // 8, dtype=torch.uint8, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                plan.launch(ld, od, stream.cuda_stream)
+                e0.record(stream)
+                plan.launch(ld, od, stream.cuda_stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(e0.elapsed_time(e1) * 1e3)
+            plan.close()
+        lat.sort()
+        return {"p50_us": lat[len(lat) // 2],
+                "p99_us": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max_us": lat[-1],
+                "n": len(lat)}
+
+    out = run(0, 30)
+    out["by_P"] = {str(P): run(P, 10) for P in (1, 8, 32)}
+    out["what"] = "device time of one 20 MHz subframe decode (13 CBs, early stop)"
+    return out
 
 
 def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 48, 56, 64),
