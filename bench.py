@@ -54,7 +54,10 @@ def parse():
                     help="built-in window counts instead of the autotuned table")
     ap.add_argument("--tune-table", default=None,
                     help="load the window table from this file instead of measuring it")
-    ap.add_argument("--save-tune", default=None, help="write the window table to this file")
+    ap.add_argument("--save-tune", default=None,
+                    help="write the window table (and, on a second line, the radix table) here")
+    ap.add_argument("--radix", choices=("tuned", "2", "4"), default="tuned",
+                    help="forward-recursion radix: the autotuner's choice per K, or one for all K")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
     ap.add_argument("--sweep", choices=["bler", "stop", "peak"],
                     help="quality sweep instead of the bench line (stop: CRC vs mutual "
@@ -259,19 +262,28 @@ def run_ours(args):
         t0 = time.perf_counter()
         if args.tune_table:
             with open(args.tune_table) as f:
-                table = [int(x) for x in f.read().split()]
+                vals = [int(x) for x in f.read().split()]
+            table = vals[:crnt.NUM_K]
             crnt.tune_set(table)
+            if len(vals) >= 2 * crnt.NUM_K:
+                crnt.tune_radix_set(vals[crnt.NUM_K:2 * crnt.NUM_K])
         else:
             table = ctx.autotune(32)
+        if args.radix != "tuned":
+            crnt.tune_radix_set([int(args.radix)] * crnt.NUM_K)
+        radix = crnt.tune_radix_get()
         if args.save_tune:
             with open(args.save_tune, "w") as f:
                 f.write(" ".join(str(x) for x in table) + "\n")
+                f.write(" ".join(str(x) for x in radix) + "\n")
         ks = (list(range(40, 513, 8)) + list(range(528, 1025, 16)) + list(range(1056, 2049, 32))
               + list(range(2112, 6145, 64)))  # the 188 CB sizes, in table order
         builtin = [max(1, min(k // 8, 128, -(-k // 48))) for k in ks]
         tune = {"w_min": 32, "seconds": round(time.perf_counter() - t0, 2),
                 "source": args.tune_table or "crnt_autotune",
                 "entries_changed_from_builtin": sum(int(a != b) for a, b in zip(table, builtin)),
+                "radix": args.radix,
+                "radix4_at_K": [k for k, r in zip(ks, radix) if r == 4],
                 "P_at_K": {str(k): p for k, p in zip(ks, table)
                            if k in (40, 256, 512, 1024, 2048, 4096, 5824, 5888, 6016, 6144)}}
 
@@ -363,7 +375,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
-        tt = None if args.no_autotune else crnt.tune_get()
+        tt = None if args.no_autotune else crnt.tune_get() + crnt.tune_radix_get()
         line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
         line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 44, 48, 52),
                                             tune_table=tt, purge=True)
@@ -371,6 +383,7 @@ def run_ours(args):
                                               cells_list=(24, 32, 36, 40, 44, 48),
                                               tune_table=tt, poisson=True)
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
+        line["radix4_forward"] = radix_leg(crnt, ctx, tbs, llr_d, flush, dev)
         line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(shapes, args.seed)
@@ -380,6 +393,45 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def radix_leg(crnt, ctx, tbs, llr_d, flush, dev, steps=60):
+    """The TTI decode with the radix-4 forward recursion at every CB size,
+    next to the installed radix table (the autotuner's choice): device time
+    per launch (L2 flushed before each) and whether the decoded bytes and
+    iteration counts are identical, as they must be."""
+    import torch
+    old = crnt.tune_radix_get()
+    stream = torch.cuda.Stream(device=dev)
+    out, outs = {}, []
+    try:
+        for name, table in (("installed", old), ("radix4_all_K", [4] * crnt.NUM_K)):
+            crnt.tune_radix_set(table)
+            plan = ctx.plan(tbs)
+            od = torch.zeros(plan.info["out_bytes"], dtype=torch.uint8, device=dev)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    flush.zero_()
+                    plan.launch(llr_d, od, stream.cuda_stream)
+                for i in range(steps):
+                    flush.zero_()
+                    ev[i][0].record(stream)
+                    plan.launch(llr_d, od, stream.cuda_stream)
+                    ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            res = plan.results(stream.cuda_stream)
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            out[name] = {"ms_per_launch": ms, "gbit_s": plan.info["info_bits"] / ms / 1e6,
+                         "radix4_entries": sum(int(r == 4) for r in table)}
+            outs.append((od.cpu().numpy().tobytes(), [r["cb_iters"] for r in res]))
+            plan.close()
+    finally:
+        crnt.tune_radix_set(old)
+    out["outputs_identical"] = outs[0] == outs[1]
+    out["radix4_vs_installed"] = out["installed"]["ms_per_launch"] / out["radix4_all_K"]["ms_per_launch"]
+    return out
 
 
 def e2e_leg(ctx, tbs, llr_h, info, args):

@@ -161,11 +161,23 @@ int crnt_tb_layout(const crnt_tb_params* tb, crnt_cb_layout* cbs, uint32_t* C);
 #define CRNT_NUM_K 188
 int crnt_tune_get(uint8_t* P_by_k, uint32_t n);       /* copies min(n, 188) entries */
 int crnt_tune_set(const uint8_t* P_by_k, uint32_t n); /* n must be 188 */
+/* Forward-recursion radix per CB size, a second process-wide table: entry i
+ * is 2 (one trellis step per forward update, the default) or 4 (two steps
+ * per update: each state takes the best of its four two-step paths).  The
+ * radix-4 recursion runs only in window passes that the decoder has proved
+ * free of int16 saturation; there the maximum over two-step paths equals two
+ * radix-2 steps exactly, so the radix never changes a decoded value, only
+ * the speed.  Passes that may saturate always use radix 2.  get writes 2 or
+ * 4; set accepts 0 (= 2), 2 or 4 and needs n = 188. */
+int crnt_tune_radix_get(uint8_t* radix_by_k, uint32_t n);
+int crnt_tune_radix_set(const uint8_t* radix_by_k, uint32_t n);
 /* Measure on ctx's GPU the batched decode throughput (6 iterations, full
  * batches of single-CB TBs per K) of candidate window counts for every CB
  * size, keep for each K the fastest whose windows are at least w_min
  * trellis steps long (0 = 32; smaller windows cost BLER), install the table
- * and copy it to P_by_k (188 entries, may be NULL).  Blocking; takes a few
+ * and copy it to P_by_k (188 entries, may be NULL).  At the kept window
+ * count it also times the radix-4 forward recursion and installs the radix
+ * table (4 where it is more than 1 % faster, else 2).  Blocking; takes a few
  * seconds; allocates device memory for its inputs and frees it. */
 int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k);
 

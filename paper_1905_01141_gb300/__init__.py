@@ -104,6 +104,8 @@ SIGNATURES = {
     "crnt_decode_batch_static": (ctypes.c_int, [_P, _U32, _P, _P, _P, _P]),
     "crnt_tune_get": (ctypes.c_int, [_P, _U32]),
     "crnt_tune_set": (ctypes.c_int, [_P, _U32]),
+    "crnt_tune_radix_get": (ctypes.c_int, [_P, _U32]),
+    "crnt_tune_radix_set": (ctypes.c_int, [_P, _U32]),
     "crnt_autotune": (ctypes.c_int, [_P, _U32, _P]),
     "crnt_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P]),
 }
@@ -203,6 +205,19 @@ def tune_set(table):
     """Install a window-count table (188 entries, 0 = built-in)."""
     t = (ctypes.c_uint8 * NUM_K)(*table)
     _check(load().crnt_tune_set(t, NUM_K), "crnt_tune_set")
+
+
+def tune_radix_get():
+    """The process-wide forward-recursion radix table (188 entries, 2 or 4)."""
+    t = (ctypes.c_uint8 * NUM_K)()
+    _check(load().crnt_tune_radix_get(t, NUM_K), "crnt_tune_radix_get")
+    return list(t)
+
+
+def tune_radix_set(table):
+    """Install a forward-recursion radix table (188 entries, 0/2 = radix 2, 4)."""
+    t = (ctypes.c_uint8 * NUM_K)(*table)
+    _check(load().crnt_tune_radix_set(t, NUM_K), "crnt_tune_radix_set")
 
 
 class Context:

@@ -177,10 +177,20 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Process-wide window-count table (crnt_tune_set / crnt_autotune).
 std::atomic<uint8_t> g_tuned[lte::kNumK];
+// Process-wide forward-recursion radix per CB size (2 or 4; 0 reads as 2).
+std::atomic<uint8_t> g_radix[lte::kNumK];
 
 int tuned_p(int K) {
   const int ki = lte::index_of(K);
   return ki < 0 ? 0 : (int)g_tuned[ki].load(std::memory_order_relaxed);
+}
+
+thread_local int t_radix_override = -1;
+
+uint8_t radix4_of(int K) {
+  if (t_radix_override >= 0) return (uint8_t)t_radix_override;
+  const int ki = lte::index_of(K);
+  return ki >= 0 && g_radix[ki].load(std::memory_order_relaxed) == 4 ? 1 : 0;
 }
 
 // Window count for a CB of size K: the caller's P clamped to [1, K/8] and
@@ -375,6 +385,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   int max_slot_bytes = 0;
   WorkItem wi{0, 0, 0, 0};
   int gmax = 0, iK = -1, iP = -1;
+  bool radix4_any = false;
   for (uint32_t i = 0; i < ncb; i++) {
     const uint32_t g = (uint32_t)(pl->keyed[i] & 0x1FFFFFF);
     const uint32_t t = pl->owner[g];
@@ -427,6 +438,8 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     d.early_stop = tp.early_stop;  // 0 none, 1 CRC, 2 mutual information
     d.new_data = tp.new_data ? 1 : 0;
     d.purge = (tp.flags & CRNT_F_PURGE) && s.C > 1 ? 1 : 0;
+    d.radix4 = radix4_of(tm.K);
+    radix4_any |= d.radix4 != 0;
     memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;
     pl->cb_r[i] = r;
@@ -506,6 +519,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   p.xpowA = ctx->xpowA;
   p.xpowB = ctx->xpowB;
   p.mi_tab = ctx->mi_tab;
+  p.radix4_any = radix4_any ? 1 : 0;
   return CRNT_OK;
 }
 

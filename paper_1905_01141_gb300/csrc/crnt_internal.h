@@ -44,7 +44,8 @@ struct CbDesc {
   uint8_t crc_b;           // 1: CRC24B per CB (C > 1); 0: CRC24A (C == 1)
   uint8_t max_iter, early_stop, new_data;
   uint8_t purge;           // 1: stop when another CB of the TB has failed
-  uint8_t pad0[3];
+  uint8_t radix4;          // 1: radix-4 forward recursion where the pass is clamp-free
+  uint8_t pad0[2];
 };
 
 struct TbDesc {
@@ -89,6 +90,7 @@ struct DecParams {
   int8_t* dbg_d;          // optional: [sum (K+4)] x 3 d-streams per CB
   int16_t* dbg_ext;       // optional: [sum K] final extrinsic, natural order
   uint8_t* dbg_hard;      // optional: [sum K] hard decisions
+  int32_t radix4_any;     // some CB selects the radix-4 forward recursion
 };
 
 // Encoder launch description: one CB per CTA.

@@ -120,6 +120,53 @@ __device__ __forceinline__ void alpha_step(const int a[8], int o[8], int S, int 
   normalise<CHK>(m, o);
 }
 
+// Two trellis steps at once (radix-4 forward recursion): every state n at
+// step k + 2 takes the best of its four two-step paths n0 -> n1 -> n, each
+// weighing gamma_k(n0 -> n1) + gamma_{k+1}(n1 -> n).  Clamp-free path only:
+// there the radix-2 recursion is the exact max-plus product and, since a
+// maximum distributes over an added constant, max over n1 of (max over n0 of
+// (a[n0] + g0) + g1) equals this maximum over the four paths as integers, so
+// both radices give the same metrics (and the same checkpoints after
+// pack_norm).  The sixteen two-step branch sums are the pairs of the two
+// steps' four branch values {0, Lp, S, S + Lp}; the unrolled loops use them
+// with compile-time indices, so only the nonzero pairs cost an add.
+__device__ __forceinline__ void alpha_step_r4(const int a[8], int o[8], int S0, int L0, int S1,
+                                              int L1) {
+  const int g0[4] = {0, L0, S0, S0 + L0};
+  const int g1[4] = {0, L1, S1, S1 + L1};
+#pragma unroll
+  for (int n = 0; n < 8; n++) {
+    int src[4], code0[4], code1[4];
+#pragma unroll
+    for (int k1 = 0; k1 < 2; k1++)
+#pragma unroll
+      for (int k0 = 0; k0 < 2; k0++) {
+        const int n1 = pred(n, k1);
+        src[2 * k1 + k0] = pred(n1, k0);
+        code0[2 * k1 + k0] = pcode(n1, k0);
+        code1[2 * k1 + k0] = pcode(n, k1);
+      }
+    // start the chain from a path with a zero branch sum when there is one
+    int z = -1;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      if (z < 0 && code0[i] == 0 && code1[i] == 0) z = i;
+    const int first = z < 0 ? 0 : z;
+    int acc = a[src[first]];
+    if (z < 0) acc += g0[code0[first]] + g1[code1[first]];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      if (i == first) continue;
+      const int c0 = code0[i], c1 = code1[i];
+      if (c0 == 0 && c1 == 0) acc = max(acc, a[src[i]]);
+      else if (c0 == 0) acc = __viaddmax_s32(a[src[i]], g1[c1], acc);
+      else if (c1 == 0) acc = __viaddmax_s32(a[src[i]], g0[c0], acc);
+      else acc = __viaddmax_s32(a[src[i]], g0[c0] + g1[c1], acc);
+    }
+    o[n] = acc;
+  }
+}
+
 template <bool CHK>
 __device__ __forceinline__ void beta_step(int b[8], int S, int T, int Lp) {
   int m[8];
@@ -434,6 +481,7 @@ struct Win {
   int f2x2;                 // QPP first-difference step
   int p, lo, len, pad;
   bool hard_on;             // DEC 1: form the hard decisions
+  bool r4;                  // radix-4 forward recursion on the clamp-free path
 };
 
 __device__ __forceinline__ int tr_w(const Win& w, int q) {
@@ -508,7 +556,9 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
 }
 
 // Forward and backward recursions of one window (after the seeds are read).
-template <int DEC, bool CHK>
+// R4: the kernel instantiation that carries the radix-4 forward recursion
+// (used by CBs with radix4 set, on clamp-free passes).
+template <int DEC, bool CHK, bool R4>
 __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restrict__ dp,
                                             uint4* ck, uint4* seedA, uint4* seedB, int a[8],
                                             int b[8], int& mx, int& mn) {
@@ -523,15 +573,31 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     dq = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
   }
   int j0 = 0;
-  for (; j0 + kSub <= len; j0 += kSub) {
-    ck[j0 / kSub] = pack_norm<CHK>(a);
+  if (R4 && !CHK && w.r4) {  // radix-4 forward recursion (same metrics, see alpha_step_r4)
+    for (; j0 + kSub <= len; j0 += kSub) {
+      ck[j0 / kSub] = pack_norm<CHK>(a);
 #pragma unroll
-    for (int jj = 0; jj < kSub; jj += 2) {
-      int S, Lp, t, o[8];
-      load_step<DEC>(w, j0 + jj, q, dq, S, Lp, t);
-      alpha_step<CHK>(a, o, S, S + Lp, Lp);
-      load_step<DEC>(w, j0 + jj + 1, q, dq, S, Lp, t);
-      alpha_step<CHK>(o, a, S, S + Lp, Lp);
+      for (int jj = 0; jj < kSub; jj += 4) {
+        int S0, L0, S1, L1, t, o[8];
+        load_step<DEC>(w, j0 + jj, q, dq, S0, L0, t);
+        load_step<DEC>(w, j0 + jj + 1, q, dq, S1, L1, t);
+        alpha_step_r4(a, o, S0, L0, S1, L1);
+        load_step<DEC>(w, j0 + jj + 2, q, dq, S0, L0, t);
+        load_step<DEC>(w, j0 + jj + 3, q, dq, S1, L1, t);
+        alpha_step_r4(o, a, S0, L0, S1, L1);
+      }
+    }
+  } else {
+    for (; j0 + kSub <= len; j0 += kSub) {
+      ck[j0 / kSub] = pack_norm<CHK>(a);
+#pragma unroll
+      for (int jj = 0; jj < kSub; jj += 2) {
+        int S, Lp, t, o[8];
+        load_step<DEC>(w, j0 + jj, q, dq, S, Lp, t);
+        alpha_step<CHK>(a, o, S, S + Lp, Lp);
+        load_step<DEC>(w, j0 + jj + 1, q, dq, S, Lp, t);
+        alpha_step<CHK>(o, a, S, S + Lp, Lp);
+      }
     }
   }
   if (j0 < len) {
@@ -590,7 +656,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
 // bounds |La| for the pass that reads it.  hard (DEC 1): the hard decisions
 // of this iteration are used (a CRC check follows); otherwise they are not
 // formed, since the next iteration overwrites them unread.
-template <int DEC>
+template <int DEC, bool R4>
 __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t* base, int p,
                                           bool run, bool first, bool hard) {
   const int K = dp->K, P = dp->P, W = dp->W;
@@ -637,6 +703,7 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     w.ext = sl.ext;
     w.hard = sl.hard;
     w.hard_on = hard;
+    w.r4 = R4 && dp->radix4 != 0;
     w.K = K;
     w.P = P;
     w.W = W;
@@ -654,9 +721,9 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     }
     int mx = 0, mn = 0;
     if (window_fast(a, b, 254 + m_in))
-      window_pass<DEC, false>(w, dp, ck, seedA, seedB, a, b, mx, mn);
+      window_pass<DEC, false, R4>(w, dp, ck, seedA, seedB, a, b, mx, mn);
     else
-      window_pass<DEC, true>(w, dp, ck, seedA, seedB, a, b, mx, mn);
+      window_pass<DEC, true, R4>(w, dp, ck, seedA, seedB, a, b, mx, mn);
     atomicMax(&sl.flags[4 + DEC], max(mx, -mn));
   }
   __syncthreads();
@@ -687,6 +754,10 @@ __device__ uint32_t crc_share(const CbDesc& d, const CbSlot& sl, int p, const ui
   return after ? gf_mulmod(r, __ldg(&xpow[after]), g) : r;
 }
 
+// R4 = false: the radix-2 kernel; R4 = true adds the radix-4 forward
+// recursion for CBs that select it (a separate instantiation, so the radix-2
+// kernel's code is not affected by the option).
+template <bool R4>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams prm) {
   __shared__ int s_item;
   __shared__ int s_remaining;
@@ -771,9 +842,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
       const int my_max = mine ? (int)dp->max_iter : 0;
       const bool run = mine && fl[0] == 0 && it <= my_max;
       const bool first = (it == 1);
-      siso_pass<0>(dp, mybase, p, run, first, false);
+      siso_pass<0, R4>(dp, mybase, p, run, first, false);
       const bool check = run && (dp->early_stop || it == my_max);
-      siso_pass<1>(dp, mybase, p, run, first, check);
+      siso_pass<1, R4>(dp, mybase, p, run, first, check);
       if (check) {
         const CbDesc& d = *dp;
         const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
@@ -889,21 +960,34 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
 int decode_max_smem() { return kSmemBudget + kSmemFixed; }
 
 static cudaError_t set_attr() {
-  return cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              decode_max_smem());
+  cudaError_t e = cudaFuncSetAttribute(decode_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       decode_max_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             decode_max_smem());
+  return e;
 }
 
+// Resident CTAs per SM at this dynamic shared memory: the smaller of the two
+// instantiations (both are built for kCtasPerSm).
 int decode_occupancy(int smem) {
   if (set_attr() != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_kernel, kThreads, smem) != cudaSuccess)
+  int n2 = 0, n4 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, decode_kernel<false>, kThreads, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n4, decode_kernel<true>, kThreads, smem) !=
+          cudaSuccess)
     return 0;
-  return n;
+  return n2 < n4 ? n2 : n4;
 }
 
 cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s) {
   if (smem > decode_max_smem()) return cudaErrorInvalidValue;
-  decode_kernel<<<grid, kThreads, smem, s>>>(p);
+  if (p.radix4_any)
+    decode_kernel<true><<<grid, kThreads, smem, s>>>(p);
+  else
+    decode_kernel<false><<<grid, kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@
 //
 // usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] FILE UES SECONDS RETX_FRACTION SEED
 //                     CELLS...
-// TABLE: a window-count table (188 numbers) installed with crnt_tune_set;
+// TABLE: a window-count table (188 numbers) installed with crnt_tune_set,
+// optionally followed by a radix table (188 numbers, crnt_tune_radix_set);
 // --purge: every TB asks for purge on failure (CRNT_F_PURGE);
 // --poisson: exponential inter-arrival times of mean 1 ms per cell instead of
 // the 1 ms period with jitter.
@@ -167,14 +168,21 @@ int main(int argc, char** argv) {
   if (argc > 2 && strcmp(argv[1], "--tune") == 0) {
     FILE* t = fopen(argv[2], "r");
     if (!t) return 2;
-    uint8_t table[CRNT_NUM_K];
+    uint8_t table[CRNT_NUM_K], radix[CRNT_NUM_K];
     for (int i = 0; i < CRNT_NUM_K; i++) {
       int v = 0;
       if (fscanf(t, "%d", &v) != 1) return 2;
       table[i] = (uint8_t)v;
     }
+    int nr = 0;  // an optional radix table follows
+    for (; nr < CRNT_NUM_K; nr++) {
+      int v = 0;
+      if (fscanf(t, "%d", &v) != 1) break;
+      radix[nr] = (uint8_t)v;
+    }
     fclose(t);
     if (crnt_tune_set(table, CRNT_NUM_K) != CRNT_OK) return 2;
+    if (nr == CRNT_NUM_K && crnt_tune_radix_set(radix, CRNT_NUM_K) != CRNT_OK) return 2;
     argv += 2;
     argc -= 2;
   }

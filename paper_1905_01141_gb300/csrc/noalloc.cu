@@ -243,6 +243,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
       d.max_iter = tp.max_iter;
       d.early_stop = tp.early_stop ? 1 : 0;
       d.new_data = 1;
+      d.radix4 = radix4_of(K);  // the process-wide radix table (a read)
       h_all_tb[ncb] = (int)t;
       h_all_r[ncb] = r;
       pay_off += d.pay_bits;
@@ -312,6 +313,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
   p.tb_ok = p.cb_ok + ncb;
   p.xpowA = (const uint32_t*)(ws + kOffXA);
   p.xpowB = (const uint32_t*)(ws + kOffXB);
+  for (int i = 0; i < ncb; i++) p.radix4_any |= h_cbs[i].radix4;
   const size_t res_bytes = 2 * (size_t)ncb + n;
   if (cudaMemcpyAsync(ws + kOffCbs, h_cbs, sizeof(CbDesc) * ncb, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||

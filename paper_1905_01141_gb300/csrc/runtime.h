@@ -146,6 +146,11 @@ void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res);
 int validate(const crnt_tb_params& t, lte::Seg* seg);
 // Window count of the process-wide table for CB size K (0 = built-in).
 int tuned_p(int K);
+// 1 if the radix table selects the radix-4 forward recursion for CB size K.
+// t_radix_override >= 0 replaces the table for plans built on this thread
+// (the autotuner's candidates).
+uint8_t radix4_of(int K);
+extern thread_local int t_radix_override;
 // Window count used for CB size K when a TB requests P (0 = table / built-in).
 int clamp_p(int K, int P);
 void serving_stop(crnt_ctx* ctx);

@@ -7,7 +7,9 @@
 // LLR values on the clamp-free path, so the inputs are zeros.  Candidates:
 // minimum window lengths w in {w_lo, 32, 40, 48, 56, 64, 80, 96} (w_lo: the
 // shortest allowed, which also uses the most threads), each giving
-// P = floor(K / w) windows of ceil(K / P) >= w steps.
+// P = floor(K / w) windows of ceil(K / P) >= w steps.  At the window count
+// it keeps, the tuner also times the radix-4 forward recursion (the same
+// decoded values) and selects it for that K when it is more than 1 % faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +21,7 @@
 
 namespace crnt {
 extern std::atomic<uint8_t> g_tuned[lte::kNumK];
+extern std::atomic<uint8_t> g_radix[lte::kNumK];
 
 namespace {
 
@@ -76,6 +79,26 @@ int crnt_tune_set(const uint8_t* P_by_k, uint32_t n) {
   return CRNT_OK;
 }
 
+int crnt_tune_radix_get(uint8_t* radix_by_k, uint32_t n) {
+  if (!radix_by_k) return CRNT_EINVAL;
+  for (uint32_t i = 0; i < n && i < (uint32_t)lte::kNumK; i++) {
+    const uint8_t r = g_radix[i].load(std::memory_order_relaxed);
+    radix_by_k[i] = r == 4 ? 4 : 2;
+  }
+  return CRNT_OK;
+}
+
+int crnt_tune_radix_set(const uint8_t* radix_by_k, uint32_t n) {
+  if (!radix_by_k || n != (uint32_t)lte::kNumK) return CRNT_EINVAL;
+  for (int i = 0; i < lte::kNumK; i++) {
+    const uint8_t r = radix_by_k[i];
+    if (r != 0 && r != 2 && r != 4) return CRNT_EINVAL;
+  }
+  for (int i = 0; i < lte::kNumK; i++)
+    g_radix[i].store(radix_by_k[i] == 4 ? 4 : 2, std::memory_order_relaxed);
+  return CRNT_OK;
+}
+
 int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
   if (!ctx) return CRNT_EINVAL;
   if (w_min == 0) w_min = 32;
@@ -120,12 +143,14 @@ int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
       cudaMemset(d_llr, 0, max_llr) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = CRNT_ENOMEM;
-  uint8_t table[lte::kNumK];
+  uint8_t table[lte::kNumK], radix[lte::kNumK];
   memset(table, 0, sizeof table);
+  memset(radix, 2, sizeof radix);
   {
     crnt_plan plan;  // re-planned per candidate; its buffers only grow
     for (int i = 0; i < lte::kNumK && rc == CRNT_OK; i++) {
       float best = 0.0f;
+      t_radix_override = 0;
       for (Cand& c : cands[i]) {
         float ms = 0.0f;
         rc = time_batch(ctx, &plan, c.K, c.P, c.n, d_llr, d_out, e0, e1, &ms);
@@ -133,19 +158,30 @@ int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
         c.rate = (float)c.n * (float)c.K / ms;
         best = std::max(best, c.rate);
       }
+      if (rc) break;
       // the longest windows among the candidates within 1 % of the fastest
-      int pick = 0;
+      const Cand* pick = nullptr;
       for (const Cand& c : cands[i])
-        if (c.rate >= 0.99f * best && (!pick || c.P < pick)) pick = c.P;
-      table[i] = (uint8_t)pick;
+        if (c.rate >= 0.99f * best && (!pick || c.P < pick->P)) pick = &c;
+      table[i] = (uint8_t)pick->P;
+      // the radix-4 forward recursion at that window count
+      float ms4 = 0.0f;
+      t_radix_override = 1;
+      rc = time_batch(ctx, &plan, pick->K, pick->P, pick->n, d_llr, d_out, e0, e1, &ms4);
+      if (rc) break;
+      if ((float)pick->n * (float)pick->K / ms4 > 1.01f * pick->rate) radix[i] = 4;
     }
+    t_radix_override = -1;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (d_llr) cudaFree(d_llr);
   if (d_out) cudaFree(d_out);
   if (rc) return rc;
-  for (int i = 0; i < lte::kNumK; i++) g_tuned[i].store(table[i], std::memory_order_relaxed);
+  for (int i = 0; i < lte::kNumK; i++) {
+    g_tuned[i].store(table[i], std::memory_order_relaxed);
+    g_radix[i].store(radix[i], std::memory_order_relaxed);
+  }
   if (P_by_k) memcpy(P_by_k, table, sizeof table);
   return CRNT_OK;
 }

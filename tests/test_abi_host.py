@@ -115,3 +115,28 @@ def test_tune_table_drives_p0_windows(crnt_lib):
         assert crnt_lib.tb_layout(dict(A=6120, G=18444))[0]["P"] == 128
     finally:
         crnt_lib.tune_set(old)
+
+
+def test_radix_table_get_set(crnt_lib):
+    # the forward-recursion radix table: 2 by default, 4 where selected; it
+    # changes no decoded value, so crnt_tb_layout does not depend on it
+    old = crnt_lib.tune_radix_get()
+    try:
+        crnt_lib.tune_radix_set([0] * crnt_lib.NUM_K)
+        assert crnt_lib.tune_radix_get() == [2] * crnt_lib.NUM_K
+        lay2 = crnt_lib.tb_layout(dict(A=75376, G=86400, Qm=6))
+        t = [2] * crnt_lib.NUM_K
+        t[-1] = 4
+        t[100] = 4
+        crnt_lib.tune_radix_set(t)
+        assert crnt_lib.tune_radix_get() == t
+        assert crnt_lib.tb_layout(dict(A=75376, G=86400, Qm=6)) == lay2
+        for bad in (1, 3, 8, 255):
+            with pytest.raises(crnt_lib.CrntError):
+                crnt_lib.tune_radix_set([bad] * crnt_lib.NUM_K)
+        assert crnt_lib.tune_radix_get() == t       # a refused table changes nothing
+        arr = (ctypes.c_uint8 * 10)()
+        assert crnt_lib.load().crnt_tune_radix_set(arr, 10) == crnt_lib.EINVAL
+        assert crnt_lib.load().crnt_tune_radix_get(None, 188) == crnt_lib.EINVAL
+    finally:
+        crnt_lib.tune_radix_set(old)

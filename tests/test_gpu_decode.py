@@ -221,9 +221,11 @@ def test_autotuned_windows_match_oracle(orc, crnt_lib, ctx):
     # where K allows); P = 0 TBs then decode with it, still bit-exact with
     # the oracle run at the same window counts
     old = crnt_lib.tune_get()
+    old_radix = crnt_lib.tune_radix_get()
     try:
         table = ctx.autotune(32)
         assert table == crnt_lib.tune_get()
+        assert set(crnt_lib.tune_radix_get()) <= {2, 4}
         ks = list(orc.k_table())
         assert len(ks) == len(table) == 188
         for K, P in zip(ks, table):
@@ -237,6 +239,44 @@ def test_autotuned_windows_match_oracle(orc, crnt_lib, ctx):
         check_batch(orc, crnt_lib, tbs, llrs, g)
     finally:
         crnt_lib.tune_set(old)
+        crnt_lib.tune_radix_set(old_radix)
+
+
+@pytest.fixture
+def radix4(crnt_lib):
+    """The radix-4 forward recursion selected for every CB size."""
+    old = crnt_lib.tune_radix_get()
+    crnt_lib.tune_radix_set([4] * crnt_lib.NUM_K)
+    yield
+    crnt_lib.tune_radix_set(old)
+
+
+@pytest.mark.parametrize("P", [1, 8, 128])
+def test_radix4_forward_single_cb(orc, crnt_lib, ctx, radix4, P):
+    # two trellis steps per forward update on clamp-free passes: the same
+    # metrics as radix 2, so every output stays bit-exact with the oracle
+    tbs, llrs = batch(orc, [dict(A=6120, G=18444, Qm=2, P=P, max_iter=6, seed=s, ebn0=1.0)
+                            for s in range(3)])
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
+
+
+def test_radix4_forward_mixed_and_saturating(orc, crnt_lib, ctx, radix4):
+    # every CB size class, ragged windows (K not a multiple of 4 P), both
+    # the clamp-free passes (radix 4) and, with noiseless and very strong
+    # inputs whose extrinsics grow large, passes that may saturate (radix 2)
+    shapes = synth.tti_batch(seed=9, n_tb=30, amax=30000)
+    shapes += synth.tti_batch(seed=10, n_tb=3, amin=60000)
+    specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=6, early_stop=i % 2,
+                  rv=i % 4, seed=300 + i, snr=s["snr_db"]) for i, s in enumerate(shapes)]
+    specs += [dict(A=6120, G=18444, Qm=2, P=P, max_iter=8, early_stop=0, seed=40 + P,
+                   noiseless=True) for P in (1, 3, 64)]
+    specs += [dict(A=520, G=1600, Qm=2, P=7, max_iter=8, early_stop=0, seed=45, snr=40.0),
+              dict(A=16, G=132, Qm=2, seed=46, snr=2.0),
+              dict(A=3000, G=3100, Qm=2, seed=47, snr=-10.0)]
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    check_batch(orc, crnt_lib, tbs, llrs, g)
 
 
 def test_purge_on_failure(orc, crnt_lib, ctx):
