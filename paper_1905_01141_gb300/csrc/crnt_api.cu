@@ -187,6 +187,62 @@ int tuned_p(int K) {
 
 thread_local int t_radix_override = -1;
 
+// Entry (g, p, k) of the (K, P) table is step j = kSub g + k of window p of
+// the interleaved pass: natural position q = PI(p W + j) (QPP, Sec. IV-B
+// Fig. 4's interleaver) and its transposed shared-memory index
+// (q mod W) P + q / W, laid out as the decoder reads them (one 16-byte group
+// of kSub addresses per window, windows adjacent); steps past a window's end
+// and the two extra last groups are zero.
+const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
+  QTabs* qs = ctx->qtabs;
+  const int ki = lte::index_of(K);
+  if (!qs || ki < 0 || P < 1 || P > (int)CRNT_MAX_P) return nullptr;
+  const uint4* r = qs->t[ki][P].load(std::memory_order_acquire);
+  if (r) return r;
+  std::lock_guard<std::mutex> lk(qs->mu);
+  r = qs->t[ki][P].load(std::memory_order_relaxed);
+  if (r) return r;
+  const int W = (K + P - 1) / P;
+  if ((K + W - 1) / W != P) return nullptr;
+  const int ng = (W + kSub - 1) / kSub + 2;
+  const size_t tb = (size_t)ng * P * 16, bytes = tb + (size_t)ng * P * 8;
+  const size_t need = al256(bytes);
+  if (qs->left < need) {
+    const size_t sz = std::max(need, (size_t)8 << 20);
+    void* p = nullptr;
+    if (cudaMalloc(&p, sz) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    qs->chunks.push_back(p);
+    qs->cur = (uint8_t*)p;
+    qs->left = sz;
+  }
+  std::vector<uint8_t> h(bytes, 0);
+  uint32_t* ht = (uint32_t*)h.data();
+  uint16_t* hq = (uint16_t*)(h.data() + tb);
+  const int64_t f1 = lte::kF1[ki], f2 = lte::kF2[ki];
+  for (int p = 0; p < P; p++) {
+    const int lo = p * W, len = std::min(W, K - lo);
+    for (int j = 0; j < len; j++) {
+      const int64_t i = lo + j;
+      const int q = (int)((f1 * i + (f2 * i % K) * i) % K);
+      const size_t e = ((size_t)(j / kSub) * P + p) * kSub + j % kSub;
+      ht[e] = (uint32_t)((q % W) * P + q / W);
+      hq[e] = (uint16_t)q;
+    }
+  }
+  uint8_t* dev = qs->cur;
+  if (cudaMemcpyAsync(dev, h.data(), bytes, cudaMemcpyHostToDevice, qs->stream) != cudaSuccess ||
+      cudaStreamSynchronize(qs->stream) != cudaSuccess)
+    return nullptr;
+  qs->cur += need;
+  qs->left -= need;
+  r = (const uint4*)dev;
+  qs->t[ki][P].store(r, std::memory_order_release);
+  return r;
+}
+
 uint8_t radix4_of(int K) {
   if (t_radix_override >= 0) return (uint8_t)t_radix_override;
   const int ki = lte::index_of(K);
@@ -385,7 +441,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   int max_slot_bytes = 0;
   WorkItem wi{0, 0, 0, 0};
   int gmax = 0, iK = -1, iP = -1;
-  bool radix4_any = false;
+  bool radix4_any = false, qtab_all = true;
   for (uint32_t i = 0; i < ncb; i++) {
     const uint32_t g = (uint32_t)(pl->keyed[i] & 0x1FFFFFF);
     const uint32_t t = pl->owner[g];
@@ -440,6 +496,9 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     d.purge = (tp.flags & CRNT_F_PURGE) && s.C > 1 ? 1 : 0;
     d.radix4 = radix4_of(tm.K);
     radix4_any |= d.radix4 != 0;
+    d.qt = qtab_get(ctx, tm.K, tm.P);
+    d.qq = qtab_q(d.qt, tm.K, tm.P);
+    qtab_all &= d.qt != nullptr;
     memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;
     pl->cb_r[i] = r;
@@ -520,6 +579,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   p.xpowB = ctx->xpowB;
   p.mi_tab = ctx->mi_tab;
   p.radix4_any = radix4_any ? 1 : 0;
+  p.qtab_all = qtab_all && ncb > 0 ? 1 : 0;
   return CRNT_OK;
 }
 
@@ -675,6 +735,20 @@ int crnt_create(crnt_ctx** out, const crnt_config* cfg) {
     crnt_destroy(c);
     return CRNT_EDEVICE;
   }
+  // address tables of the window counts P = 0 requests get now (others on
+  // first use); without them the decoder computes the addresses
+  c->qtabs = new (std::nothrow) QTabs;
+  if (c->qtabs &&
+      cudaStreamCreateWithFlags(&c->qtabs->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c->qtabs;
+    c->qtabs = nullptr;
+  }
+  if (c->qtabs) {
+    for (int i = 0; i < lte::kNumK; i++) {
+      const int K = lte::k_of(i), Pr = clamp_p(K, 0), W = (K + Pr - 1) / Pr;
+      qtab_get(c, K, (K + W - 1) / W);
+    }
+  }
   *out = c;
   return CRNT_OK;
 }
@@ -698,6 +772,12 @@ int crnt_destroy(crnt_ctx* ctx) {
   if (ctx->xpowA) cudaFree(ctx->xpowA);
   if (ctx->xpowB) cudaFree(ctx->xpowB);
   if (ctx->mi_tab) cudaFree(ctx->mi_tab);
+  if (ctx->qtabs) {
+    for (void* p : ctx->qtabs->chunks) cudaFree(p);
+    if (ctx->qtabs->stream) cudaStreamDestroy(ctx->qtabs->stream);
+    delete ctx->qtabs;
+    ctx->qtabs = nullptr;
+  }
   if (ctx->harq.arena) cudaFree(ctx->harq.arena);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

@@ -46,6 +46,10 @@ struct CbDesc {
   uint8_t purge;           // 1: stop when another CB of the TB has failed
   uint8_t radix4;          // 1: radix-4 forward recursion where the pass is clamp-free
   uint8_t pad0[2];
+  const uint4* qt;         // interleaved-pass address table of (K, P), or null:
+                           // [ceil(W/kSub) + 2 groups][P windows] x kSub
+                           // transposed addresses (the last two groups zero)
+  const uint2* qq;         // the same steps' natural positions (uint16, same order)
 };
 
 struct TbDesc {
@@ -91,6 +95,7 @@ struct DecParams {
   int16_t* dbg_ext;       // optional: [sum K] final extrinsic, natural order
   uint8_t* dbg_hard;      // optional: [sum K] hard decisions
   int32_t radix4_any;     // some CB selects the radix-4 forward recursion
+  int32_t qtab_all;       // every CB has an interleaved-pass address table
 };
 
 // Encoder launch description: one CB per CTA.

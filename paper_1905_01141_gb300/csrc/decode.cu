@@ -482,6 +482,8 @@ struct Win {
   int p, lo, len, pad;
   bool hard_on;             // DEC 1: form the hard decisions
   bool r4;                  // radix-4 forward recursion on the clamp-free path
+  const uint4* __restrict__ qt;  // interleaved-pass address table (QT kernels)
+  const uint2* __restrict__ qq;  // its natural positions, 16 bits each
 };
 
 __device__ __forceinline__ int tr_w(const Win& w, int q) {
@@ -490,22 +492,35 @@ __device__ __forceinline__ int tr_w(const Win& w, int q) {
 }
 
 // Load the branch-metric inputs of step j (window-relative) of pass DEC.
-// DEC 1 walks the QPP addresses (q, dq) and returns the natural position.
-template <int DEC>
-__device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, int& S, int& Lp,
-                                          int& t) {
+// DEC 1 walks the QPP addresses (q, dq) and returns the natural position;
+// with QT the caller passes the step's transposed address tq, read from the
+// CB's address table, and q, dq are not used.
+template <int DEC, bool QT>
+__device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, int tq, int& S,
+                                          int& Lp, int& t) {
   const int idx = j * w.P + w.p;
   if (DEC == 0) {
     t = idx;
+  } else if (QT) {
+    t = tq;
   } else {
     t = tr_w(w, q);
   }
   S = (int)w.sys[t] + (int)w.ext[t];
   Lp = w.par[idx];
-  if (DEC == 1) {
+  if (DEC == 1 && !QT) {
     q = modadd(q, dq, w.K);
     dq = modadd(dq, w.f2x2, w.K);
   }
+}
+
+// Component k (compile-time after unrolling) of a table entry.
+__device__ __forceinline__ int comp4(const uint4& e, int k) {
+  return k == 0 ? (int)e.x : k == 1 ? (int)e.y : k == 2 ? (int)e.z : (int)e.w;
+}
+__device__ __forceinline__ int comp2(const uint2& e, int k) {
+  const unsigned v = k < 2 ? e.x : e.y;
+  return (k & 1) ? (int)(v >> 16) : (int)(v & 0xFFFFu);
 }
 
 // Backward processing of one sub-window [j0, j0 + slen) of a window:
@@ -514,10 +529,12 @@ __device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, 
 // (no per-step guards).  mx / mn track the largest / smallest extrinsic
 // written.  With
 // w.hard_on (DEC 1 only) the hard decisions sign(Lambda) are also recorded
-// at the natural positions.
-template <int DEC, bool FULL, bool CHK>
+// at the natural positions.  QT (DEC 1): te holds the sub-window's four
+// transposed addresses and qe (with w.hard_on) their natural positions.
+template <int DEC, bool FULL, bool CHK, bool QT>
 __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
-                                                int dq, int b[8], int& mx, int& mn) {
+                                                int dq, uint4 te, uint2 qe, int b[8], int& mx,
+                                                int& mn) {
   int A[kSub][8];
   int Sv[kSub], Lv[kSub], Qv[kSub];
   int vprev = 0;  // extrinsics enter the max / min tracking in pairs
@@ -525,9 +542,10 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
 #pragma unroll
   for (int jj = 0; jj < kSub; jj++) {
     if (FULL || jj < slen) {
-      Qv[jj] = q;
+      if (!QT) Qv[jj] = q;
       int t;
-      load_step<DEC>(w, j0 + jj, q, dq, Sv[jj], Lv[jj], t);
+      load_step<DEC, QT>(w, j0 + jj, q, dq, QT ? comp4(te, jj) : 0, Sv[jj], Lv[jj], t);
+      if (QT) Qv[jj] = t;
       if (jj + 1 < kSub && (FULL || jj + 1 < slen))
         alpha_step<CHK>(A[jj], A[jj + 1], Sv[jj], Sv[jj] + Lv[jj], Lv[jj]);
     }
@@ -545,9 +563,9 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
         mx = __vimax3_s32(mx, vprev, v);
         mn = __vimin3_s32(mn, vprev, v);
       }
-      w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : tr_w(w, Qv[jj])] = (int16_t)v;
+      w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : QT ? Qv[jj] : tr_w(w, Qv[jj])] = (int16_t)v;
       if (DEC == 1 && w.hard_on) {  // branch-free: ORs a zero when lam >= 0
-        const int qq = Qv[jj] + w.pad;
+        const int qq = (QT ? comp2(qe, jj) : Qv[jj]) + w.pad;
         atomicOr(&w.hard[qq >> 5], ((unsigned)lam >> 31) << (31 - (qq & 31)));
       }
       beta_step<CHK>(b, S, S + Lp, Lp);
@@ -557,45 +575,71 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
 
 // Forward and backward recursions of one window (after the seeds are read).
 // R4: the kernel instantiation that carries the radix-4 forward recursion
-// (used by CBs with radix4 set, on clamp-free passes).
-template <int DEC, bool CHK, bool R4>
+// (used by CBs with radix4 set, on clamp-free passes).  QT: the interleaved
+// pass reads its addresses from the CB's table (w.qt, one uint4 of four
+// transposed addresses per kSub-step group and window, plus two zero groups
+// at the end so that groups can always be fetched two ahead).  The table
+// lives in global memory (L2), so its loads are issued ahead of use: groups
+// 0 and 1 (pf0, pf1) before the pass's barrier, then two groups ahead in the
+// forward pass and one sub-window ahead in the backward pass, whose first
+// group is fetched before the forward pass.
+template <int DEC, bool CHK, bool R4, bool QT>
 __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restrict__ dp,
                                             uint4* ck, uint4* seedA, uint4* seedB, int a[8],
-                                            int b[8], int& mx, int& mn) {
+                                            int b[8], int& mx, int& mn, uint4 pf0, uint4 pf1) {
+  constexpr bool TQ = QT && DEC == 1;  // table addresses in this pass
   const int K = w.K, P = w.P, p = w.p, lo = w.lo, len = w.len;
   const int f1 = dp->f1, f2 = dp->f2;
   const int f2sub = DEC ? dp->f2sub : 0, f2jump = DEC ? dp->f2jump : 0;
+  const uint4* __restrict__ tq = TQ ? w.qt + p : nullptr;  // group g at tq[g * P]
 
   // ---- forward pass with a checkpoint every kSub steps
   int q = 0, dq = 0;
-  if (DEC == 1) {
+  if (DEC == 1 && !TQ) {
     q = qpp_at(lo, f1, f2, K);
     dq = (f1 + (f2 * ((2 * lo + 1) % K)) % K) % K;
+  }
+  const int nsub = (len + kSub - 1) / kSub;
+  uint4 te = pf0, te1 = pf1, tb = make_uint4(0u, 0u, 0u, 0u);
+  uint2 qn = make_uint2(0u, 0u);
+  if (TQ) {
+    tb = __ldg(tq + (nsub - 1) * P);
+    if (w.hard_on) qn = __ldg(w.qq + (nsub - 1) * P + p);
   }
   int j0 = 0;
   if (R4 && !CHK && w.r4) {  // radix-4 forward recursion (same metrics, see alpha_step_r4)
     for (; j0 + kSub <= len; j0 += kSub) {
       ck[j0 / kSub] = pack_norm<CHK>(a);
+      const uint4 cur = te;
+      if (TQ) {
+        te = te1;
+        te1 = __ldg(tq + (j0 / kSub + 2) * P);
+      }
 #pragma unroll
       for (int jj = 0; jj < kSub; jj += 4) {
         int S0, L0, S1, L1, t, o[8];
-        load_step<DEC>(w, j0 + jj, q, dq, S0, L0, t);
-        load_step<DEC>(w, j0 + jj + 1, q, dq, S1, L1, t);
+        load_step<DEC, TQ>(w, j0 + jj, q, dq, comp4(cur, jj), S0, L0, t);
+        load_step<DEC, TQ>(w, j0 + jj + 1, q, dq, comp4(cur, jj + 1), S1, L1, t);
         alpha_step_r4(a, o, S0, L0, S1, L1);
-        load_step<DEC>(w, j0 + jj + 2, q, dq, S0, L0, t);
-        load_step<DEC>(w, j0 + jj + 3, q, dq, S1, L1, t);
+        load_step<DEC, TQ>(w, j0 + jj + 2, q, dq, comp4(cur, jj + 2), S0, L0, t);
+        load_step<DEC, TQ>(w, j0 + jj + 3, q, dq, comp4(cur, jj + 3), S1, L1, t);
         alpha_step_r4(o, a, S0, L0, S1, L1);
       }
     }
   } else {
     for (; j0 + kSub <= len; j0 += kSub) {
       ck[j0 / kSub] = pack_norm<CHK>(a);
+      const uint4 cur = te;
+      if (TQ) {
+        te = te1;
+        te1 = __ldg(tq + (j0 / kSub + 2) * P);
+      }
 #pragma unroll
       for (int jj = 0; jj < kSub; jj += 2) {
         int S, Lp, t, o[8];
-        load_step<DEC>(w, j0 + jj, q, dq, S, Lp, t);
+        load_step<DEC, TQ>(w, j0 + jj, q, dq, comp4(cur, jj), S, Lp, t);
         alpha_step<CHK>(a, o, S, S + Lp, Lp);
-        load_step<DEC>(w, j0 + jj + 1, q, dq, S, Lp, t);
+        load_step<DEC, TQ>(w, j0 + jj + 1, q, dq, comp4(cur, jj + 1), S, Lp, t);
         alpha_step<CHK>(o, a, S, S + Lp, Lp);
       }
     }
@@ -604,7 +648,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     ck[j0 / kSub] = pack_norm<CHK>(a);
     for (int j = j0; j < len; j++) {
       int S, Lp, t, o[8];
-      load_step<DEC>(w, j, q, dq, S, Lp, t);
+      load_step<DEC, TQ>(w, j, q, dq, TQ ? comp4(te, j - j0) : 0, S, Lp, t);
       alpha_step<CHK>(a, o, S, S + Lp, Lp);
 #pragma unroll
       for (int s = 0; s < 8; s++) a[s] = o[s];
@@ -616,10 +660,9 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
   // at the start of the last sub-window, walked backwards by kSub steps:
   // PI(x - kSub) = PI(x) - J(x - kSub) with J(x) = kSub f1 + f2 (2 kSub x +
   // kSub^2), J(x - kSub) = J(x) - 2 kSub^2 f2, delta(x - kSub) = delta(x) -
-  // 2 kSub f2.
-  const int nsub = (len + kSub - 1) / kSub;
+  // 2 kSub f2.  With the table, sub-window sw reads group sw instead.
   int pis = 0, dls = 0, jmp = 0;
-  if (DEC == 1) {
+  if (DEC == 1 && !TQ) {
     const int is = lo + kSub * (nsub - 1);
     pis = qpp_at(is, f1, f2, K);
     dls = (f1 + (f2 * ((2 * is + 1) % K)) % K) % K;
@@ -628,10 +671,18 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     jmp = ((kSub * f1) % K + (f2 * t) % K) % K;
   }
   int sw = nsub - 1;
+  te = tb;
   const int last_len = len - kSub * sw;
   if (last_len < kSub) {
-    sub_window_back<DEC, false, CHK>(w, ck[sw], kSub * sw, last_len, pis, dls, b, mx, mn);
-    if (DEC == 1) {
+    const uint4 cur = te;
+    const uint2 qcur = qn;
+    if (TQ) {
+      te = __ldg(tq + max(sw - 1, 0) * P);
+      if (w.hard_on) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
+    }
+    sub_window_back<DEC, false, CHK, TQ>(w, ck[sw], kSub * sw, last_len, pis, dls, cur, qcur, b,
+                                         mx, mn);
+    if (DEC == 1 && !TQ) {
       pis = modsub(pis, jmp, K);
       dls = modsub(dls, f2sub, K);
       jmp = modsub(jmp, f2jump, K);
@@ -639,8 +690,15 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     sw--;
   }
   for (; sw >= 0; sw--) {
-    sub_window_back<DEC, true, CHK>(w, ck[sw], kSub * sw, kSub, pis, dls, b, mx, mn);
-    if (DEC == 1) {
+    const uint4 cur = te;
+    const uint2 qcur = qn;
+    if (TQ) {
+      te = __ldg(tq + max(sw - 1, 0) * P);
+      if (w.hard_on) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
+    }
+    sub_window_back<DEC, true, CHK, TQ>(w, ck[sw], kSub * sw, kSub, pis, dls, cur, qcur, b, mx,
+                                        mn);
+    if (DEC == 1 && !TQ) {
       pis = modsub(pis, jmp, K);
       dls = modsub(dls, f2sub, K);
       jmp = modsub(jmp, f2jump, K);
@@ -656,7 +714,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
 // bounds |La| for the pass that reads it.  hard (DEC 1): the hard decisions
 // of this iteration are used (a CRC check follows); otherwise they are not
 // formed, since the next iteration overwrites them unread.
-template <int DEC, bool R4>
+template <int DEC, bool R4, bool QT>
 __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t* base, int p,
                                           bool run, bool first, bool hard) {
   const int K = dp->K, P = dp->P, W = dp->W;
@@ -667,6 +725,12 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
 
   int a[8], b[8];
   int m_in = 0;
+  uint4 pf0 = make_uint4(0u, 0u, 0u, 0u), pf1 = pf0;
+  if (QT && DEC == 1 && run) {  // the first two address groups, fetched across the barrier
+    const uint4* __restrict__ qt = dp->qt;
+    pf0 = __ldg(qt + p);
+    pf1 = __ldg(qt + P + p);
+  }
   if (run) {
     if (p == 0) {
       a[0] = OFF;
@@ -704,6 +768,8 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     w.hard = sl.hard;
     w.hard_on = hard;
     w.r4 = R4 && dp->radix4 != 0;
+    w.qt = QT ? dp->qt : nullptr;
+    w.qq = QT ? dp->qq : nullptr;
     w.K = K;
     w.P = P;
     w.W = W;
@@ -721,9 +787,9 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
     }
     int mx = 0, mn = 0;
     if (window_fast(a, b, 254 + m_in))
-      window_pass<DEC, false, R4>(w, dp, ck, seedA, seedB, a, b, mx, mn);
+      window_pass<DEC, false, R4, QT>(w, dp, ck, seedA, seedB, a, b, mx, mn, pf0, pf1);
     else
-      window_pass<DEC, true, R4>(w, dp, ck, seedA, seedB, a, b, mx, mn);
+      window_pass<DEC, true, R4, QT>(w, dp, ck, seedA, seedB, a, b, mx, mn, pf0, pf1);
     atomicMax(&sl.flags[4 + DEC], max(mx, -mn));
   }
   __syncthreads();
@@ -756,8 +822,9 @@ __device__ uint32_t crc_share(const CbDesc& d, const CbSlot& sl, int p, const ui
 
 // R4 = false: the radix-2 kernel; R4 = true adds the radix-4 forward
 // recursion for CBs that select it (a separate instantiation, so the radix-2
-// kernel's code is not affected by the option).
-template <bool R4>
+// kernel's code is not affected by the option).  QT: every CB carries an
+// address table for its interleaved pass (else the addresses are computed).
+template <bool R4, bool QT>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams prm) {
   __shared__ int s_item;
   __shared__ int s_remaining;
@@ -842,9 +909,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
       const int my_max = mine ? (int)dp->max_iter : 0;
       const bool run = mine && fl[0] == 0 && it <= my_max;
       const bool first = (it == 1);
-      siso_pass<0, R4>(dp, mybase, p, run, first, false);
+      siso_pass<0, R4, QT>(dp, mybase, p, run, first, false);
       const bool check = run && (dp->early_stop || it == my_max);
-      siso_pass<1, R4>(dp, mybase, p, run, first, check);
+      siso_pass<1, R4, QT>(dp, mybase, p, run, first, check);
       if (check) {
         const CbDesc& d = *dp;
         const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
@@ -959,35 +1026,51 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
 
 int decode_max_smem() { return kSmemBudget + kSmemFixed; }
 
+template <bool R4, bool QT>
+cudaError_t set_attr_one() {
+  return cudaFuncSetAttribute(decode_kernel<R4, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              decode_max_smem());
+}
 static cudaError_t set_attr() {
-  cudaError_t e = cudaFuncSetAttribute(decode_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       decode_max_smem());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             decode_max_smem());
+  cudaError_t e = set_attr_one<false, false>();
+  if (e == cudaSuccess) e = set_attr_one<false, true>();
+  if (e == cudaSuccess) e = set_attr_one<true, false>();
+  if (e == cudaSuccess) e = set_attr_one<true, true>();
   return e;
 }
 
-// Resident CTAs per SM at this dynamic shared memory: the smaller of the two
-// instantiations (both are built for kCtasPerSm).
+template <bool R4, bool QT>
+int occupancy_one(int smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_kernel<R4, QT>, kThreads, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+// Resident CTAs per SM at this dynamic shared memory: the smallest over the
+// kernel's instantiations (all are built for kCtasPerSm).
 int decode_occupancy(int smem) {
   if (set_attr() != cudaSuccess) return 0;
-  int n2 = 0, n4 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, decode_kernel<false>, kThreads, smem) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n4, decode_kernel<true>, kThreads, smem) !=
-          cudaSuccess)
-    return 0;
-  return n2 < n4 ? n2 : n4;
+  const int a = occupancy_one<false, false>(smem), b = occupancy_one<false, true>(smem);
+  const int c = occupancy_one<true, false>(smem), d = occupancy_one<true, true>(smem);
+  const int ab = a < b ? a : b, cd = c < d ? c : d;
+  return ab < cd ? ab : cd;
 }
 
 cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s) {
   if (smem > decode_max_smem()) return cudaErrorInvalidValue;
-  if (p.radix4_any)
-    decode_kernel<true><<<grid, kThreads, smem, s>>>(p);
-  else
-    decode_kernel<false><<<grid, kThreads, smem, s>>>(p);
+  if (p.radix4_any) {
+    if (p.qtab_all)
+      decode_kernel<true, true><<<grid, kThreads, smem, s>>>(p);
+    else
+      decode_kernel<true, false><<<grid, kThreads, smem, s>>>(p);
+  } else {
+    if (p.qtab_all)
+      decode_kernel<false, true><<<grid, kThreads, smem, s>>>(p);
+    else
+      decode_kernel<false, false><<<grid, kThreads, smem, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

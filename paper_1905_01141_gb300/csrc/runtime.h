@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -55,6 +56,22 @@ struct HarqPool {
 
 struct Serving;
 
+// Address tables of the interleaved SISO pass, one per (K, P) on the
+// context's device (CbDesc::qt): built on the host and uploaded on first
+// use, kept until the context is destroyed.
+struct QTabs {
+  std::mutex mu;  // guards building (readers use the atomics)
+  std::atomic<const uint4*> t[lte::kNumK][CRNT_MAX_P + 1];
+  std::vector<void*> chunks;  // device allocations
+  uint8_t* cur = nullptr;     // free space in the last chunk
+  size_t left = 0;
+  cudaStream_t stream = nullptr;
+  QTabs() {
+    for (auto& row : t)
+      for (auto& x : row) x.store(nullptr, std::memory_order_relaxed);
+  }
+};
+
 // Fields of a CB descriptor fixed by (K, requested P) alone.
 struct KTmpl {
   int32_t K, W, P, divM, divS, f1, f2, f2x2, f2sub, f2jump, R, ND, ncb, slot;
@@ -71,6 +88,7 @@ struct crnt_ctx {
   uint32_t* xpowA = nullptr;
   uint32_t* xpowB = nullptr;
   int32_t* mi_tab = nullptr;  // [kMiTable] table of the mutual-information stop rule
+  crnt::QTabs* qtabs = nullptr;  // interleaved-pass address tables
   crnt::HarqPool harq;
   std::mutex harq_mu;     // guards harq
   std::mutex stage_mu;    // guards the staging buffers and the cached plan
@@ -146,6 +164,15 @@ void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res);
 int validate(const crnt_tb_params& t, lte::Seg* seg);
 // Window count of the process-wide table for CB size K (0 = built-in).
 int tuned_p(int K);
+// The interleaved-pass address table of CB size K split into P windows of
+// W = ceil(K / P) steps (P as used: ceil(K / W) == P); its natural-position
+// part follows at qtab_q.  Null when it cannot be built (no device memory):
+// the decoder then computes the addresses.
+const uint4* qtab_get(crnt_ctx* ctx, int K, int P);
+inline const uint2* qtab_q(const uint4* t, int K, int P) {
+  const int W = (K + P - 1) / P;
+  return t ? (const uint2*)(t + (size_t)((W + kSub - 1) / kSub + 2) * P) : nullptr;
+}
 // 1 if the radix table selects the radix-4 forward recursion for CB size K.
 // t_radix_override >= 0 replaces the table for plans built on this thread
 // (the autotuner's candidates).
