@@ -24,6 +24,8 @@
 // Forward metrics are checkpointed every kSub steps and recomputed, kSub
 // steps at a time, into registers during the backward pass.
 #include <cstdint>
+#include <type_traits>
+
 #include "crnt_internal.h"
 #include "rm_geom.cuh"
 
@@ -529,9 +531,11 @@ __device__ __forceinline__ int comp2(const uint2& e, int k) {
 // (no per-step guards).  mx / mn track the largest / smallest extrinsic
 // written.  With
 // w.hard_on (DEC 1 only) the hard decisions sign(Lambda) are also recorded
-// at the natural positions.  QT (DEC 1): te holds the sub-window's four
-// transposed addresses and qe (with w.hard_on) their natural positions.
-template <int DEC, bool FULL, bool CHK, bool QT>
+// at the natural positions; HM selects that test at compile time (0: no
+// hard decisions, 1: hard decisions, 2: read w.hard_on).  QT (DEC 1): te
+// holds the sub-window's four transposed addresses and qe (with hard
+// decisions) their natural positions.
+template <int DEC, bool FULL, bool CHK, bool QT, int HM>
 __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
                                                 int dq, uint4 te, uint2 qe, int b[8], int& mx,
                                                 int& mn) {
@@ -564,7 +568,7 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
         mn = __vimin3_s32(mn, vprev, v);
       }
       w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : QT ? Qv[jj] : tr_w(w, Qv[jj])] = (int16_t)v;
-      if (DEC == 1 && w.hard_on) {  // branch-free: ORs a zero when lam >= 0
+      if (DEC == 1 && (HM == 1 || (HM == 2 && w.hard_on))) {  // ORs a zero when lam >= 0
         const int qq = (QT ? comp2(qe, jj) : Qv[jj]) + w.pad;
         atomicOr(&w.hard[qq >> 5], ((unsigned)lam >> 31) << (31 - (qq & 31)));
       }
@@ -680,8 +684,8 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
       te = __ldg(tq + max(sw - 1, 0) * P);
       if (w.hard_on) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
     }
-    sub_window_back<DEC, false, CHK, TQ>(w, ck[sw], kSub * sw, last_len, pis, dls, cur, qcur, b,
-                                         mx, mn);
+    sub_window_back<DEC, false, CHK, TQ, 2>(w, ck[sw], kSub * sw, last_len, pis, dls, cur, qcur,
+                                            b, mx, mn);
     if (DEC == 1 && !TQ) {
       pis = modsub(pis, jmp, K);
       dls = modsub(dls, f2sub, K);
@@ -689,21 +693,30 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     }
     sw--;
   }
-  for (; sw >= 0; sw--) {
-    const uint4 cur = te;
-    const uint2 qcur = qn;
-    if (TQ) {
-      te = __ldg(tq + max(sw - 1, 0) * P);
-      if (w.hard_on) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
+  // the full sub-windows, in two copies so that passes without hard
+  // decisions carry no per-step test for them
+  auto full_back = [&](auto hm) {
+    constexpr int HM = decltype(hm)::value;
+    for (; sw >= 0; sw--) {
+      const uint4 cur = te;
+      const uint2 qcur = qn;
+      if (TQ) {
+        te = __ldg(tq + max(sw - 1, 0) * P);
+        if (HM == 1) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
+      }
+      sub_window_back<DEC, true, CHK, TQ, HM>(w, ck[sw], kSub * sw, kSub, pis, dls, cur, qcur, b,
+                                              mx, mn);
+      if (DEC == 1 && !TQ) {
+        pis = modsub(pis, jmp, K);
+        dls = modsub(dls, f2sub, K);
+        jmp = modsub(jmp, f2jump, K);
+      }
     }
-    sub_window_back<DEC, true, CHK, TQ>(w, ck[sw], kSub * sw, kSub, pis, dls, cur, qcur, b, mx,
-                                        mn);
-    if (DEC == 1 && !TQ) {
-      pis = modsub(pis, jmp, K);
-      dls = modsub(dls, f2sub, K);
-      jmp = modsub(jmp, f2jump, K);
-    }
-  }
+  };
+  if (DEC == 1 && w.hard_on)
+    full_back(std::integral_constant<int, 1>());
+  else
+    full_back(std::integral_constant<int, 0>());
   if (p > 0) seedB[p - 1] = pack_norm<CHK>(b);
 }
 
