@@ -187,12 +187,13 @@ int tuned_p(int K) {
 
 thread_local int t_radix_override = -1;
 
-// Entry (g, p, k) of the (K, P) table is step j = kSub g + k of window p of
-// the interleaved pass: natural position q = PI(p W + j) (QPP, Sec. IV-B
-// Fig. 4's interleaver) and its transposed shared-memory index
-// (q mod W) P + q / W, laid out as the decoder reads them (one 16-byte group
-// of kSub addresses per window, windows adjacent); steps past a window's end
-// and the two extra last groups are zero.
+// Tables of CB size K with P windows.  Entry (g, p, k) of the first is step
+// j = kSub g + k of window p of the interleaved pass: natural position q =
+// PI(p W + j) (QPP, Sec. IV-B Fig. 4's interleaver) and its transposed
+// shared-memory index (q mod W) P + q / W, laid out as the decoder reads
+// them (one 16-byte group of kSub addresses per window, windows adjacent);
+// steps past a window's end and the two extra last groups are zero.  The
+// de-rate-matching map follows (below).
 const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
   QTabs* qs = ctx->qtabs;
   const int ki = lte::index_of(K);
@@ -205,7 +206,9 @@ const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
   const int W = (K + P - 1) / P;
   if ((K + W - 1) / W != P) return nullptr;
   const int ng = (W + kSub - 1) / kSub + 2;
-  const size_t tb = (size_t)ng * P * 16, bytes = tb + (size_t)ng * P * 8;
+  const int R = lte::rows(K), KPI = 32 * R, ND = KPI - (K + 4), Nv = 3 * (K + 4), tp = W * P;
+  const size_t tb = (size_t)ng * P * 16, qb = (size_t)ng * P * 8;
+  const size_t bytes = tb + qb + (size_t)Nv * 4;
   const size_t need = al256(bytes);
   if (qs->left < need) {
     const size_t sz = std::max(need, (size_t)8 << 20);
@@ -221,6 +224,7 @@ const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
   std::vector<uint8_t> h(bytes, 0);
   uint32_t* ht = (uint32_t*)h.data();
   uint16_t* hq = (uint16_t*)(h.data() + tb);
+  uint32_t* hd = (uint32_t*)(h.data() + tb + qb);
   const int64_t f1 = lte::kF1[ki], f2 = lte::kF2[ki];
   for (int p = 0; p < P; p++) {
     const int lo = p * W, len = std::min(W, K - lo);
@@ -232,6 +236,34 @@ const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
       hq[e] = (uint16_t)q;
     }
   }
+  // de-rate-matching map (no filler bits): the circular buffer w = [v0,
+  // interlace(v1, v2)] of TS 36.212 5.1.4.1 walked in order; the r-th
+  // non-NULL position p gets (p << 16) | destination, the destination being
+  // stream s, bit y - ND of its sub-block interleaver input (y the padded
+  // index, NULL when y < ND), stored at s tp + transposed index, or, for the
+  // four tail bits of each stream, 3 tp + 3 (y - ND - K) + s.
+  int nv = 0;
+  auto put = [&](int p, int s, int y) {
+    if (y < ND) return;  // dummy bit: NULL
+    const int di = y - ND;
+    const int dst = di < K ? s * tp + (di % W) * P + di / W : 3 * tp + 3 * (di - K) + s;
+    hd[nv++] = ((uint32_t)p << 16) | (uint32_t)dst;
+  };
+  for (int c = 0; c < 32; c++) {
+    int pc = 0;
+    for (int b = 0; b < 5; b++) pc |= ((c >> b) & 1) << (4 - b);
+    for (int i = 0; i < R; i++) put(c * R + i, 0, pc + 32 * i);
+  }
+  for (int c = 0; c < 32; c++) {
+    int pc = 0;
+    for (int b = 0; b < 5; b++) pc |= ((c >> b) & 1) << (4 - b);
+    for (int i = 0; i < R; i++) {
+      const int p = KPI + 2 * (c * R + i);
+      put(p, 1, pc + 32 * i);
+      put(p + 1, 2, (pc + 32 * i + 1) % KPI);
+    }
+  }
+  if (nv != Nv) return nullptr;
   uint8_t* dev = qs->cur;
   if (cudaMemcpyAsync(dev, h.data(), bytes, cudaMemcpyHostToDevice, qs->stream) != cudaSuccess ||
       cudaStreamSynchronize(qs->stream) != cudaSuccess)
@@ -498,6 +530,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     radix4_any |= d.radix4 != 0;
     d.qt = qtab_get(ctx, tm.K, tm.P);
     d.qq = qtab_q(d.qt, tm.K, tm.P);
+    d.dm = F == 0 ? qtab_dm(d.qt, tm.K, tm.P) : nullptr;
     qtab_all &= d.qt != nullptr;
     memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;

@@ -376,8 +376,30 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     return (q - w * W) * P + w;
   };
   int8_t* const streams[3] = {sl.sys, sl.par1, sl.par2};
-  // rows x = unit * R + i, walked with (unit, i) updated incrementally
-  const int nrows = 64 * R;
+  const uint32_t* __restrict__ dm = d.dm;
+  if (dm != nullptr) {
+    // with the (K, P) map (no filler bits): one circular-buffer rank r per
+    // thread and step; the map gives its buffer position (soft buffer) and
+    // its place in the slot (streams at s W P, tail bits after 3 W P).
+    // NULL positions are not visited: no step reads their soft entries.
+    int8_t* const base = sl.sys;
+    const int tp3 = 3 * W * P;
+#pragma unroll 4
+    for (int r = tid; r < Nv; r += nthr) {
+      const uint32_t m = __ldg(dm + r);
+      int k = r - rank0;
+      if (k < 0) k += Nv;
+      const int pos = (int)(m >> 16), dst = (int)(m & 0xFFFFu);
+      int acc = combine ? soft[pos] : 0;
+      for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
+      const int8_t v = (int8_t)acc;
+      if (dst < tp3) base[dst] = v;
+      else sl.tail[dst - tp3] = v;
+      if (soft) soft[pos] = v;
+    }
+  }
+  // otherwise rows x = unit * R + i, walked with (unit, i) updated incrementally
+  const int nrows = dm != nullptr ? 0 : 64 * R;
   int unit = tid / R, i = tid - (tid / R) * R;
   const int du = nthr / R, di_ = nthr - du * R;
   for (int x = tid; x < nrows; x += nthr) {

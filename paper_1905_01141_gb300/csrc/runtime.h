@@ -173,6 +173,12 @@ inline const uint2* qtab_q(const uint4* t, int K, int P) {
   const int W = (K + P - 1) / P;
   return t ? (const uint2*)(t + (size_t)((W + kSub - 1) / kSub + 2) * P) : nullptr;
 }
+// The de-rate-matching map that follows it (CbDesc::dm; CBs without filler bits).
+inline const uint32_t* qtab_dm(const uint4* t, int K, int P) {
+  const int W = (K + P - 1) / P;
+  return t ? (const uint32_t*)(qtab_q(t, K, P) + (size_t)((W + kSub - 1) / kSub + 2) * P)
+           : nullptr;
+}
 // 1 if the radix table selects the radix-4 forward recursion for CB size K.
 // t_radix_override >= 0 replaces the table for plans built on this thread
 // (the autotuner's candidates).
