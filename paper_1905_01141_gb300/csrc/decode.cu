@@ -384,7 +384,7 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     // NULL positions are not visited: no step reads their soft entries.
     int8_t* const base = sl.sys;
     const int tp3 = 3 * W * P;
-#pragma unroll 4
+#pragma unroll 8
     for (int r = tid; r < Nv; r += nthr) {
       const uint32_t m = __ldg(dm + r);
       int k = r - rank0;
