@@ -187,67 +187,24 @@ int tuned_p(int K) {
 
 thread_local int t_radix_override = -1;
 
-// Tables of CB size K with P windows.  Entry (g, p, k) of the first is step
-// j = kSub g + k of window p of the interleaved pass: natural position q =
-// PI(p W + j) (QPP, Sec. IV-B Fig. 4's interleaver) and its transposed
-// shared-memory index (q mod W) P + q / W, laid out as the decoder reads
-// them (one 16-byte group of kSub addresses per window, windows adjacent);
-// steps past a window's end and the two extra last groups are zero.  The
-// de-rate-matching map follows (below).
-const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
-  QTabs* qs = ctx->qtabs;
-  const int ki = lte::index_of(K);
-  if (!qs || ki < 0 || P < 1 || P > (int)CRNT_MAX_P) return nullptr;
-  const uint4* r = qs->t[ki][P].load(std::memory_order_acquire);
-  if (r) return r;
-  std::lock_guard<std::mutex> lk(qs->mu);
-  r = qs->t[ki][P].load(std::memory_order_relaxed);
-  if (r) return r;
-  const int W = (K + P - 1) / P;
-  if ((K + W - 1) / W != P) return nullptr;
-  const int ng = (W + kSub - 1) / kSub + 2;
-  const int R = lte::rows(K), KPI = 32 * R, ND = KPI - (K + 4), Nv = 3 * (K + 4), tp = W * P;
-  const size_t tb = (size_t)ng * P * 16, qb = (size_t)ng * P * 8;
-  const size_t bytes = tb + qb + (size_t)Nv * 4;
-  const size_t need = al256(bytes);
-  if (qs->left < need) {
-    const size_t sz = std::max(need, (size_t)8 << 20);
-    void* p = nullptr;
-    if (cudaMalloc(&p, sz) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    qs->chunks.push_back(p);
-    qs->cur = (uint8_t*)p;
-    qs->left = sz;
-  }
-  std::vector<uint8_t> h(bytes, 0);
-  uint32_t* ht = (uint32_t*)h.data();
-  uint16_t* hq = (uint16_t*)(h.data() + tb);
-  uint32_t* hd = (uint32_t*)(h.data() + tb + qb);
-  const int64_t f1 = lte::kF1[ki], f2 = lte::kF2[ki];
-  for (int p = 0; p < P; p++) {
-    const int lo = p * W, len = std::min(W, K - lo);
-    for (int j = 0; j < len; j++) {
-      const int64_t i = lo + j;
-      const int q = (int)((f1 * i + (f2 * i % K) * i) % K);
-      const size_t e = ((size_t)(j / kSub) * P + p) * kSub + j % kSub;
-      ht[e] = (uint32_t)((q % W) * P + q / W);
-      hq[e] = (uint16_t)q;
-    }
-  }
-  // de-rate-matching map (no filler bits): the circular buffer w = [v0,
-  // interlace(v1, v2)] of TS 36.212 5.1.4.1 walked in order; the r-th
-  // non-NULL position p gets (p << 16) | destination, the destination being
-  // stream s, bit y - ND of its sub-block interleaver input (y the padded
-  // index, NULL when y < ND), stored at s tp + transposed index, or, for the
-  // four tail bits of each stream, 3 tp + 3 (y - ND - K) + s.
+// De-rate-matching map of CB size K with P windows and F filler bits: the
+// circular buffer w = [v0, interlace(v1, v2)] of TS 36.212 5.1.4.1 walked in
+// order; the r-th non-NULL position p gets (p << 16) | destination, the
+// destination being stream s, bit y - ND of its sub-block interleaver input
+// (y the padded index; NULL when y < ND, a dummy, or, in streams 0 and 1,
+// when y < ND + F, a filler bit), stored at s tp + transposed index, or, for
+// the four tail bits of each stream, 3 tp + 3 (y - ND - K) + s.  Returns the
+// number of non-NULL positions (entries written: at most n).
+static int build_dm(uint32_t* hd, int n, int K, int P, int F) {
+  const int W = (K + P - 1) / P, tp = W * P;
+  const int R = lte::rows(K), KPI = 32 * R, ND = KPI - (K + 4);
   int nv = 0;
   auto put = [&](int p, int s, int y) {
-    if (y < ND) return;  // dummy bit: NULL
+    if (y < ND || (s < 2 && y < ND + F)) return;  // NULL
     const int di = y - ND;
     const int dst = di < K ? s * tp + (di % W) * P + di / W : 3 * tp + 3 * (di - K) + s;
-    hd[nv++] = ((uint32_t)p << 16) | (uint32_t)dst;
+    if (nv < n) hd[nv] = ((uint32_t)p << 16) | (uint32_t)dst;
+    nv++;
   };
   for (int c = 0; c < 32; c++) {
     int pc = 0;
@@ -263,15 +220,94 @@ const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
       put(p + 1, 2, (pc + 32 * i + 1) % KPI);
     }
   }
-  if (nv != Nv) return nullptr;
+  return nv;
+}
+
+// Copies h (bytes) into the tables' device memory (caller holds qs->mu).
+static const uint8_t* qt_upload(QTabs* qs, const void* h, size_t bytes) {
+  const size_t need = al256(bytes);
+  if (qs->left < need) {
+    const size_t sz = std::max(need, (size_t)8 << 20);
+    void* p = nullptr;
+    if (cudaMalloc(&p, sz) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    qs->chunks.push_back(p);
+    qs->cur = (uint8_t*)p;
+    qs->left = sz;
+  }
   uint8_t* dev = qs->cur;
-  if (cudaMemcpyAsync(dev, h.data(), bytes, cudaMemcpyHostToDevice, qs->stream) != cudaSuccess ||
+  if (cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, qs->stream) != cudaSuccess ||
       cudaStreamSynchronize(qs->stream) != cudaSuccess)
     return nullptr;
   qs->cur += need;
   qs->left -= need;
-  r = (const uint4*)dev;
-  qs->t[ki][P].store(r, std::memory_order_release);
+  return dev;
+}
+
+// Tables of CB size K with P windows.  Entry (g, p, k) of the first is step
+// j = kSub g + k of window p of the interleaved pass: natural position q =
+// PI(p W + j) (QPP, Sec. IV-B Fig. 4's interleaver) and its transposed
+// shared-memory index (q mod W) P + q / W, laid out as the decoder reads
+// them (one 16-byte group of kSub addresses per window, windows adjacent);
+// steps past a window's end and the two extra last groups are zero.  The
+// de-rate-matching map without filler bits follows.
+const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
+  QTabs* qs = ctx->qtabs;
+  const int ki = lte::index_of(K);
+  if (!qs || ki < 0 || P < 1 || P > (int)CRNT_MAX_P) return nullptr;
+  const uint4* r = qs->t[ki][P].load(std::memory_order_acquire);
+  if (r) return r;
+  std::lock_guard<std::mutex> lk(qs->mu);
+  r = qs->t[ki][P].load(std::memory_order_relaxed);
+  if (r) return r;
+  const int W = (K + P - 1) / P;
+  if ((K + W - 1) / W != P) return nullptr;
+  const int ng = (W + kSub - 1) / kSub + 2, Nv = 3 * (K + 4);
+  const size_t tb = (size_t)ng * P * 16, qb = (size_t)ng * P * 8;
+  const size_t bytes = tb + qb + (size_t)Nv * 4;
+  std::vector<uint8_t> h(bytes, 0);
+  uint32_t* ht = (uint32_t*)h.data();
+  uint16_t* hq = (uint16_t*)(h.data() + tb);
+  const int64_t f1 = lte::kF1[ki], f2 = lte::kF2[ki];
+  for (int p = 0; p < P; p++) {
+    const int lo = p * W, len = std::min(W, K - lo);
+    for (int j = 0; j < len; j++) {
+      const int64_t i = lo + j;
+      const int q = (int)((f1 * i + (f2 * i % K) * i) % K);
+      const size_t e = ((size_t)(j / kSub) * P + p) * kSub + j % kSub;
+      ht[e] = (uint32_t)((q % W) * P + q / W);
+      hq[e] = (uint16_t)q;
+    }
+  }
+  if (build_dm((uint32_t*)(h.data() + tb + qb), Nv, K, P, 0) != Nv) return nullptr;
+  r = (const uint4*)qt_upload(qs, h.data(), bytes);
+  if (r) qs->t[ki][P].store(r, std::memory_order_release);
+  return r;
+}
+
+// The de-rate-matching map of (K, P, F) (F, a multiple of 8 below 64 by the
+// segmentation of TS 36.212 5.1.2, only on a TB's first CB): the one after
+// the (K, P) tables for F = 0, else its own, built on first use.
+const uint32_t* dmap_get(crnt_ctx* ctx, int K, int P, int F) {
+  const uint4* t = qtab_get(ctx, K, P);
+  if (!t) return nullptr;
+  if (F == 0) return qtab_dm(t, K, P);
+  QTabs* qs = ctx->qtabs;
+  const int ki = lte::index_of(K), f = F >> 3;
+  if ((F & 7) || f < 1 || f > QTabs::kFill) return nullptr;
+  std::atomic<const uint32_t*>& slot = qs->dmf[(ki * (CRNT_MAX_P + 1) + P) * QTabs::kFill + f - 1];
+  const uint32_t* r = slot.load(std::memory_order_acquire);
+  if (r) return r;
+  std::lock_guard<std::mutex> lk(qs->mu);
+  r = slot.load(std::memory_order_relaxed);
+  if (r) return r;
+  const int Nv = 3 * (K + 4) - 2 * F;
+  std::vector<uint32_t> h((size_t)Nv);
+  if (build_dm(h.data(), Nv, K, P, F) != Nv) return nullptr;
+  r = (const uint32_t*)qt_upload(qs, h.data(), (size_t)Nv * 4);
+  if (r) slot.store(r, std::memory_order_release);
   return r;
 }
 
@@ -530,7 +566,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     radix4_any |= d.radix4 != 0;
     d.qt = qtab_get(ctx, tm.K, tm.P);
     d.qq = qtab_q(d.qt, tm.K, tm.P);
-    d.dm = F == 0 ? qtab_dm(d.qt, tm.K, tm.P) : nullptr;
+    d.dm = dmap_get(ctx, tm.K, tm.P, F);
     qtab_all &= d.qt != nullptr;
     memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;

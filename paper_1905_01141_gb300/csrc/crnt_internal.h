@@ -50,7 +50,7 @@ struct CbDesc {
                            // [ceil(W/kSub) + 2 groups][P windows] x kSub
                            // transposed addresses (the last two groups zero)
   const uint2* qq;         // the same steps' natural positions (uint16, same order)
-  const uint32_t* dm;      // de-rate-matching map of (K, P) without filler, or null:
+  const uint32_t* dm;      // de-rate-matching map of (K, P, F), or null:
                            // per circular-buffer rank r < Nv, (position << 16) |
                            // destination (stream s: s W P + transposed index;
                            // tail bit: 3 W P + 3 (d - K) + s)

@@ -378,10 +378,11 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
   int8_t* const streams[3] = {sl.sys, sl.par1, sl.par2};
   const uint32_t* __restrict__ dm = d.dm;
   if (dm != nullptr) {
-    // with the (K, P) map (no filler bits): one circular-buffer rank r per
-    // thread and step; the map gives its buffer position (soft buffer) and
-    // its place in the slot (streams at s W P, tail bits after 3 W P).
-    // NULL positions are not visited: no step reads their soft entries.
+    // with the (K, P, F) map: one circular-buffer rank r per thread and
+    // step; the map gives its buffer position (soft buffer) and its place in
+    // the slot (streams at s W P, tail bits after 3 W P).  NULL positions
+    // (dummies, filler bits) are not visited: no step reads their soft
+    // entries, and the filler loop below fills the filler places.
     int8_t* const base = sl.sys;
     const int tp3 = 3 * W * P;
 #pragma unroll 8
