@@ -149,6 +149,19 @@ int crnt_qpp_params(uint32_t K, uint32_t* f1, uint32_t* f2);
  * as described at crnt_tb_params; CRNT_EINVAL otherwise. */
 int crnt_tb_layout(const crnt_tb_params* tb, crnt_cb_layout* cbs, uint32_t* C);
 
+/* De-rate-matching map of a CB of size K with F filler bits split into P
+ * windows (P clamped like crnt_tb_params::P; 0 = the window table's), the
+ * map the decoder reads (TS 36.212 5.1.4.1 circular buffer): entry k, for
+ * k < Nv = 3 (K + 4) - 2 F, describes where the k-th received LLR of
+ * redundancy version rv lands (the k-th non-NULL buffer position from k0;
+ * with E > Nv LLR k + Nv lands there too).  Bits 0..15: its place in the
+ * CB's shared-memory slot -- for bit d < K of stream s, s W P + (d mod W) P
+ * + d / W with W = ceil(K / P); for tail bit d >= K, 3 W P + 3 (d - K) + s;
+ * bits 16..31: its circular-buffer position.  Host-side query (no GPU).
+ * CRNT_EINVAL for an unknown K, rv > 3, F not a multiple of 8 below 64, a
+ * null map or n < Nv. */
+int crnt_derm_map(uint32_t K, uint32_t P, uint32_t F, uint32_t rv, uint32_t* map, uint32_t n);
+
 /* ---- window-count table (autotuner) ----------------------------------- */
 /* A TB that asks for P = 0 gets, for each CB size K, the window count of a
  * process-wide table shared by every context: entry i holds P for the i-th

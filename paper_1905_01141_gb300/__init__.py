@@ -86,6 +86,7 @@ SIGNATURES = {
     "crnt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "crnt_qpp_params": (ctypes.c_int, [_U32, _P, _P]),
     "crnt_tb_layout": (ctypes.c_int, [_P, _P, _P]),
+    "crnt_derm_map": (ctypes.c_int, [_U32, _U32, _U32, _U32, _P, _U32]),
     "crnt_create": (ctypes.c_int, [_P, _P]),
     "crnt_destroy": (ctypes.c_int, [_P]),
     "crnt_plan_create": (ctypes.c_int, [_P, _P, _U32, _P]),
@@ -189,6 +190,14 @@ def tb_layout(tb):
     _check(load().crnt_tb_layout(ctypes.byref(t), cbs, ctypes.byref(C)), "crnt_tb_layout")
     keys = [f[0] for f in CbLayout._fields_]
     return [{k: getattr(cbs[r], k) for k in keys} for r in range(C.value)]
+
+
+def derm_map(K, P, F, rv):
+    """crnt_derm_map: where each received LLR of a CB lands (uint32 array)."""
+    n = 3 * (K + 4) - 2 * F
+    m = (ctypes.c_uint32 * n)()
+    _check(load().crnt_derm_map(K, P, F, rv, m, n), "crnt_derm_map")
+    return list(m)
 
 
 NUM_K = 188

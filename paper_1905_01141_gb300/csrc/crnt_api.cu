@@ -741,6 +741,22 @@ int crnt_qpp_params(uint32_t K, uint32_t* f1, uint32_t* f2) {
   return CRNT_OK;
 }
 
+int crnt_derm_map(uint32_t K, uint32_t P, uint32_t F, uint32_t rv, uint32_t* map, uint32_t n) {
+  if (!map || lte::index_of((int)K) < 0 || rv > 3 || (F & 7) || F >= 64 || F >= K)
+    return CRNT_EINVAL;
+  const int Pr = clamp_p((int)K, (int)P), W = ((int)K + Pr - 1) / Pr;
+  const int Pe = ((int)K + W - 1) / W;
+  const int Nv = 3 * ((int)K + 4) - 2 * (int)F;
+  if (n < (uint32_t)Nv) return CRNT_EINVAL;
+  std::vector<uint32_t> h((size_t)Nv);
+  if (build_dm(h.data(), Nv, (int)K, Pe, (int)F) != Nv) return CRNT_EINVAL;
+  uint32_t mb = 0, m2 = 0;
+  rm_masks(32 * lte::rows((int)K) - ((int)K + 4), (int)F, &mb, &m2);
+  const int rank0 = rank_of_k0((int)K, (int)F, (int)rv, mb, m2);
+  for (int k = 0; k < Nv; k++) map[k] = h[(size_t)((k + rank0) % Nv)];
+  return CRNT_OK;
+}
+
 int crnt_tb_layout(const crnt_tb_params* tb, crnt_cb_layout* cbs, uint32_t* C) {
   if (!tb || !cbs || !C) return CRNT_EINVAL;
   lte::Seg s;

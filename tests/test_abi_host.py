@@ -140,3 +140,38 @@ def test_radix_table_get_set(crnt_lib):
         assert crnt_lib.load().crnt_tune_radix_get(None, 188) == crnt_lib.EINVAL
     finally:
         crnt_lib.tune_radix_set(old)
+
+
+@pytest.mark.parametrize("K,F,P,rv", [(40, 0, 1, 0), (40, 8, 5, 1), (512, 24, 9, 2),
+                                      (1024, 0, 21, 3), (5824, 16, 121, 1),
+                                      (6144, 0, 128, 0), (6144, 56, 128, 3), (2112, 40, 7, 2)])
+def test_derm_map_matches_oracle_rate_matching(orc, crnt_lib, K, F, P, rv):
+    # the decoder's de-rate-matching map against the oracle's circular buffer:
+    # with one distinct LLR per non-NULL position (E = Nv), each received LLR k
+    # must land exactly where the map says, and the map must cover every
+    # non-NULL bit of the three streams once (filler bits of streams 0 and 1
+    # excepted)
+    Nv = 3 * (K + 4) - 2 * F
+    rng = np.random.default_rng(K * 131 + F * 7 + rv)
+    e = rng.integers(-127, 128, Nv).astype(np.int8)
+    d = orc.derm_cb(e, K, F, rv)[:3]
+    m = np.array(crnt_lib.derm_map(K, P, F, rv), dtype=np.int64)
+    assert len(m) == Nv
+    Pr = max(1, min(P, K // 8, 128))
+    W = -(-K // Pr)
+    Pe = -(-K // W)
+    tp = W * Pe
+    dst, pos = m & 0xFFFF, m >> 16
+    tail = dst >= 3 * tp
+    s = np.where(tail, (dst - 3 * tp) % 3, dst // tp)
+    t = dst % tp
+    di = np.where(tail, K + (dst - 3 * tp) // 3, (t % Pe) * W + t // Pe)
+    got = np.array([d[si][x] for si, x in zip(s, di)], dtype=np.int8)
+    assert np.array_equal(got, e)
+    hit = set(zip(s.tolist(), di.tolist()))
+    assert len(hit) == Nv
+    want = {(si, x) for si in range(3) for x in range(K + 4) if not (si < 2 and x < F)}
+    assert hit == want
+    assert len(set(pos.tolist())) == Nv and pos.max() < 96 * ((K + 4 + 31) // 32)
+    with pytest.raises(crnt_lib.CrntError):
+        crnt_lib.derm_map(K, P, F + 4, rv)
