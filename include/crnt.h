@@ -149,6 +149,15 @@ int crnt_qpp_params(uint32_t K, uint32_t* f1, uint32_t* f2);
  * as described at crnt_tb_params; CRNT_EINVAL otherwise. */
 int crnt_tb_layout(const crnt_tb_params* tb, crnt_cb_layout* cbs, uint32_t* C);
 
+/* Interleaved-pass addresses of a CB of size K split into P windows (P
+ * clamped like crnt_tb_params::P; 0 = the window table's), as the decoder
+ * reads them: entry p W + j (window p, step j, W = ceil(K / P)) holds, for
+ * j < the window's length, q = PI(p W + j) (the QPP interleaver, TS 36.212
+ * 5.1.3.2.3) in bits 16..31 and its transposed shared-memory index
+ * (q mod W) P + q / W in bits 0..15; 0 past a window's end.  Host-side query
+ * (no GPU).  CRNT_EINVAL for an unknown K, a null map or n < W P. */
+int crnt_interleaver_map(uint32_t K, uint32_t P, uint32_t* map, uint32_t n);
+
 /* De-rate-matching map of a CB of size K with F filler bits split into P
  * windows (P clamped like crnt_tb_params::P; 0 = the window table's), the
  * map the decoder reads (TS 36.212 5.1.4.1 circular buffer): entry k, for

@@ -87,6 +87,7 @@ SIGNATURES = {
     "crnt_qpp_params": (ctypes.c_int, [_U32, _P, _P]),
     "crnt_tb_layout": (ctypes.c_int, [_P, _P, _P]),
     "crnt_derm_map": (ctypes.c_int, [_U32, _U32, _U32, _U32, _P, _U32]),
+    "crnt_interleaver_map": (ctypes.c_int, [_U32, _U32, _P, _U32]),
     "crnt_create": (ctypes.c_int, [_P, _P]),
     "crnt_destroy": (ctypes.c_int, [_P]),
     "crnt_plan_create": (ctypes.c_int, [_P, _P, _U32, _P]),
@@ -190,6 +191,14 @@ def tb_layout(tb):
     _check(load().crnt_tb_layout(ctypes.byref(t), cbs, ctypes.byref(C)), "crnt_tb_layout")
     keys = [f[0] for f in CbLayout._fields_]
     return [{k: getattr(cbs[r], k) for k in keys} for r in range(C.value)]
+
+
+def interleaver_map(K, P):
+    """crnt_interleaver_map: per (window, step) the QPP position and its transposed index."""
+    n = K + 128  # >= W * P for every clamped P
+    m = (ctypes.c_uint32 * n)()
+    _check(load().crnt_interleaver_map(K, P, m, n), "crnt_interleaver_map")
+    return list(m)
 
 
 def derm_map(K, P, F, rv):

@@ -223,6 +223,24 @@ static int build_dm(uint32_t* hd, int n, int K, int P, int F) {
   return nv;
 }
 
+// Interleaved-pass address table of CB size K with P windows (layout of
+// CbDesc::qt / qq): entry (g, p, k), step j = kSub g + k of window p, holds
+// the transposed index of q = PI(p W + j) in ht and q in hq.  ki: K's index.
+static void build_qt(uint32_t* ht, uint16_t* hq, int ki, int K, int P) {
+  const int W = (K + P - 1) / P;
+  const int64_t f1 = lte::kF1[ki], f2 = lte::kF2[ki];
+  for (int p = 0; p < P; p++) {
+    const int lo = p * W, len = std::min(W, K - lo);
+    for (int j = 0; j < len; j++) {
+      const int64_t i = lo + j;
+      const int q = (int)((f1 * i + (f2 * i % K) * i) % K);
+      const size_t e = ((size_t)(j / kSub) * P + p) * kSub + j % kSub;
+      ht[e] = (uint32_t)((q % W) * P + q / W);
+      hq[e] = (uint16_t)q;
+    }
+  }
+}
+
 // Copies h (bytes) into the tables' device memory (caller holds qs->mu).
 static const uint8_t* qt_upload(QTabs* qs, const void* h, size_t bytes) {
   const size_t need = al256(bytes);
@@ -268,19 +286,7 @@ const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
   const size_t tb = (size_t)ng * P * 16, qb = (size_t)ng * P * 8;
   const size_t bytes = tb + qb + (size_t)Nv * 4;
   std::vector<uint8_t> h(bytes, 0);
-  uint32_t* ht = (uint32_t*)h.data();
-  uint16_t* hq = (uint16_t*)(h.data() + tb);
-  const int64_t f1 = lte::kF1[ki], f2 = lte::kF2[ki];
-  for (int p = 0; p < P; p++) {
-    const int lo = p * W, len = std::min(W, K - lo);
-    for (int j = 0; j < len; j++) {
-      const int64_t i = lo + j;
-      const int q = (int)((f1 * i + (f2 * i % K) * i) % K);
-      const size_t e = ((size_t)(j / kSub) * P + p) * kSub + j % kSub;
-      ht[e] = (uint32_t)((q % W) * P + q / W);
-      hq[e] = (uint16_t)q;
-    }
-  }
+  build_qt((uint32_t*)h.data(), (uint16_t*)(h.data() + tb), ki, K, P);
   if (build_dm((uint32_t*)(h.data() + tb + qb), Nv, K, P, 0) != Nv) return nullptr;
   r = (const uint4*)qt_upload(qs, h.data(), bytes);
   if (r) qs->t[ki][P].store(r, std::memory_order_release);
@@ -738,6 +744,23 @@ int crnt_qpp_params(uint32_t K, uint32_t* f1, uint32_t* f2) {
   if (i < 0 || !f1 || !f2) return CRNT_EINVAL;
   *f1 = lte::kF1[i];
   *f2 = lte::kF2[i];
+  return CRNT_OK;
+}
+
+int crnt_interleaver_map(uint32_t K, uint32_t P, uint32_t* map, uint32_t n) {
+  const int ki = lte::index_of((int)K);
+  if (!map || ki < 0) return CRNT_EINVAL;
+  const int Pr = clamp_p((int)K, (int)P), W = ((int)K + Pr - 1) / Pr;
+  const int Pe = ((int)K + W - 1) / W, ng = (W + kSub - 1) / kSub;
+  if (n < (uint32_t)(W * Pe)) return CRNT_EINVAL;
+  std::vector<uint32_t> ht((size_t)ng * Pe * kSub, 0u);
+  std::vector<uint16_t> hq(ht.size(), 0);
+  build_qt(ht.data(), hq.data(), ki, (int)K, Pe);
+  for (int p = 0; p < Pe; p++)
+    for (int j = 0; j < W; j++) {
+      const size_t e = ((size_t)(j / kSub) * Pe + p) * kSub + j % kSub;
+      map[(size_t)p * W + j] = ((uint32_t)hq[e] << 16) | ht[e];
+    }
   return CRNT_OK;
 }
 

@@ -175,3 +175,23 @@ def test_derm_map_matches_oracle_rate_matching(orc, crnt_lib, K, F, P, rv):
     assert len(set(pos.tolist())) == Nv and pos.max() < 96 * ((K + 4 + 31) // 32)
     with pytest.raises(crnt_lib.CrntError):
         crnt_lib.derm_map(K, P, F + 4, rv)
+
+
+@pytest.mark.parametrize("K,P", [(40, 1), (40, 5), (512, 9), (1024, 21), (2112, 7),
+                                 (5824, 121), (6144, 128), (6144, 100)])
+def test_interleaver_map_matches_oracle_qpp(orc, crnt_lib, K, P):
+    # the decoder's interleaved-pass address table against the oracle's QPP
+    # permutation: step j of window p reads natural position PI(p W + j),
+    # stored at its transposed shared-memory index
+    pi = np.asarray(orc.qpp(K), dtype=np.int64)
+    m = np.array(crnt_lib.interleaver_map(K, P), dtype=np.int64)
+    Pr = max(1, min(P, K // 8, 128))
+    W = -(-K // Pr)
+    Pe = -(-K // W)
+    m = m[:W * Pe].reshape(Pe, W)
+    for p in range(Pe):
+        n = min(W, K - p * W)
+        q, t = m[p, :n] >> 16, m[p, :n] & 0xFFFF
+        assert np.array_equal(q, pi[p * W:p * W + n]), p
+        assert np.array_equal(t, (q % W) * Pe + q // W), p
+        assert not m[p, n:].any()
