@@ -242,11 +242,12 @@ int crnt_plan_destroy(crnt_plan* plan);
 
 /* Blocking decode of n TBs.  llr: concatenated G LLRs of every TB (host or
  * device); out: concatenated A/8 bytes (host or device); res: n results
- * (host).  Device buffers and page-locked host buffers (cudaHostAlloc,
- * cudaHostRegister) are read and written in place by the kernels (host ones
- * over the CPU-GPU link); pageable host buffers are staged through the
- * context's device arena.  Batches of 24 or more TBs are decoded as three
- * chunks whose planning and copies overlap the decoding of earlier chunks. */
+ * (host).  Device buffers are used in place; host LLRs are copied into the
+ * context's device arena (page-locked ones by DMA); a page-locked host out
+ * (cudaHostAlloc, cudaHostRegister) is written in place by the kernels over
+ * the CPU-GPU link, a pageable one staged.  Batches of 24 or more TBs are
+ * decoded as three chunks whose planning and copies overlap the decoding of
+ * earlier chunks. */
 int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, const int8_t* llr,
                       uint8_t* out, crnt_tb_result* res);
 /* Blocking decode of one TB (n = 1 of the above). */

@@ -90,6 +90,15 @@ bool find_divider(int W, int qmax, int* M, int* s) {
 // page-locked host memory (cudaHostAlloc / cudaHostRegister) through its
 // mapped device address -- kernels then read and write it in place over the
 // CPU-GPU link; nullptr for pageable host memory, which must be staged.
+// host_memory: p is page-locked or pageable host memory.
+bool host_memory(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown to CUDA: pageable
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
 void* device_view(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -952,8 +961,12 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
                       uint8_t* out, crnt_tb_result* res) {
   if (!ctx || !tbs || !llr || !out || !res || n == 0) return CRNT_EINVAL;
   cudaSetDevice(ctx->device);
-  // device or page-locked buffers are used in place; pageable ones staged
-  const int8_t* llr_view = (const int8_t*)device_view(llr);
+  // device buffers are used in place; host LLRs are copied into the arena
+  // (page-locked ones by DMA at the link's rate, which beat the kernels
+  // reading them in place over the link); page-locked output is written in
+  // place, pageable output staged
+  const bool llr_host = host_memory(llr);
+  const int8_t* llr_view = llr_host ? nullptr : (const int8_t*)device_view(llr);
   uint8_t* out_view = (uint8_t*)device_view(out);
   const bool llr_dev = llr_view != nullptr, out_dev = out_view != nullptr;
   std::lock_guard<std::mutex> lk(ctx->stage_mu);
