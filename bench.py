@@ -377,10 +377,10 @@ def run_ours(args):
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
         tt = None if args.no_autotune else crnt.tune_get() + crnt.tune_radix_get()
         line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
-        line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 44, 48, 52),
+        line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 48, 56, 64, 72),
                                             tune_table=tt, purge=True)
         line["serving_poisson"] = serving_leg(crnt, dev, args.seed,
-                                              cells_list=(24, 32, 36, 40, 44, 48),
+                                              cells_list=(24, 32, 40, 48, 56, 64, 72),
                                               tune_table=tt, poisson=True)
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
         line["radix4_forward"] = radix_leg(crnt, ctx, tbs, llr_d, flush, dev)
@@ -501,7 +501,8 @@ def subframe_latency(crnt, ctx, dev):
     return out
 
 
-def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 28, 32, 36, 40, 44, 48, 56, 64),
+def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 44, 48, 52, 56, 64, 72, 80,
+                                              96),
                 seconds=1.5, tune_table=None, purge=False, poisson=False):
     """Serving loop under cell load, driven by the native open-loop load
     generator (crnt_loadgen, a client of crnt_submit / crnt_poll): every cell

@@ -203,16 +203,31 @@ thread_local int t_radix_override = -1;
 // (y the padded index; NULL when y < ND, a dummy, or, in streams 0 and 1,
 // when y < ND + F, a filler bit), stored at s tp + transposed index, or, for
 // the four tail bits of each stream, 3 tp + 3 (y - ND - K) + s.  Returns the
-// number of non-NULL positions (entries written: at most n).
-static int build_dm(uint32_t* hd, int n, int K, int P, int F) {
+// number of non-NULL positions (entries written: at most n).  fkey (may be
+// null, n entries): per entry, the bit index y - ND where a filler count
+// above it would make the position NULL (streams 0 and 1, bits below 64),
+// else 64 -- the map of F > 0 is the F = 0 map without the entries whose key
+// is below F.
+static int build_dm(uint32_t* hd, uint8_t* fkey, int n, int K, int P, int F) {
   const int W = (K + P - 1) / P, tp = W * P;
   const int R = lte::rows(K), KPI = 32 * R, ND = KPI - (K + 4);
+  std::vector<uint32_t> tr((size_t)K);  // transposed index of bit d, by walking
+  for (int d = 0, r = 0, c = 0; d < K; d++) {
+    tr[(size_t)d] = (uint32_t)(r * P + c);
+    if (++r == W) {
+      r = 0;
+      c++;
+    }
+  }
   int nv = 0;
   auto put = [&](int p, int s, int y) {
     if (y < ND || (s < 2 && y < ND + F)) return;  // NULL
     const int di = y - ND;
-    const int dst = di < K ? s * tp + (di % W) * P + di / W : 3 * tp + 3 * (di - K) + s;
-    if (nv < n) hd[nv] = ((uint32_t)p << 16) | (uint32_t)dst;
+    const int dst = di < K ? s * tp + (int)tr[(size_t)di] : 3 * tp + 3 * (di - K) + s;
+    if (nv < n) {
+      hd[nv] = ((uint32_t)p << 16) | (uint32_t)dst;
+      if (fkey) fkey[nv] = (uint8_t)(s < 2 && di < 64 ? di : 64);
+    }
     nv++;
   };
   for (int c = 0; c < 32; c++) {
@@ -230,6 +245,15 @@ static int build_dm(uint32_t* hd, int n, int K, int P, int F) {
     }
   }
   return nv;
+}
+
+// Byte offset of the (K, P, F) de-rate-matching map inside the (K, P) entry
+// (after the address tables; maps for F = 0, 8, ..., 56 in turn).
+static size_t dm_offset(int K, int P, int F) {
+  const int W = (K + P - 1) / P, ng = (W + kSub - 1) / kSub + 2;
+  size_t off = (size_t)ng * P * 24;
+  for (int f = 0; f < F; f += 8) off += (size_t)(3 * (K + 4) - 2 * f) * 4;
+  return off;
 }
 
 // Interleaved-pass address table of CB size K with P windows (layout of
@@ -292,38 +316,38 @@ const uint4* qtab_get(crnt_ctx* ctx, int K, int P) {
   const int W = (K + P - 1) / P;
   if ((K + W - 1) / W != P) return nullptr;
   const int ng = (W + kSub - 1) / kSub + 2, Nv = 3 * (K + 4);
-  const size_t tb = (size_t)ng * P * 16, qb = (size_t)ng * P * 8;
-  const size_t bytes = tb + qb + (size_t)Nv * 4;
+  const size_t tb = (size_t)ng * P * 16;
+  const size_t bytes = dm_offset(K, P, 64);
   std::vector<uint8_t> h(bytes, 0);
   build_qt((uint32_t*)h.data(), (uint16_t*)(h.data() + tb), ki, K, P);
-  if (build_dm((uint32_t*)(h.data() + tb + qb), Nv, K, P, 0) != Nv) return nullptr;
+  std::vector<uint8_t> fkey((size_t)Nv);
+  uint32_t* m0 = (uint32_t*)(h.data() + dm_offset(K, P, 0));
+  if (build_dm(m0, fkey.data(), Nv, K, P, 0) != Nv) return nullptr;
+  // filler counts F < K: the F = 0 map without the filler bits (the maps of
+  // F >= K, which no segmentation produces, stay zero and are never used)
+  for (int F = 8; F < 64 && F < K; F += 8) {
+    uint32_t* mf = (uint32_t*)(h.data() + dm_offset(K, P, F));
+    const int nmax = Nv - 2 * F;
+    int nf = 0;
+    for (int r = 0; r < Nv; r++)
+      if (fkey[(size_t)r] >= F) {
+        if (nf < nmax) mf[nf] = m0[r];
+        nf++;
+      }
+    if (nf != nmax) return nullptr;
+  }
   r = (const uint4*)qt_upload(qs, h.data(), bytes);
   if (r) qs->t[ki][P].store(r, std::memory_order_release);
   return r;
 }
 
 // The de-rate-matching map of (K, P, F) (F, a multiple of 8 below 64 by the
-// segmentation of TS 36.212 5.1.2, only on a TB's first CB): the one after
-// the (K, P) tables for F = 0, else its own, built on first use.
+// segmentation of TS 36.212 5.1.2, only on a TB's first CB), stored in the
+// (K, P) entry.
 const uint32_t* dmap_get(crnt_ctx* ctx, int K, int P, int F) {
+  if ((F & 7) || F < 0 || F >= 64 || F >= K) return nullptr;
   const uint4* t = qtab_get(ctx, K, P);
-  if (!t) return nullptr;
-  if (F == 0) return qtab_dm(t, K, P);
-  QTabs* qs = ctx->qtabs;
-  const int ki = lte::index_of(K), f = F >> 3;
-  if ((F & 7) || f < 1 || f > QTabs::kFill) return nullptr;
-  std::atomic<const uint32_t*>& slot = qs->dmf[(ki * (CRNT_MAX_P + 1) + P) * QTabs::kFill + f - 1];
-  const uint32_t* r = slot.load(std::memory_order_acquire);
-  if (r) return r;
-  std::lock_guard<std::mutex> lk(qs->mu);
-  r = slot.load(std::memory_order_relaxed);
-  if (r) return r;
-  const int Nv = 3 * (K + 4) - 2 * F;
-  std::vector<uint32_t> h((size_t)Nv);
-  if (build_dm(h.data(), Nv, K, P, F) != Nv) return nullptr;
-  r = (const uint32_t*)qt_upload(qs, h.data(), (size_t)Nv * 4);
-  if (r) slot.store(r, std::memory_order_release);
-  return r;
+  return t ? (const uint32_t*)((const uint8_t*)t + dm_offset(K, P, F)) : nullptr;
 }
 
 uint8_t radix4_of(int K) {
@@ -781,7 +805,7 @@ int crnt_derm_map(uint32_t K, uint32_t P, uint32_t F, uint32_t rv, uint32_t* map
   const int Nv = 3 * ((int)K + 4) - 2 * (int)F;
   if (n < (uint32_t)Nv) return CRNT_EINVAL;
   std::vector<uint32_t> h((size_t)Nv);
-  if (build_dm(h.data(), Nv, (int)K, Pe, (int)F) != Nv) return CRNT_EINVAL;
+  if (build_dm(h.data(), nullptr, Nv, (int)K, Pe, (int)F) != Nv) return CRNT_EINVAL;
   uint32_t mb = 0, m2 = 0;
   rm_masks(32 * lte::rows((int)K) - ((int)K + 4), (int)F, &mb, &m2);
   const int rank0 = rank_of_k0((int)K, (int)F, (int)rv, mb, m2);

@@ -2,7 +2,7 @@
 // public C ABI only (crnt_submit / crnt_poll).
 //
 // Every cell sends one subframe (its UEs' TBs) per 1 ms period, at a random
-// phase plus uniform jitter, from a native submitter thread that follows the
+// phase plus uniform jitter, from native submitter threads that follow the
 // arrival times; a poller thread collects results.  Latency of a TB = its
 // completion time (the library's t_done_ns, steady clock) minus its
 // scheduled arrival.  A fraction of TBs are HARQ retransmissions of the same
@@ -12,13 +12,14 @@
 // n int64 LLR offsets, then the LLR bytes.  TB u of cell c is entry
 // (c * ues + u) mod n.  Output: one JSON object per cell count on stdout.
 //
-// usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] FILE UES SECONDS RETX_FRACTION SEED
-//                     CELLS...
+// usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--threads T] FILE UES SECONDS
+//                     RETX_FRACTION SEED CELLS...
 // TABLE: a window-count table (188 numbers) installed with crnt_tune_set,
 // optionally followed by a radix table (188 numbers, crnt_tune_radix_set);
 // --purge: every TB asks for purge on failure (CRNT_F_PURGE);
 // --poisson: exponential inter-arrival times of mean 1 ms per cell instead of
-// the 1 ms period with jitter.
+// the 1 ms period with jitter; --threads T: submitter threads, cells dealt
+// round-robin (default 4; each copies its cells' LLRs in crnt_submit).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -60,18 +61,26 @@ struct Point {
 
 Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
                 const std::vector<const int8_t*>& ptr, int ues, int cells, double seconds,
-                double retx, uint64_t seed, uint32_t extra_flags, bool poisson) {
+                double retx, uint64_t seed, uint32_t extra_flags, bool poisson, int nthreads) {
   const int n = (int)par.size();
   uint64_t rs = seed * 1000003ull + (uint64_t)cells;
   std::vector<double> phase(cells);
   for (int c = 0; c < cells; c++) phase[c] = unit(rs) * 1e6;
   std::mutex mu;
-  std::unordered_map<uint64_t, std::pair<int64_t, uint32_t>> pending;  // ticket -> (arrival, A)
+  // ticket -> (arrival, A); results that arrive before their ticket is
+  // registered wait in `early` (ticket -> (done time, status))
+  std::unordered_map<uint64_t, std::pair<int64_t, uint32_t>> pending;
+  std::unordered_map<uint64_t, std::pair<int64_t, int>> early;
   std::vector<double> lat;
-  std::atomic<bool> done_submitting{false};
+  std::atomic<int> submitting{nthreads};
   long n_bits = 0, errors = 0;
   const int64_t t0 = now_ns() + 2000000;
   const int64_t t_end = t0 + (int64_t)(seconds * 1e9);
+  auto record = [&](int64_t arrival, uint32_t A, int64_t done, int status) {
+    if (status != CRNT_OK) errors++;
+    lat.push_back((double)(done - arrival) / 1e3);
+    n_bits += A;
+  };
   // poller
   std::thread poller([&] {
     std::vector<crnt_tb_result> res(4096);
@@ -82,72 +91,86 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
       std::lock_guard<std::mutex> lk(mu);
       for (int i = 0; i < k; i++) {
         auto it = pending.find(res[i].ticket);
-        if (it == pending.end()) continue;
-        if (res[i].status != CRNT_OK) errors++;
-        lat.push_back((double)((int64_t)res[i].t_done_ns - it->second.first) / 1e3);
-        n_bits += it->second.second;
+        if (it == pending.end()) {
+          early[res[i].ticket] = {(int64_t)res[i].t_done_ns, res[i].status};
+          continue;
+        }
+        record(it->second.first, it->second.second, (int64_t)res[i].t_done_ns, res[i].status);
         pending.erase(it);
       }
-      if (done_submitting.load() && pending.empty()) break;
+      if (submitting.load() == 0 && pending.empty() && early.empty()) break;
       if (now_ns() > t_end + 5000000000ll) break;
     }
   });
-  // submitter: arrivals in time order
-  using Ev = std::pair<int64_t, int>;  // (arrival, cell)
-  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> q;
-  std::vector<int> sf(cells, 0);
-  for (int c = 0; c < cells; c++) q.push(Ev{t0 + (int64_t)phase[c], c});
-  std::vector<crnt_tb_params> tb(ues);
-  std::vector<const int8_t*> lp(ues);
-  std::vector<uint64_t> tk(ues);
-  long subframes = 0, refused = 0;
-  while (!q.empty()) {
-    const Ev ev = q.top();
-    q.pop();
-    if (ev.first >= t_end) continue;
-    while (now_ns() < ev.first) {
-    }
-    const int c = ev.second;
-    const int pid = sf[c] % 8;
-    for (int u = 0; u < ues; u++) {
-      const int e = (c * ues + u) % n;
-      tb[u] = par[e];
-      lp[u] = ptr[e];
-      tb[u].cell = (uint32_t)c;
-      tb[u].ue = (uint32_t)u;
-      tb[u].harq_pid = (uint32_t)pid;
-      tb[u].flags = CRNT_F_HARQ | extra_flags;
-      const bool rt = sf[c] >= 8 && unit(rs) < retx;
-      static const uint8_t rv_cycle[4] = {2, 3, 1, 0};
-      tb[u].new_data = rt ? 0 : 1;
-      tb[u].rv = rt ? rv_cycle[(sf[c] / 8) % 4] : 0;
-    }
-    {
-      // tickets are registered before the poller can see their results
-      std::lock_guard<std::mutex> lk(mu);
+  // submitters: thread h serves the cells c with c mod nthreads == h, each
+  // in arrival-time order (several threads, as several fronthaul links
+  // would, so that the host-side copies of the LLRs are not one core's work)
+  std::atomic<long> subframes{0}, refused{0};
+  auto submitter = [&](int h) {
+    uint64_t rh = seed * 7919ull + (uint64_t)cells * 131ull + (uint64_t)h;
+    using Ev = std::pair<int64_t, int>;  // (arrival, cell)
+    std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> q;
+    std::vector<int> sf(cells, 0);
+    for (int c = h; c < cells; c += nthreads) q.push(Ev{t0 + (int64_t)phase[c], c});
+    std::vector<crnt_tb_params> tb(ues);
+    std::vector<const int8_t*> lp(ues);
+    std::vector<uint64_t> tk(ues);
+    while (!q.empty()) {
+      const Ev ev = q.top();
+      q.pop();
+      if (ev.first >= t_end) continue;
+      while (now_ns() < ev.first) {
+      }
+      const int c = ev.second;
+      const int pid = sf[c] % 8;
+      for (int u = 0; u < ues; u++) {
+        const int e = (c * ues + u) % n;
+        tb[u] = par[e];
+        lp[u] = ptr[e];
+        tb[u].cell = (uint32_t)c;
+        tb[u].ue = (uint32_t)u;
+        tb[u].harq_pid = (uint32_t)pid;
+        tb[u].flags = CRNT_F_HARQ | extra_flags;
+        const bool rt = sf[c] >= 8 && unit(rh) < retx;
+        static const uint8_t rv_cycle[4] = {2, 3, 1, 0};
+        tb[u].new_data = rt ? 0 : 1;
+        tb[u].rv = rt ? rv_cycle[(sf[c] / 8) % 4] : 0;
+      }
       const int rc = crnt_submit(ctx, tb.data(), lp.data(), (uint32_t)ues, tk.data());
       if (rc == CRNT_OK) {
-        for (int u = 0; u < ues; u++) pending[tk[u]] = {ev.first, tb[u].A};
+        std::lock_guard<std::mutex> lk(mu);
+        for (int u = 0; u < ues; u++) {
+          auto it = early.find(tk[u]);
+          if (it != early.end()) {
+            record(ev.first, tb[u].A, it->second.first, it->second.second);
+            early.erase(it);
+          } else {
+            pending[tk[u]] = {ev.first, tb[u].A};
+          }
+        }
       } else {
         refused++;
       }
+      subframes++;
+      sf[c]++;
+      if (poisson) {
+        const double gap = -std::log(1.0 - unit(rh)) * 1e6;  // exponential, mean 1 ms
+        q.push(Ev{ev.first + (int64_t)gap, c});
+      } else {
+        const double jit = (unit(rh) - 0.5) * 400000.0;
+        q.push(Ev{t0 + (int64_t)sf[c] * 1000000 + (int64_t)(phase[c] + jit), c});
+      }
     }
-    subframes++;
-    sf[c]++;
-    if (poisson) {
-      const double gap = -std::log(1.0 - unit(rs)) * 1e6;  // exponential, mean 1 ms
-      q.push(Ev{ev.first + (int64_t)gap, c});
-    } else {
-      const double jit = (unit(rs) - 0.5) * 400000.0;
-      q.push(Ev{t0 + (int64_t)sf[c] * 1000000 + (int64_t)(phase[c] + jit), c});
-    }
-  }
-  done_submitting.store(true);
+    submitting--;
+  };
+  std::vector<std::thread> subs;
+  for (int h = 0; h < nthreads; h++) subs.emplace_back(submitter, h);
+  for (auto& th : subs) th.join();
   poller.join();
   Point p;
   p.cells = cells;
-  p.subframes = subframes;
-  p.refused = refused;
+  p.subframes = subframes.load();
+  p.refused = refused.load();
   p.errors = errors;
   std::sort(lat.begin(), lat.end());
   p.tbs = (long)lat.size();
@@ -188,11 +211,16 @@ int main(int argc, char** argv) {
   }
   uint32_t extra_flags = 0;
   bool poisson = false;
+  int nthreads = 4;
   for (;;) {
     if (argc > 1 && strcmp(argv[1], "--purge") == 0) {
       extra_flags = CRNT_F_PURGE;
     } else if (argc > 1 && strcmp(argv[1], "--poisson") == 0) {
       poisson = true;
+    } else if (argc > 2 && strcmp(argv[1], "--threads") == 0) {
+      nthreads = std::max(1, std::min(64, atoi(argv[2])));
+      argv += 1;
+      argc -= 1;
     } else {
       break;
     }
@@ -201,8 +229,8 @@ int main(int argc, char** argv) {
   }
   if (argc < 7) {
     fprintf(stderr,
-            "usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] FILE UES SECONDS RETX SEED "
-            "CELLS...\n");
+            "usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--threads T] FILE UES "
+            "SECONDS RETX SEED CELLS...\n");
     return 2;
   }
   FILE* f = fopen(argv[1], "rb");
@@ -233,11 +261,11 @@ int main(int argc, char** argv) {
   if (crnt_create(&ctx, &cfg) != CRNT_OK) return 3;
   // warm-up pass (not reported): the serving loop's buffers come up here
   run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1, extra_flags,
-            poisson);
+            poisson, nthreads);
   for (int a = 6; a < argc; a++) {
     const int cells = atoi(argv[a]);
     const Point p =
-        run_point(ctx, par, ptr, ues, cells, seconds, retx, seed, extra_flags, poisson);
+        run_point(ctx, par, ptr, ues, cells, seconds, retx, seed, extra_flags, poisson, nthreads);
     printf("{\"cells\": %d, \"tbs\": %ld, \"subframes\": %ld, \"refused_subframes\": %ld, "
            "\"errors\": %ld, \"p50_us\": %.1f, \"p99_us\": %.1f, \"deadline_miss\": %.6f, "
            "\"gbit_s\": %.4f}\n",

@@ -56,22 +56,20 @@ struct HarqPool {
 
 struct Serving;
 
-// Address tables of the interleaved SISO pass, one per (K, P) on the
-// context's device (CbDesc::qt): built on the host and uploaded on first
-// use, kept until the context is destroyed.
+// Tables of one (K, P) on the context's device: the interleaved SISO pass's
+// addresses (CbDesc::qt, qq) and the de-rate-matching maps of the eight
+// filler counts (CbDesc::dm); built on the host and uploaded on first use,
+// kept until the context is destroyed.
 struct QTabs {
-  static constexpr int kFill = 7;  // filler counts 8, 16, ..., 56 have their own maps
   std::mutex mu;  // guards building (readers use the atomics)
   std::atomic<const uint4*> t[lte::kNumK][CRNT_MAX_P + 1];
-  std::vector<std::atomic<const uint32_t*>> dmf;  // [K index][P][F / 8 - 1]
   std::vector<void*> chunks;  // device allocations
   uint8_t* cur = nullptr;     // free space in the last chunk
   size_t left = 0;
   cudaStream_t stream = nullptr;
-  QTabs() : dmf((size_t)lte::kNumK * (CRNT_MAX_P + 1) * kFill) {
+  QTabs() {
     for (auto& row : t)
       for (auto& x : row) x.store(nullptr, std::memory_order_relaxed);
-    for (auto& x : dmf) x.store(nullptr, std::memory_order_relaxed);
   }
 };
 
@@ -178,12 +176,6 @@ inline const uint2* qtab_q(const uint4* t, int K, int P) {
 }
 // The de-rate-matching map of (K, P, F) (CbDesc::dm), null if it cannot be built.
 const uint32_t* dmap_get(crnt_ctx* ctx, int K, int P, int F);
-// The de-rate-matching map without filler bits, stored after the (K, P) tables.
-inline const uint32_t* qtab_dm(const uint4* t, int K, int P) {
-  const int W = (K + P - 1) / P;
-  return t ? (const uint32_t*)(qtab_q(t, K, P) + (size_t)((W + kSub - 1) / kSub + 2) * P)
-           : nullptr;
-}
 // 1 if the radix table selects the radix-4 forward recursion for CB size K.
 // t_radix_override >= 0 replaces the table for plans built on this thread
 // (the autotuner's candidates).
