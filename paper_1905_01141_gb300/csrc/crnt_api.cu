@@ -876,8 +876,9 @@ int crnt_create(crnt_ctx** out, const crnt_config* cfg) {
     crnt_destroy(c);
     return CRNT_EDEVICE;
   }
-  // address tables of the window counts P = 0 requests get now (others on
-  // first use); without them the decoder computes the addresses
+  // the per-(K, P) tables (interleaved-pass addresses, de-rate-matching
+  // maps) of the window counts P = 0 requests get, now (others on first
+  // use); without them the decoder computes addresses and walks the buffer
   c->qtabs = new (std::nothrow) QTabs;
   if (c->qtabs &&
       cudaStreamCreateWithFlags(&c->qtabs->stream, cudaStreamNonBlocking) != cudaSuccess) {
