@@ -195,3 +195,16 @@ def test_interleaver_map_matches_oracle_qpp(orc, crnt_lib, K, P):
         assert np.array_equal(q, pi[p * W:p * W + n]), p
         assert np.array_equal(t, (q % W) * Pe + q // W), p
         assert not m[p, n:].any()
+
+
+def test_load_generator_built_and_checks_its_arguments(crnt_lib):
+    # the native load generator is a client of the C ABI only; argument
+    # errors end it with status 2 before it touches a GPU
+    import subprocess
+    from paper_1905_01141_gb300 import build as crnt_build
+    assert os.path.exists(crnt_build.LOADGEN)
+    r = subprocess.run([crnt_build.LOADGEN], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 2 and "usage" in r.stderr
+    r = subprocess.run([crnt_build.LOADGEN, "--threads", "2", "--poisson", "/nonexistent", "8",
+                        "1", "0.1", "1", "4"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 2
