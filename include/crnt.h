@@ -293,7 +293,8 @@ int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb,
  * CRNT_EAGAIN when admission is refused (nothing of the call is queued).
  * TBs that share a HARQ key (cell, ue, harq_pid) must not be in flight at
  * the same time (a retransmission is submitted after the previous
- * transmission's result was polled, as the HARQ round trip implies). */
+ * transmission's result was polled, as the HARQ round trip implies).
+ * Several threads may submit at once; each call copies its own LLRs. */
 int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* llrs, uint32_t n,
                 uint64_t* tickets_out);
 /* Collect up to max finished TBs, waiting at most timeout_us for the first.
