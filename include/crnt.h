@@ -105,8 +105,12 @@ typedef struct crnt_tb_result {
     uint8_t cb_iters_run[CRNT_MAX_CB]; /* iterations actually run per CB (a failure
                                        under a stop rule may stop before max_iter;
                                        a purged CB reports the ones it ran) */
-    uint16_t P_used;                /* window count requested after clamping, for K+ */
-    uint16_t pad0;
+    uint16_t P_used;                /* window count used for K+ (after clamping: the
+                                       windows the decoder actually runs) */
+    uint16_t sat_passes;            /* window passes of this TB's CBs that ran the
+                                       saturating int16 arithmetic (the decoder's exact
+                                       path; every other pass was proved unable to
+                                       saturate and ran clamp-free), capped at 65535 */
     uint64_t ticket;                /* serving ticket (0 elsewhere) */
     uint64_t t_submit_ns, t_start_ns, t_done_ns; /* serving timestamps (CLOCK_MONOTONIC) */
 } crnt_tb_result;
@@ -203,15 +207,6 @@ int crnt_tune_radix_set(const uint8_t* radix_by_k, uint32_t n);
  * seconds; allocates device memory for its inputs and frees it. */
 int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k);
 
-/* ---- measurement ------------------------------------------------------ */
-/* Issue rate of one integer instruction kind on `device`, in warp-
- * instructions per SM clock, from a fully resident probe kernel with 8
- * independent chains per thread (clock64 timing): kind 0 = DPX add-max
- * s32 (the trellis ACS instruction), 1 = DPX add-max s16x2, 2 = 32-bit
- * multiply-add, 3 = kinds 0 and 2 interleaved 1:1.  Grounds the decode
- * kernel's ALU-issue roofline; the paper has no counterpart. */
-int crnt_int_issue_probe(int device, int kind, double* warp_instr_per_clk_per_sm);
-
 /* ---- context ---------------------------------------------------------- */
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates the
  * HARQ soft-buffer arena lazily.  CRNT_EDEVICE if CUDA is unusable. */
@@ -259,18 +254,23 @@ int crnt_decode_tb(crnt_ctx* ctx, const int8_t* llr, const crnt_tb_params* tb, u
  * not allocate device memory -- for example code that runs inside another
  * framework's memory pool or between phases where allocation is forbidden --
  * and so cannot create a context (crnt_create allocates).  Descriptors, the
- * work queue, CRC tables and per-launch scratch live in one fixed file-scope
- * device array of about 134 KiB held by every GPU that loads the library; no
- * cudaMalloc, cudaFree, pinned or library allocation happens in this call.
- * llr (device, concatenated G LLRs) in, out (device, concatenated A/8 bytes)
- * out, res[n] (host) results; runs on `stream` (NULL = default) on the
- * current device and returns after that stream has finished the decode.
- * Limits: n <= 64 TBs and at most 832 code blocks in total, else
- * CRNT_ENOMEM ("exceeds the static workspace"); no HARQ combining
- * (CRNT_F_HARQ gives CRNT_EINVAL).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and uploads the CRC tables
- * with synchronous copies, so make that first call before any stream
- * capture.  Every call shares the array: calls whose GPU work overlaps (two
+ * work queue, the CRC and mutual-information tables and per-launch scratch
+ * live in one fixed file-scope device array of about 153 KiB held by every
+ * GPU that loads the library; no cudaMalloc, cudaFree, pinned or library
+ * allocation happens in this call.  llr (concatenated G LLRs) in, out
+ * (concatenated A/8 bytes) out, both device, managed or page-locked host
+ * memory (pageable host memory gives CRNT_EINVAL: there is nowhere to stage
+ * it), res[n] (host) results, the same fields as crnt_decode_batch; runs on
+ * `stream` (NULL = default) on the current device and returns after that
+ * stream has finished the decode, also when it fails.  Limits: n <= 64 TBs
+ * and at most 832 code blocks in total, else CRNT_ENOMEM ("exceeds the
+ * static workspace"); no HARQ combining (CRNT_F_HARQ gives CRNT_EINVAL);
+ * purge on failure and all stop rules work as elsewhere.  Without a context
+ * there are no per-(K, P) tables, so the kernel computes its interleaver
+ * addresses and circular-buffer walk (same results).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * uploads the tables with synchronous copies, so make that first call before
+ * any stream capture.  Every call shares the array: calls whose GPU work overlaps (two
  * streams, or two host threads) race on it, so do not overlap them. */
 int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, const int8_t* llr,
                              uint8_t* out, crnt_tb_result* res, void* stream);

@@ -49,7 +49,7 @@ class TbResult(ctypes.Structure):
                 ("K_plus", ctypes.c_uint16), ("K_minus", ctypes.c_uint16), ("F", ctypes.c_uint16),
                 ("cb_iters", ctypes.c_uint8 * MAX_CB), ("cb_crc_ok", ctypes.c_uint8 * MAX_CB),
                 ("cb_iters_run", ctypes.c_uint8 * MAX_CB),
-                ("P_used", ctypes.c_uint16), ("pad0", ctypes.c_uint16),
+                ("P_used", ctypes.c_uint16), ("sat_passes", ctypes.c_uint16),
                 ("ticket", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
                 ("t_start_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
 
@@ -59,6 +59,7 @@ class TbResult(ctypes.Structure):
                     Km=self.K_minus, F=self.F, cb_iters=list(self.cb_iters[:C]),
                     cb_crc_ok=[bool(x) for x in self.cb_crc_ok[:C]],
                     cb_iters_run=list(self.cb_iters_run[:C]), P_used=self.P_used,
+                    sat_passes=self.sat_passes,
                     ticket=self.ticket, t_submit_ns=self.t_submit_ns,
                     t_start_ns=self.t_start_ns, t_done_ns=self.t_done_ns)
 
@@ -109,7 +110,6 @@ SIGNATURES = {
     "crnt_tune_radix_get": (ctypes.c_int, [_P, _U32]),
     "crnt_tune_radix_set": (ctypes.c_int, [_P, _U32]),
     "crnt_autotune": (ctypes.c_int, [_P, _U32, _P]),
-    "crnt_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P]),
 }
 
 

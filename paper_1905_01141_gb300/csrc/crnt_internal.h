@@ -92,6 +92,7 @@ struct DecParams {
   uint8_t* cb_ok;         // [n_cbs]
   uint8_t* cb_runs;       // [n_cbs] iterations run (may be null)
   uint8_t* tb_ok;         // [n_tbs]
+  uint32_t* tb_sat;       // [n_tbs] window passes on the saturating path (may be null)
   const uint32_t* xpowA;  // x^(32 s) mod gCRC24A, s < 2400
   const uint32_t* xpowB;  // x^(32 s) mod gCRC24B, s < 200
   const int32_t* mi_tab;  // [kMiTable] mutual-information table (stop rule 2)

@@ -300,9 +300,9 @@ struct CbSlot {
   uint4* seed;   // [4][P]: alpha dec0, alpha dec1, beta dec0, beta dec1
   uint4* ck;     // [P][nck]
   int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|,
-                 // [6] stopped by a purge, [8] / [9] mutual information of this / the
-                 // previous iteration (2^16 units per bit, summed over the CB),
-                 // [10] iterations run
+                 // [6] stopped by a purge, [7] window passes on the saturating path,
+                 // [8] / [9] mutual information of this / the previous iteration
+                 // (2^16 units per bit, summed over the CB), [10] iterations run
 };
 __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
   CbSlot s;
@@ -443,6 +443,7 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     sl.flags[4] = 0;
     sl.flags[5] = 0;
     sl.flags[6] = 0;
+    sl.flags[7] = 0;
     sl.flags[8] = 0;
     sl.flags[9] = 0;
   }
@@ -822,10 +823,12 @@ __device__ __forceinline__ void siso_pass(const CbDesc* __restrict__ dp, uint8_t
       for (int j = 2; j >= 0; j--) beta_tail_step(b, t[2 * j], t[2 * j + 1]);
     }
     int mx = 0, mn = 0;
-    if (window_fast(a, b, 254 + m_in))
+    if (window_fast(a, b, 254 + m_in)) {
       window_pass<DEC, false, R4, QT>(w, dp, ck, seedA, seedB, a, b, mx, mn, pf0, pf1);
-    else
+    } else {
       window_pass<DEC, true, R4, QT>(w, dp, ck, seedA, seedB, a, b, mx, mn, pf0, pf1);
+      atomicAdd(&sl.flags[7], 1);  // counted per CB, reported per TB
+    }
     atomicMax(&sl.flags[4 + DEC], max(mx, -mn));
   }
   __syncthreads();
@@ -1033,6 +1036,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
       prm.cb_iters[sorted_idx] = (uint8_t)sl.flags[1];
       if (prm.cb_runs) prm.cb_runs[sorted_idx] = (uint8_t)sl.flags[10];
       prm.cb_ok[sorted_idx] = cb_ok ? 1 : 0;
+      if (prm.tb_sat && sl.flags[7]) atomicAdd(&prm.tb_sat[d.tb], (unsigned)sl.flags[7]);
       const TbDesc tb = prm.tbs[d.tb];
       if (tb.C == 1) {
         prm.tb_ok[d.tb] = cb_ok ? 1 : 0;

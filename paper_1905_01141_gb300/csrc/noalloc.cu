@@ -3,9 +3,10 @@
 // pool they do not own, or an allocator that is forbidden at that point).
 //
 // Everything the decode kernel needs besides the caller's inputs and outputs
-// -- the code-block descriptors, the work queue, the CRC shift tables and the
-// per-launch scratch (queue head, per-TB counters and CRC accumulators,
-// per-CB results) -- lives in one file-scope __device__ array of fixed size.
+// -- the code-block descriptors, the work queue, the CRC shift tables, the
+// mutual-information table of stop rule 2 and the per-launch scratch (queue
+// head, per-TB counters and CRC accumulators, per-CB results) -- lives in one
+// file-scope __device__ array of fixed size.
 // The host side plans into fixed static arrays of the same capacity.  Nothing
 // is allocated on the device or in pinned host memory; the kernel is the same
 // fused decode kernel the other entry points launch.
@@ -18,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -42,10 +44,12 @@ constexpr size_t kOffXB = kOffXA + al(4 * kXA);
 constexpr size_t kOffState = kOffXB + al(4 * kXB);
 constexpr size_t kOffDone = kOffState + 256;
 constexpr size_t kOffCrc = kOffDone + al(4 * kStaticTbs);
-constexpr size_t kZeroBytes = kOffCrc + al(8 * kStaticTbs) - kOffState;
-constexpr size_t kOffRes = kOffCrc + al(8 * kStaticTbs);  // cb_iters | cb_ok | tb_ok
-constexpr size_t kResBytes = 2 * kStaticCbs + kStaticTbs;
-constexpr size_t kStaticBytes = al(kOffRes + kResBytes);
+constexpr size_t kOffSat = kOffCrc + al(8 * kStaticTbs);  // per-TB saturating-pass counts
+constexpr size_t kZeroBytes = kOffSat + al(4 * kStaticTbs) - kOffState;
+constexpr size_t kOffRes = kOffSat + al(4 * kStaticTbs);  // cb_iters | cb_ok | cb_runs | tb_ok
+constexpr size_t kResBytes = 3 * kStaticCbs + kStaticTbs;
+constexpr size_t kOffMi = al(kOffRes + kResBytes);        // mutual-information table
+constexpr size_t kStaticBytes = kOffMi + al(4 * kMiTable);
 static_assert(kStaticBytes <= 512 * 1024, "static decode workspace stays within 512 KiB");
 
 // The workspace.  Host code must not take its address directly: the name is
@@ -65,7 +69,7 @@ TbDesc h_tbs[kStaticTbs];
 WorkItem h_items[kStaticCbs];
 lte::Seg h_segs[kStaticTbs];
 uint16_t h_pused[kStaticTbs];
-uint8_t h_res[kResBytes];
+uint8_t h_back[kOffRes - kOffSat + kResBytes];  // counts | results, copied back together
 
 int clamp_windows(int K, int P) {
   if (P <= 0) P = tuned_p(K);  // the process-wide table (a read, no allocation)
@@ -149,7 +153,8 @@ int k0_rank(int K, int F, int rv, uint32_t mb, uint32_t m2) {
   return (32 * R - X) + 2 * R * c - pre0(c) - __builtin_popcount(m2 & ((1u << c) - 1u));
 }
 
-// One-time set-up on the current device: workspace address and CRC tables.
+// One-time set-up on the current device: workspace address, CRC and
+// mutual-information tables.
 int setup(int dev) {
   if (dev < 0 || dev >= kMaxDevices) return CRNT_EDEVICE;
   if (g_dev_ptr[dev]) return CRNT_OK;
@@ -159,14 +164,35 @@ int setup(int dev) {
     return CRNT_EDEVICE;
   }
   static uint32_t xa[kXA], xb[kXB];
+  static int32_t mi[kMiTable];
   xpow_fill(0x1864CFBu, kXA, xa);
   xpow_fill(0x1800063u, kXB, xb);
+  // stop rule 2: T(x) = round(2^16 log2(1 + exp(-x/8))), as crnt_create builds it
+  for (int x = 0; x < kMiTable; x++)
+    mi[x] = (int32_t)std::floor(65536.0 * std::log2(1.0 + std::exp(-(double)x / 8.0)) + 0.5);
   if (cudaMemcpy((uint8_t*)ptr + kOffXA, xa, sizeof xa, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy((uint8_t*)ptr + kOffXB, xb, sizeof xb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy((uint8_t*)ptr + kOffMi, mi, sizeof mi, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return CRNT_EDEVICE;
   g_dev_ptr[dev] = ptr;
   return CRNT_OK;
+}
+
+// The address under which the kernel can use a caller buffer: device and
+// managed memory as is, page-locked host memory through its mapped device
+// address; nullptr for anything else (pageable host memory cannot be read by
+// the kernel, and this entry point has no staging buffer to copy it into).
+// cudaPointerGetAttributes allocates nothing.
+void* kernel_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return (void*)p;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  return nullptr;
 }
 
 }  // namespace
@@ -185,6 +211,9 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
   if (rc) return rc;
   uint8_t* ws = (uint8_t*)g_dev_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
+  const int8_t* llr_k = (const int8_t*)kernel_view(llr);
+  uint8_t* out_k = (uint8_t*)kernel_view(out);
+  if (!llr_k || !out_k) return CRNT_EINVAL;  // pageable or unknown memory
 
   // ---- host planning into static storage
   int ncb = 0;
@@ -195,7 +224,6 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     rc = validate(tp, &sg);
     if (rc) return rc;
     if (tp.flags & CRNT_F_HARQ) return CRNT_EINVAL;  // no soft-buffer arena here
-    if (tp.early_stop > 1) return CRNT_EINVAL;       // no mutual-information table here
     if (ncb + sg.C > kStaticCbs) return CRNT_ENOMEM;
     TbDesc& td = h_tbs[t];
     memset(&td, 0, sizeof td);
@@ -203,7 +231,6 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     td.A = (int)tp.A;
     td.C = sg.C;
     td.cb0 = ncb;
-    h_pused[t] = (uint16_t)clamp_windows(sg.Kp, tp.P);
     const int B = (int)tp.A + 24;
     int pay_off = 0, eoff = 0;
     for (int r = 0; r < sg.C; r++) {
@@ -218,7 +245,8 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
       d.E = lte::e_r((int)tp.G, tp.Qm, tp.NL, sg.C, r);
       d.k0 = lte::k0(K, tp.rv);
       d.W = W;
-      d.P = (K + W - 1) / W;
+      d.P = (K + W - 1) / W;  // the windows actually run (ceil(K / W) <= Pr)
+      if (K == sg.Kp) h_pused[t] = (uint16_t)d.P;
       if (!divider(W, K + 4, &d.divM, &d.divS)) return CRNT_EINVAL;
       const int ki = lte::index_of(K);
       d.f1 = lte::kF1[ki];
@@ -241,8 +269,9 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
       d.n_after = B - pay_off - d.pay_bits;
       d.crc_b = sg.C > 1;
       d.max_iter = tp.max_iter;
-      d.early_stop = tp.early_stop ? 1 : 0;
+      d.early_stop = tp.early_stop;  // 0 none, 1 CRC, 2 mutual information
       d.new_data = 1;
+      d.purge = (tp.flags & CRNT_F_PURGE) && sg.C > 1 ? 1 : 0;
       d.radix4 = radix4_of(K);  // the process-wide radix table (a read)
       h_all_tb[ncb] = (int)t;
       h_all_r[ncb] = r;
@@ -302,30 +331,42 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
   p.n_items = nitems;
   p.n_cbs = ncb;
   p.n_tbs = (int)n;
-  p.llr = llr;
-  p.out = out;
+  p.llr = llr_k;
+  p.out = out_k;
   p.soft = nullptr;
   p.state = (DecState*)(ws + kOffState);
   p.tb_done = (int32_t*)(ws + kOffDone);
   p.tb_crc = (uint32_t*)(ws + kOffCrc);
-  p.cb_iters = ws + kOffRes;
+  p.tb_sat = (uint32_t*)(ws + kOffSat);
+  p.cb_iters = ws + kOffRes;  // cb_iters | cb_ok | cb_runs | tb_ok, as the plan path
   p.cb_ok = p.cb_iters + ncb;
-  p.tb_ok = p.cb_ok + ncb;
+  p.cb_runs = p.cb_iters + 2 * (size_t)ncb;
+  p.tb_ok = p.cb_iters + 3 * (size_t)ncb;
   p.xpowA = (const uint32_t*)(ws + kOffXA);
   p.xpowB = (const uint32_t*)(ws + kOffXB);
+  p.mi_tab = (const int32_t*)(ws + kOffMi);
   for (int i = 0; i < ncb; i++) p.radix4_any |= h_cbs[i].radix4;
-  const size_t res_bytes = 2 * (size_t)ncb + n;
-  if (cudaMemcpyAsync(ws + kOffCbs, h_cbs, sizeof(CbDesc) * ncb, cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(ws + kOffTbs, h_tbs, sizeof(TbDesc) * n, cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
+  const size_t back_bytes = (kOffRes - kOffSat) + 3 * (size_t)ncb + n;
+  bool ok =
+      cudaMemcpyAsync(ws + kOffCbs, h_cbs, sizeof(CbDesc) * ncb, cudaMemcpyHostToDevice, s) ==
+          cudaSuccess &&
+      cudaMemcpyAsync(ws + kOffTbs, h_tbs, sizeof(TbDesc) * n, cudaMemcpyHostToDevice, s) ==
+          cudaSuccess &&
       cudaMemcpyAsync(ws + kOffItems, h_items, sizeof(WorkItem) * nitems, cudaMemcpyHostToDevice,
-                      s) != cudaSuccess ||
-      cudaMemsetAsync(ws + kOffState, 0, kZeroBytes, s) != cudaSuccess ||
-      launch_decode(p, grid, smem, s) != cudaSuccess ||
-      cudaMemcpyAsync(h_res, ws + kOffRes, res_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+                      s) == cudaSuccess &&
+      cudaMemsetAsync(ws + kOffState, 0, kZeroBytes, s) == cudaSuccess &&
+      launch_decode(p, grid, smem, s) == cudaSuccess &&
+      cudaMemcpyAsync(h_back, ws + kOffSat, back_bytes, cudaMemcpyDeviceToHost, s) ==
+          cudaSuccess;
+  // wait for whatever was enqueued, also on failure, so that no kernel of
+  // this call still uses the shared workspace when the next call clears it
+  ok = (cudaStreamSynchronize(s) == cudaSuccess) && ok;
+  if (!ok) {
+    cudaGetLastError();
     return CRNT_EDEVICE;
+  }
+  const uint32_t* sat = (const uint32_t*)h_back;
+  const uint8_t* h_res = h_back + (kOffRes - kOffSat);
   for (uint32_t t = 0; t < n; t++) {
     crnt_tb_result& r = res[t];
     memset(&r, 0, sizeof r);
@@ -335,14 +376,14 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     r.K_minus = (uint16_t)h_segs[t].Km;
     r.F = (uint16_t)h_segs[t].F;
     r.P_used = h_pused[t];
-    r.tb_crc_ok = h_res[2 * ncb + t];
+    r.sat_passes = (uint16_t)std::min<uint32_t>(sat[t], 65535u);
+    r.tb_crc_ok = h_res[3 * ncb + t];
   }
   for (int i = 0; i < ncb; i++) {
-    res[h_cb_tb[i]].cb_iters[h_cb_r[i]] = h_res[i];
-    res[h_cb_tb[i]].cb_crc_ok[h_cb_r[i]] = h_res[ncb + i];
-    // stop rules 0 and 1 only: a failure ran all max_iter iterations
-    const int mi = tbs[h_cb_tb[i]].max_iter;
-    res[h_cb_tb[i]].cb_iters_run[h_cb_r[i]] = (uint8_t)std::min((int)h_res[i], mi);
+    crnt_tb_result& r = res[h_cb_tb[i]];
+    r.cb_iters[h_cb_r[i]] = h_res[i];
+    r.cb_crc_ok[h_cb_r[i]] = h_res[ncb + i];
+    r.cb_iters_run[h_cb_r[i]] = h_res[2 * ncb + i];
   }
   return CRNT_OK;
 }

@@ -9,6 +9,12 @@
 // Kinds: 0 = DPX add-max s32 (VIADDMNMX, the ACS / Lambda instruction),
 // 1 = DPX add-max s16x2 (the packed form), 2 = 32-bit integer multiply-add
 // (IMAD, FMA pipe), 3 = add-max and multiply-add interleaved 1:1.
+//
+// A measurement tool, not part of the decoding library: it is built into its
+// own shared object (libcrnt_probe.so) with the one entry point
+//   int crnt_int_issue_probe(int device, int kind, double* warp_instr_per_clk_per_sm);
+// returning CRNT_OK, CRNT_EINVAL for an unknown kind or a null result, or
+// CRNT_EDEVICE on a CUDA error.
 #include <cuda_runtime.h>
 
 #include <cstdint>

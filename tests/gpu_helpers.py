@@ -6,12 +6,13 @@ import numpy as np
 import synth
 
 
-def make_tb(orc, A, G, Qm, seed, rv=0, ebn0=None, snr=None, noiseless=False):
-    """Payload bits and int8 LLRs of one TB (oracle encoder, synth channel)."""
+def make_tb(orc, A, G, Qm, seed, rv=0, ebn0=None, snr=None, noiseless=False, amp=100):
+    """Payload bits and int8 LLRs of one TB (oracle encoder, synth channel;
+    noiseless: +-amp)."""
     a = synth.bits(seed, 100, A)
     e = orc.encode_tb(a, G, Qm=Qm, rv=rv)
     if noiseless:
-        llr = np.where(e == 0, 100, -100).astype(np.int8)
+        llr = np.where(e == 0, amp, -amp).astype(np.int8)
     elif ebn0 is not None:
         llr = synth.channel_llrs(e, 1, synth.sigma2_ebn0(ebn0, A / G), seed, 200)
     else:
@@ -87,11 +88,23 @@ def _diff(x, y):
     return dict(n=len(d), first=[(int(i), int(x[i]), int(y[i])) for i in d[:4]])
 
 
+def oracle_batch(orc, crnt, tbs, llrs, idx, workers=None):
+    """oracle_tb of the TBs idx on a thread pool (the oracle's ctypes calls
+    release the GIL); returns {t: oracle_tb(...)}."""
+    import concurrent.futures as cf
+    import os
+    workers = workers or min(32, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {t: ex.submit(oracle_tb, orc, crnt, tbs[t], llrs[t]) for t in idx}
+        return {t: f.result() for t, f in futs.items()}
+
+
 def check_batch(orc, crnt, tbs, llrs, g, sample=None):
     """Compare every (or a sample of) TB of a GPU run with the oracle:
     de-rate-matched streams, hard decisions, extrinsics, iteration counts,
     CRC flags and payload bytes -- all bit-exact."""
-    idx = range(len(tbs)) if sample is None else sample
+    idx = list(range(len(tbs)) if sample is None else sample)
+    want = oracle_batch(orc, crnt, tbs, llrs, idx)
     dbg_off = [0]
     for t in tbs:
         for c in crnt.tb_layout(t):
@@ -104,7 +117,7 @@ def check_batch(orc, crnt, tbs, llrs, g, sample=None):
     out_off = np.cumsum([0] + [t["A"] // 8 for t in tbs])
     for t in idx:
         tb = tbs[t]
-        cbs, bits, tb_ok, _ = oracle_tb(orc, crnt, tb, llrs[t])
+        cbs, bits, tb_ok, _ = want[t]
         res = g["res"][t]
         assert res["C"] == len(cbs)
         for r, (d0, d1, d2, it, hard, ext, ran) in enumerate(cbs):
@@ -126,3 +139,4 @@ def check_batch(orc, crnt, tbs, llrs, g, sample=None):
         assert res["tb_crc_ok"] == tb_ok, ("tbok", t)
         got = np.unpackbits(g["out"][out_off[t]:out_off[t + 1]])
         assert np.array_equal(got, bits), ("payload", t)
+    return want
