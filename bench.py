@@ -58,6 +58,9 @@ def parse():
                     help="write the window table (and, on a second line, the radix table) here")
     ap.add_argument("--radix", choices=("tuned", "2", "4"), default="tuned",
                     help="forward-recursion radix: the autotuner's choice per K, or one for all K")
+    ap.add_argument("--shape", choices=("tuned", "1", "2"), default="tuned",
+                    help="CTA shape: the autotuner's choice per K, or one for all K (1 one CB "
+                         "per thread, 2 CB pairs in 16-bit lanes)")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
     ap.add_argument("--sweep", choices=["bler", "stop", "peak"],
                     help="quality sweep instead of the bench line (stop: CRC vs mutual "
@@ -267,15 +270,21 @@ def run_ours(args):
             crnt.tune_set(table)
             if len(vals) >= 2 * crnt.NUM_K:
                 crnt.tune_radix_set(vals[crnt.NUM_K:2 * crnt.NUM_K])
+            if len(vals) >= 3 * crnt.NUM_K:
+                crnt.tune_shape_set(vals[2 * crnt.NUM_K:3 * crnt.NUM_K])
         else:
             table = ctx.autotune(32)
         if args.radix != "tuned":
             crnt.tune_radix_set([int(args.radix)] * crnt.NUM_K)
+        if args.shape != "tuned":
+            crnt.tune_shape_set([int(args.shape)] * crnt.NUM_K)
         radix = crnt.tune_radix_get()
+        shape = crnt.tune_shape_get()
         if args.save_tune:
             with open(args.save_tune, "w") as f:
                 f.write(" ".join(str(x) for x in table) + "\n")
                 f.write(" ".join(str(x) for x in radix) + "\n")
+                f.write(" ".join(str(x) for x in shape) + "\n")
         ks = (list(range(40, 513, 8)) + list(range(528, 1025, 16)) + list(range(1056, 2049, 32))
               + list(range(2112, 6145, 64)))  # the 188 CB sizes, in table order
         builtin = [max(1, min(k // 8, 128, -(-k // 48))) for k in ks]
@@ -284,6 +293,8 @@ def run_ours(args):
                 "entries_changed_from_builtin": sum(int(a != b) for a, b in zip(table, builtin)),
                 "radix": args.radix,
                 "radix4_at_K": [k for k, r in zip(ks, radix) if r == 4],
+                "shape": args.shape,
+                "pair_shape_at_K": [k for k, v in zip(ks, shape) if v == 2],
                 "P_at_K": {str(k): p for k, p in zip(ks, table)
                            if k in (40, 256, 512, 1024, 2048, 4096, 5824, 5888, 6016, 6144)}}
 
@@ -371,7 +382,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_tb": args.n_tb, "n_cb": info["n_cb"],
                        "info_bits_per_step": info["info_bits"], "llr_bytes": info["llr_bytes"],
-                       "work_items": info["n_items"], "grid": info["grid"],
+                       "work_items": info["n_items"], "pair_items": info["pair_items"],
+                       "grid": info["grid"], "smem_bytes_per_cta": info["smem_bytes"],
                        "l2": "flushed (256 MiB write) before every timed step",
                        "autotune": tune,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -382,7 +394,8 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
-        tt = None if args.no_autotune else crnt.tune_get() + crnt.tune_radix_get()
+        tt = (None if args.no_autotune
+              else crnt.tune_get() + crnt.tune_radix_get() + crnt.tune_shape_get())
         line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
         line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 48, 56, 64, 72),
                                             tune_table=tt, purge=True)

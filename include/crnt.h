@@ -134,6 +134,8 @@ typedef struct crnt_plan_info {
     uint64_t trellis_steps; /* sum of K over CBs (one SISO pass visits each once) */
     uint64_t dbg_elems;   /* sum of (K+4) over CBs: length of the debug arrays */
     uint32_t n_items, grid;
+    uint32_t pair_items;  /* work items that decode a CB pair (shape table entry 2) */
+    uint32_t smem_bytes;  /* dynamic shared memory of one decode CTA */
 } crnt_plan_info;
 
 /* ---- library ---------------------------------------------------------- */
@@ -197,14 +199,30 @@ int crnt_tune_set(const uint8_t* P_by_k, uint32_t n); /* n must be 188 */
  * 4; set accepts 0 (= 2), 2 or 4 and needs n = 188. */
 int crnt_tune_radix_get(uint8_t* radix_by_k, uint32_t n);
 int crnt_tune_radix_set(const uint8_t* radix_by_k, uint32_t n);
+/* CTA shape per CB size, a third process-wide table (the paper's
+ * parallelism granularity per worker, Sec. IV-B "Scheduler", chosen by
+ * measurement).  Entry i is 1 (the default: the P windows of a CB run on P
+ * threads, one window each) or 2 (CB pairs: two CBs of that size and window
+ * count run on the same P threads, window p of both in the two 16-bit halves
+ * of each register, so every add-max instruction advances two CBs; such
+ * batches run two CTAs per SM).  A pass that cannot be proved to stay within
+ * 16 bits runs one CB at a time, so the shape never changes a decoded value,
+ * only the speed.  Pairs need the context's per-(K, P) tables and the
+ * radix-2 recursion; the allocation-free entry point runs shape 1.  get
+ * writes 1 or 2; set accepts 0 (= 1), 1 or 2 and needs n = 188. */
+int crnt_tune_shape_get(uint8_t* shape_by_k, uint32_t n);
+int crnt_tune_shape_set(const uint8_t* shape_by_k, uint32_t n);
 /* Measure on ctx's GPU the batched decode throughput (6 iterations, full
  * batches of single-CB TBs per K) of candidate window counts for every CB
- * size, keep for each K the fastest whose windows are at least w_min
- * trellis steps long (0 = 32; smaller windows cost BLER), install the table
- * and copy it to P_by_k (188 entries, may be NULL).  At the kept window
- * count it also times the radix-4 forward recursion and installs the radix
- * table (4 where it is more than 1 % faster, else 2).  Blocking; takes a few
- * seconds; allocates device memory for its inputs and frees it. */
+ * size -- P = floor(K / w) in both CTA shapes and, for CB pairs, P = ceil(K /
+ * w) (windows filling the pair path's 8-step sub-windows), w in {32, 40,
+ * 48, 56, 64, 80, 96} -- keep for each K the longest windows (at least w_min
+ * trellis steps, 0 = 32; smaller windows cost BLER) within 1 % of the
+ * fastest candidate, install the table and copy it to P_by_k (188 entries,
+ * may be NULL).  At the kept window count it installs the faster shape in
+ * the shape table and times the radix-4 forward recursion, installing the
+ * radix table (4 where it is more than 1 % faster than both shapes, else 2).  Blocking; takes a few seconds; allocates device
+ * memory for its inputs and frees it. */
 int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k);
 
 /* ---- context ---------------------------------------------------------- */

@@ -74,7 +74,8 @@ class PlanInfo(ctypes.Structure):
                 ("llr_bytes", ctypes.c_uint64), ("out_bytes", ctypes.c_uint64),
                 ("info_bits", ctypes.c_uint64), ("trellis_steps", ctypes.c_uint64),
                 ("dbg_elems", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
-                ("grid", ctypes.c_uint32)]
+                ("grid", ctypes.c_uint32), ("pair_items", ctypes.c_uint32),
+                ("smem_bytes", ctypes.c_uint32)]
 
 
 _lib = None
@@ -109,6 +110,8 @@ SIGNATURES = {
     "crnt_tune_set": (ctypes.c_int, [_P, _U32]),
     "crnt_tune_radix_get": (ctypes.c_int, [_P, _U32]),
     "crnt_tune_radix_set": (ctypes.c_int, [_P, _U32]),
+    "crnt_tune_shape_get": (ctypes.c_int, [_P, _U32]),
+    "crnt_tune_shape_set": (ctypes.c_int, [_P, _U32]),
     "crnt_autotune": (ctypes.c_int, [_P, _U32, _P]),
 }
 
@@ -236,6 +239,20 @@ def tune_radix_set(table):
     """Install a forward-recursion radix table (188 entries, 0/2 = radix 2, 4)."""
     t = (ctypes.c_uint8 * NUM_K)(*table)
     _check(load().crnt_tune_radix_set(t, NUM_K), "crnt_tune_radix_set")
+
+
+def tune_shape_get():
+    """The process-wide CTA shape table (188 entries: 1 one CB per thread,
+    2 CB pairs in 16-bit lanes)."""
+    t = (ctypes.c_uint8 * NUM_K)()
+    _check(load().crnt_tune_shape_get(t, NUM_K), "crnt_tune_shape_get")
+    return list(t)
+
+
+def tune_shape_set(table):
+    """Install a CTA shape table (188 entries, 0/1 = one CB per thread, 2 = pairs)."""
+    t = (ctypes.c_uint8 * NUM_K)(*table)
+    _check(load().crnt_tune_shape_set(t, NUM_K), "crnt_tune_shape_set")
 
 
 class Context:

@@ -188,6 +188,9 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 std::atomic<uint8_t> g_tuned[lte::kNumK];
 // Process-wide forward-recursion radix per CB size (2 or 4; 0 reads as 2).
 std::atomic<uint8_t> g_radix[lte::kNumK];
+// Process-wide CTA shape per CB size: 1 = one CB per thread (windows across
+// the threads), 2 = CB pairs in 16-bit lanes; 0 reads as 1.
+std::atomic<uint8_t> g_shape[lte::kNumK];
 
 int tuned_p(int K) {
   const int ki = lte::index_of(K);
@@ -195,6 +198,13 @@ int tuned_p(int K) {
 }
 
 thread_local int t_radix_override = -1;
+thread_local int t_shape_override = -1;
+
+uint8_t shape_of(int K) {
+  if (t_shape_override > 0) return (uint8_t)t_shape_override;
+  const int ki = lte::index_of(K);
+  return ki >= 0 && g_shape[ki].load(std::memory_order_relaxed) == 2 ? 2 : 1;
+}
 
 // De-rate-matching map of CB size K with P windows and F filler bits: the
 // circular buffer w = [v0, interlace(v1, v2)] of TS 36.212 5.1.4.1 walked in
@@ -543,11 +553,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   pl->cb_tb.resize(ncb);
   pl->cb_r.resize(ncb);
 
-  // ---- pass 2: descriptors in sorted order, grouped into work items of
-  // equal (K, P), as many CBs as the CTA's threads and shared memory allow
-  int max_slot_bytes = 0;
-  WorkItem wi{0, 0, 0, 0};
-  int gmax = 0, iK = -1, iP = -1;
+  // ---- pass 2: descriptors in sorted order
   bool radix4_any = false, qtab_all = true;
   for (uint32_t i = 0; i < ncb; i++) {
     const uint32_t g = (uint32_t)(pl->keyed[i] & 0x1FFFFFF);
@@ -610,36 +616,63 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;
     pl->cb_r[i] = r;
+  }
+
+  // ---- pass 3: work items of equal (K, P).  A CB size whose shape-table
+  // entry is 2 forms CB pairs (two CBs on the same threads in 16-bit lanes,
+  // one pair slot) when every CB of the batch has its address tables (the
+  // pair kernel reads them) and the CB uses the radix-2 recursion; an odd
+  // CB left over runs alone.  Otherwise as many CBs as the CTA's threads
+  // and shared memory allow.
+  const bool allow_pairs = qtab_all && ncb > 1;
+  int max_item_bytes = 0;
+  bool pair_any = false;
+  WorkItem wi{0, 0, 0, 0};
+  int gmax = 0, iK = -1, iP = -1, islot = 0;
+  auto close_item = [&]() {
+    if (wi.mode == 1 && wi.n == 1) {
+      wi.mode = 0;
+      wi.smem_per_cb = islot;
+    }
+    pair_any |= wi.mode == 1;
+    max_item_bytes = std::max(max_item_bytes, wi.mode == 1 ? wi.smem_per_cb : wi.n * wi.smem_per_cb);
+    hi[pl->items.size()] = wi;
+    pl->items.push_back(wi);
+  };
+  for (uint32_t i = 0; i < ncb; i++) {
+    const CbDesc& d = hc[i];
     if (wi.n == 0 || wi.n >= gmax || d.K != iK || d.P != iP) {
-      if (wi.n) {
-        max_slot_bytes = std::max(max_slot_bytes, wi.n * wi.smem_per_cb);
-        hi[pl->items.size()] = wi;
-        pl->items.push_back(wi);
-      }
-      wi.cb0 = (int)i;
-      wi.n = 0;
-      wi.smem_per_cb = tm.slot;
-      wi.pad0 = 0;
-      gmax = std::max(1, std::min(kThreads / tm.P, kSmemBudget / tm.slot));
+      if (wi.n) close_item();
       iK = d.K;
       iP = d.P;
+      islot = align16(dec_cb_smem(d.K, d.P, d.W));
+      const int pslot = dec_pair_smem(d.K, d.P, d.W);
+      wi.cb0 = (int)i;
+      wi.n = 0;
+      if (allow_pairs && shape_of(d.K) == 2 && !d.radix4 && d.qt && pslot <= kSmemBudgetPair) {
+        wi.mode = 1;
+        wi.smem_per_cb = pslot;
+        gmax = 2;
+      } else {
+        wi.mode = 0;
+        wi.smem_per_cb = islot;
+        gmax = std::max(1, std::min(kThreads / d.P, kSmemBudget / islot));
+      }
     }
     wi.n++;
   }
-  if (wi.n) {
-    max_slot_bytes = std::max(max_slot_bytes, wi.n * wi.smem_per_cb);
-    hi[pl->items.size()] = wi;
-    pl->items.push_back(wi);
-  }
+  if (wi.n) close_item();
   pl->n_cb = ncb;
-  pl->smem = kSmemFixed + max_slot_bytes;
+  pl->smem = kSmemFixed + max_item_bytes;
   static std::mutex occ_mu;
-  static std::map<int, int> occ_cache;  // dynamic smem -> resident CTAs per SM
+  static std::map<int, int> occ_cache;  // (dynamic smem, kernel flags) -> resident CTAs per SM
   int per_sm;
   {
+    const int key = pl->smem * 8 + (radix4_any ? 1 : 0) + (qtab_all ? 2 : 0) + (pair_any ? 4 : 0);
     std::lock_guard<std::mutex> lk(occ_mu);
-    auto it = occ_cache.find(pl->smem);
-    if (it == occ_cache.end()) it = occ_cache.emplace(pl->smem, decode_occupancy(pl->smem)).first;
+    auto it = occ_cache.find(key);
+    if (it == occ_cache.end())
+      it = occ_cache.emplace(key, decode_occupancy(pl->smem, radix4_any, qtab_all, pair_any)).first;
     per_sm = it->second;
   }
   if (per_sm < 1) return CRNT_EDEVICE;
@@ -655,6 +688,9 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   inf.dbg_elems = (uint64_t)dbg_off;
   inf.n_items = (uint32_t)pl->items.size();
   inf.grid = (uint32_t)grid;
+  inf.pair_items = 0;
+  for (const WorkItem& w : pl->items) inf.pair_items += w.mode == 1 ? 1u : 0u;
+  inf.smem_bytes = (uint32_t)pl->smem;
 
   // ---- upload: descriptors, TB table, zeroed state and work items in one
   // copy (asynchronous on `stream`)
@@ -689,6 +725,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   p.mi_tab = ctx->mi_tab;
   p.radix4_any = radix4_any ? 1 : 0;
   p.qtab_all = qtab_all && ncb > 0 ? 1 : 0;
+  p.pair_any = pair_any ? 1 : 0;
   return CRNT_OK;
 }
 

@@ -11,9 +11,16 @@ namespace crnt {
 
 constexpr int kThreads = 128;          // threads per decode CTA
 constexpr int kCtasPerSm = 3;          // resident decode CTAs per SM (register-bound)
-constexpr int kSmemBudget = 72 * 1024; // dynamic smem per decode CTA
+constexpr int kSmemBudget = 72 * 1024; // dynamic smem per decode CTA (one CB per thread)
 constexpr int kMaxP = kThreads;        // windows per SISO pass (one thread each)
 constexpr int kSub = 4;                // sub-window length of the alpha recompute
+// CB pairs: one thread runs window p of two CBs of equal (K, P) in the two
+// 16-bit lanes of its registers.  Kernels that carry pair items hold two
+// CTAs per SM (up to 255 registers a thread) of at most kSmemBudgetPair
+// bytes each; the pair path checkpoints its forward metrics every kSubP steps.
+constexpr int kCtasPerSmPair = 2;
+constexpr int kSmemBudgetPair = 110 * 1024;
+constexpr int kSubP = 8;
 constexpr int kMaxK = 6144;
 // Fixed shared memory of a decode CTA ahead of the CB slots: the CRC24A /
 // CRC24B byte tables (2 x 256 words) and the mutual-information table (128
@@ -64,11 +71,12 @@ struct TbDesc {
 };
 
 // A work item: n consecutive CBs (sorted order) of equal K and P, decoded
-// together by one CTA.
+// together by one CTA.  mode 0: one CB per P threads (n <= kThreads / P);
+// mode 1: a CB pair (n = 2) in one pair slot, both CBs on the same P threads.
 struct WorkItem {
   int32_t cb0, n;
-  int32_t smem_per_cb;
-  int32_t pad0;
+  int32_t smem_per_cb;  // mode 0: bytes per CB slot; mode 1: bytes of the pair slot
+  int32_t mode;
 };
 
 // Per-batch device state written by the kernel.
@@ -101,6 +109,7 @@ struct DecParams {
   uint8_t* dbg_hard;      // optional: [sum K] hard decisions
   int32_t radix4_any;     // some CB selects the radix-4 forward recursion
   int32_t qtab_all;       // every CB has an interleaved-pass address table
+  int32_t pair_any;       // some work item is a CB pair (needs qtab_all)
 };
 
 // Encoder launch description: one CB per CTA.
@@ -125,10 +134,13 @@ struct EncParams {
   const uint32_t* xpowB;      // x^(32 s) mod gCRC24B
 };
 
-// Kernel launchers (decode.cu / encode.cu).
+// Kernel launchers (decode.cu / encode.cu).  The decode kernel instantiation
+// is chosen from p.radix4_any, p.qtab_all and p.pair_any.
 cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s);
 int decode_max_smem();
-int decode_occupancy(int smem);  // resident decode CTAs per SM at this smem
+// resident decode CTAs per SM at this dynamic smem, for the instantiation a
+// launch with these flags uses
+int decode_occupancy(int smem, bool radix4_any, bool qtab_all, bool pair_any);
 cudaError_t launch_encode(const EncParams& p, int n_cbs, cudaStream_t s);
 
 // Shared-memory bytes of one CB slot in the decode kernel.
@@ -144,6 +156,35 @@ __host__ __device__ inline int dec_cb_smem(int K, int P, int W) {
          + 4 * P * 16                   // alpha/beta seeds of both decoders
          + P * nck * 16                 // alpha checkpoints
          + 64;                          // per-CB flags
+}
+
+// Pair slot of two CBs of size K with P windows of W steps: the three
+// streams of both CBs interleaved byte by byte ([sys | par1 | par2], 2 W P
+// bytes each: byte 2 t + L holds CB L's element at transposed index t), the
+// extrinsics as 16-bit pairs (4 W P bytes), then per CB its tail LLRs, hard
+// decisions and boundary seeds, the checkpoints of the P threads (ceil(W /
+// kSubP) pairs of 8 packed registers each, 32 bytes) and per CB its flags.
+struct PairLayout {
+  int o_ext, o_tail, o_hard, hard_bytes, o_seed, seed_bytes, o_ck, ck_per_thread, o_flags, total;
+};
+__host__ __device__ inline PairLayout pair_layout(int K, int P, int W) {
+  PairLayout l;
+  const int tp = W * P;
+  const int nwords = (K + 31) / 32 + 1;
+  l.o_ext = align16(6 * tp);
+  l.o_tail = l.o_ext + align16(4 * tp);
+  l.o_hard = l.o_tail + 32;
+  l.hard_bytes = align16(4 * nwords);
+  l.o_seed = l.o_hard + 2 * l.hard_bytes;
+  l.seed_bytes = 4 * P * 16;
+  l.o_ck = l.o_seed + 2 * l.seed_bytes;
+  l.ck_per_thread = 32 * ((W + kSubP - 1) / kSubP);
+  l.o_flags = l.o_ck + P * l.ck_per_thread;
+  l.total = l.o_flags + 2 * 64;
+  return l;
+}
+__host__ __device__ inline int dec_pair_smem(int K, int P, int W) {
+  return align16(pair_layout(K, P, W).total);
 }
 
 }  // namespace crnt

@@ -290,6 +290,9 @@ __device__ __forceinline__ int qpp_at(int x, int f1, int f2, int K) {
 // mutual-information table, then the CB slots.
 extern __shared__ __align__(16) uint8_t smem[];
 
+// A CB's view of its shared-memory slot.  In a one-CB slot element t of a
+// stream or of the extrinsic sits at index t (str = 1); in a pair slot lane
+// L's element t sits at index 2 t (str = 2) of pointers offset by L.
 struct CbSlot {
   int8_t* sys;
   int8_t* par1;
@@ -298,11 +301,15 @@ struct CbSlot {
   int8_t* tail;
   uint32_t* hard;
   uint4* seed;   // [4][P]: alpha dec0, alpha dec1, beta dec0, beta dec1
-  uint4* ck;     // [P][nck]
+  uint4* ck;     // one-CB slot: [P][ceil(W / kSub)]; pair slot: per thread 2 ceil(W / kSubP)
   int* flags;    // [0] done, [1] iterations, [2] CB CRC, [3] TB CRC part, [4..5] max |Le|,
                  // [6] stopped by a purge, [7] window passes on the saturating path,
                  // [8] / [9] mutual information of this / the previous iteration
                  // (2^16 units per bit, summed over the CB), [10] iterations run
+  int str;       // index stride of sys / par1 / par2 / ext
+  int ck_stride; // uint4 of checkpoints per thread
+  int8_t* stage; // where the CB's received LLRs are staged before de-rate-matching
+  int stage_cap; // bytes available there (free until the first SISO pass)
 };
 __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) {
   CbSlot s;
@@ -324,6 +331,32 @@ __device__ __forceinline__ CbSlot make_slot(uint8_t* base, int K, int P, int W) 
   s.ck = (uint4*)q;
   q += P * nck * 16;
   s.flags = (int*)q;
+  s.str = 1;
+  s.ck_stride = nck;
+  s.stage = (int8_t*)s.seed;
+  s.stage_cap = 16 * P * (4 + nck);
+  return s;
+}
+// Lane L (0 or 1) of a pair slot (layout: pair_layout).  Both lanes share
+// the checkpoint area and the staging area (the seeds and checkpoints of both
+// CBs), which the pair's two CBs use one after the other.
+__device__ __forceinline__ CbSlot make_pair_slot(uint8_t* base, int K, int P, int W, int L) {
+  const PairLayout l = pair_layout(K, P, W);
+  const int tp = W * P;
+  CbSlot s;
+  s.sys = (int8_t*)base + L;
+  s.par1 = (int8_t*)base + 2 * tp + L;
+  s.par2 = (int8_t*)base + 4 * tp + L;
+  s.ext = (int16_t*)(base + l.o_ext) + L;
+  s.tail = (int8_t*)(base + l.o_tail + 16 * L);
+  s.hard = (uint32_t*)(base + l.o_hard + l.hard_bytes * L);
+  s.seed = (uint4*)(base + l.o_seed + l.seed_bytes * L);
+  s.ck = (uint4*)(base + l.o_ck);
+  s.flags = (int*)(base + l.o_flags + 64 * L);
+  s.str = 2;
+  s.ck_stride = l.ck_per_thread / 16;
+  s.stage = (int8_t*)(base + l.o_seed);
+  s.stage_cap = l.o_flags - l.o_seed;
   return s;
 }
 // transposed shared-memory index of natural position q < K
@@ -361,6 +394,9 @@ __device__ __forceinline__ uint32_t crc_word(uint32_t r, uint32_t w, const uint3
 // and writes the result to its d-stream (and back to the soft buffer).
 // The received LLRs e are read from `e`: the CB's LLRs in global memory, or
 // their copy staged in shared memory by stage_llrs.
+// STR: the slot's index stride (1 one-CB slot, 2 lane of a pair slot; the
+// caller zeroes a pair slot's extrinsics).
+template <int STR>
 __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
                         int8_t* __restrict__ soft_arena, int tid, int nthr) {
   // descriptor fields in registers: the shared-memory stores below go
@@ -394,7 +430,7 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
       int acc = combine ? soft[pos] : 0;
       for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
       const int8_t v = (int8_t)acc;
-      if (dst < tp3) base[dst] = v;
+      if (dst < tp3) base[STR * dst] = v;  // streams are contiguous: s tp + t -> STR (s tp + t)
       else sl.tail[dst - tp3] = v;
       if (soft) soft[pos] = v;
     }
@@ -412,7 +448,7 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
           int acc = combine ? soft[p] : 0;
           for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
           const int8_t v = (int8_t)acc;
-          if (di < K) streams[st][tr(di)] = v;
+          if (di < K) streams[st][STR * tr(di)] = v;
           else sl.tail[3 * (di - K) + st] = v;
           if (soft) soft[p] = v;
         },
@@ -429,12 +465,14 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
   // filler: known zero bits in the systematic stream, unknown parity 1
   for (int k = tid; k < F; k += nthr) {
     const int t = tr(k);
-    sl.sys[t] = 127;
-    sl.par1[t] = 0;
+    sl.sys[STR * t] = 127;
+    sl.par1[STR * t] = 0;
   }
-  const int tp = W * P;
-  uint4* ext16 = (uint4*)sl.ext;  // the ext area is 16-byte aligned and padded
-  for (int k = tid; k < (2 * tp + 15) / 16; k += nthr) ext16[k] = make_uint4(0, 0, 0, 0);
+  if (STR == 1) {
+    const int tp = W * P;
+    uint4* ext16 = (uint4*)sl.ext;  // the ext area is 16-byte aligned and padded
+    for (int k = tid; k < (2 * tp + 15) / 16; k += nthr) ext16[k] = make_uint4(0, 0, 0, 0);
+  }
   if (tid == 0) {
     sl.flags[0] = 0;
     sl.flags[1] = 0;
@@ -461,9 +499,8 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
 __device__ __forceinline__ const int8_t* llr_src(const CbDesc& d, const CbSlot& sl,
                                                  const int8_t* llr) {
   const int8_t* e = llr + d.llr_off;
-  const int cap = 16 * d.P * (4 + (d.W + kSub - 1) / kSub);
-  if (d.E + 15 > cap) return e;
-  return (const int8_t*)sl.seed + ((uintptr_t)e & 15u);
+  if (d.E + 15 > sl.stage_cap) return e;
+  return (const int8_t*)sl.stage + ((uintptr_t)e & 15u);
 }
 __device__ void stage_llrs(const CbDesc& d, const CbSlot& sl, const int8_t* __restrict__ llr,
                            int tid, int nthr) {
@@ -472,7 +509,7 @@ __device__ void stage_llrs(const CbDesc& d, const CbSlot& sl, const int8_t* __re
   const int8_t* src = llr_src(d, sl, llr);
   if (src == e) return;
   const int s0 = (int)((uintptr_t)e & 15u);
-  int8_t* st = (int8_t*)sl.seed + s0;
+  int8_t* st = sl.stage + s0;
   const int head = min(E, (16 - s0) & 15);
   const int n16 = (E - head) >> 4;
   const int tail0 = head + 16 * n16;
@@ -521,7 +558,8 @@ __device__ __forceinline__ int tr_w(const Win& w, int q) {
 // DEC 1 walks the QPP addresses (q, dq) and returns the natural position;
 // with QT the caller passes the step's transposed address tq, read from the
 // CB's address table, and q, dq are not used.
-template <int DEC, bool QT>
+// STR: index stride of the slot (2 when the window is one lane of a pair slot).
+template <int DEC, bool QT, int STR = 1>
 __device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, int tq, int& S,
                                           int& Lp, int& t) {
   const int idx = j * w.P + w.p;
@@ -532,8 +570,8 @@ __device__ __forceinline__ void load_step(const Win& w, int j, int& q, int& dq, 
   } else {
     t = tr_w(w, q);
   }
-  S = (int)w.sys[t] + (int)w.ext[t];
-  Lp = w.par[idx];
+  S = (int)w.sys[STR * t] + (int)w.ext[STR * t];
+  Lp = w.par[STR * idx];
   if (DEC == 1 && !QT) {
     q = modadd(q, dq, w.K);
     dq = modadd(dq, w.f2x2, w.K);
@@ -559,7 +597,7 @@ __device__ __forceinline__ int comp2(const uint2& e, int k) {
 // hard decisions, 1: hard decisions, 2: read w.hard_on).  QT (DEC 1): te
 // holds the sub-window's four transposed addresses and qe (with hard
 // decisions) their natural positions.
-template <int DEC, bool FULL, bool CHK, bool QT, int HM>
+template <int DEC, bool FULL, bool CHK, bool QT, int HM, int STR = 1>
 __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, int slen, int q,
                                                 int dq, uint4 te, uint2 qe, int b[8], int& mx,
                                                 int& mn) {
@@ -572,7 +610,7 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
     if (FULL || jj < slen) {
       if (!QT) Qv[jj] = q;
       int t;
-      load_step<DEC, QT>(w, j0 + jj, q, dq, QT ? comp4(te, jj) : 0, Sv[jj], Lv[jj], t);
+      load_step<DEC, QT, STR>(w, j0 + jj, q, dq, QT ? comp4(te, jj) : 0, Sv[jj], Lv[jj], t);
       if (QT) Qv[jj] = t;
       if (jj + 1 < kSub && (FULL || jj + 1 < slen))
         alpha_step<CHK>(A[jj], A[jj + 1], Sv[jj], Sv[jj] + Lv[jj], Lv[jj]);
@@ -591,7 +629,8 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
         mx = __vimax3_s32(mx, vprev, v);
         mn = __vimin3_s32(mn, vprev, v);
       }
-      w.ext[DEC == 0 ? (j0 + jj) * w.P + w.p : QT ? Qv[jj] : tr_w(w, Qv[jj])] = (int16_t)v;
+      w.ext[STR * (DEC == 0 ? (j0 + jj) * w.P + w.p : QT ? Qv[jj] : tr_w(w, Qv[jj]))] =
+          (int16_t)v;
       if (DEC == 1 && (HM == 1 || (HM == 2 && w.hard_on))) {  // ORs a zero when lam >= 0
         const int qq = (QT ? comp2(qe, jj) : Qv[jj]) + w.pad;
         atomicOr(&w.hard[qq >> 5], ((unsigned)lam >> 31) << (31 - (qq & 31)));
@@ -611,7 +650,7 @@ __device__ __forceinline__ void sub_window_back(const Win& w, uint4 ck, int j0, 
 // 0 and 1 (pf0, pf1) before the pass's barrier, then two groups ahead in the
 // forward pass and one sub-window ahead in the backward pass, whose first
 // group is fetched before the forward pass.
-template <int DEC, bool CHK, bool R4, bool QT>
+template <int DEC, bool CHK, bool R4, bool QT, int STR = 1>
 __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restrict__ dp,
                                             uint4* ck, uint4* seedA, uint4* seedB, int a[8],
                                             int b[8], int& mx, int& mn, uint4 pf0, uint4 pf1) {
@@ -646,11 +685,11 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
 #pragma unroll
       for (int jj = 0; jj < kSub; jj += 4) {
         int S0, L0, S1, L1, t, o[8];
-        load_step<DEC, TQ>(w, j0 + jj, q, dq, comp4(cur, jj), S0, L0, t);
-        load_step<DEC, TQ>(w, j0 + jj + 1, q, dq, comp4(cur, jj + 1), S1, L1, t);
+        load_step<DEC, TQ, STR>(w, j0 + jj, q, dq, comp4(cur, jj), S0, L0, t);
+        load_step<DEC, TQ, STR>(w, j0 + jj + 1, q, dq, comp4(cur, jj + 1), S1, L1, t);
         alpha_step_r4(a, o, S0, L0, S1, L1);
-        load_step<DEC, TQ>(w, j0 + jj + 2, q, dq, comp4(cur, jj + 2), S0, L0, t);
-        load_step<DEC, TQ>(w, j0 + jj + 3, q, dq, comp4(cur, jj + 3), S1, L1, t);
+        load_step<DEC, TQ, STR>(w, j0 + jj + 2, q, dq, comp4(cur, jj + 2), S0, L0, t);
+        load_step<DEC, TQ, STR>(w, j0 + jj + 3, q, dq, comp4(cur, jj + 3), S1, L1, t);
         alpha_step_r4(o, a, S0, L0, S1, L1);
       }
     }
@@ -665,9 +704,9 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
 #pragma unroll
       for (int jj = 0; jj < kSub; jj += 2) {
         int S, Lp, t, o[8];
-        load_step<DEC, TQ>(w, j0 + jj, q, dq, comp4(cur, jj), S, Lp, t);
+        load_step<DEC, TQ, STR>(w, j0 + jj, q, dq, comp4(cur, jj), S, Lp, t);
         alpha_step<CHK>(a, o, S, S + Lp, Lp);
-        load_step<DEC, TQ>(w, j0 + jj + 1, q, dq, comp4(cur, jj + 1), S, Lp, t);
+        load_step<DEC, TQ, STR>(w, j0 + jj + 1, q, dq, comp4(cur, jj + 1), S, Lp, t);
         alpha_step<CHK>(o, a, S, S + Lp, Lp);
       }
     }
@@ -676,7 +715,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
     ck[j0 / kSub] = pack_norm<CHK>(a);
     for (int j = j0; j < len; j++) {
       int S, Lp, t, o[8];
-      load_step<DEC, TQ>(w, j, q, dq, TQ ? comp4(te, j - j0) : 0, S, Lp, t);
+      load_step<DEC, TQ, STR>(w, j, q, dq, TQ ? comp4(te, j - j0) : 0, S, Lp, t);
       alpha_step<CHK>(a, o, S, S + Lp, Lp);
 #pragma unroll
       for (int s = 0; s < 8; s++) a[s] = o[s];
@@ -708,7 +747,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
       te = __ldg(tq + max(sw - 1, 0) * P);
       if (w.hard_on) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
     }
-    sub_window_back<DEC, false, CHK, TQ, 2>(w, ck[sw], kSub * sw, last_len, pis, dls, cur, qcur,
+    sub_window_back<DEC, false, CHK, TQ, 2, STR>(w, ck[sw], kSub * sw, last_len, pis, dls, cur, qcur,
                                             b, mx, mn);
     if (DEC == 1 && !TQ) {
       pis = modsub(pis, jmp, K);
@@ -728,7 +767,7 @@ __device__ __forceinline__ void window_pass(const Win& w, const CbDesc* __restri
         te = __ldg(tq + max(sw - 1, 0) * P);
         if (HM == 1) qn = __ldg(w.qq + max(sw - 1, 0) * P + p);
       }
-      sub_window_back<DEC, true, CHK, TQ, HM>(w, ck[sw], kSub * sw, kSub, pis, dls, cur, qcur, b,
+      sub_window_back<DEC, true, CHK, TQ, HM, STR>(w, ck[sw], kSub * sw, kSub, pis, dls, cur, qcur, b,
                                               mx, mn);
       if (DEC == 1 && !TQ) {
         pis = modsub(pis, jmp, K);
@@ -859,12 +898,770 @@ __device__ uint32_t crc_share(const CbDesc& d, const CbSlot& sl, int p, const ui
   return after ? gf_mulmod(r, __ldg(&xpow[after]), g) : r;
 }
 
+// ---------------------------------------------------------------- CB pairs
+// A thread of a pair item runs window p of two CBs of equal (K, P) at once:
+// CB A in the low and CB B in the high 16-bit lane of each register, every
+// add-max a DPX s16x2 instruction.  Both CBs' streams and extrinsics are
+// interleaved in the pair slot, so one load serves both lanes, and the
+// interleaved pass's addresses (equal for both) come from one table read.
+// The lanes hold metrics relative to state 0 of the last normalisation,
+// which happens every kSubP steps (checkpoints in the forward pass, sub-
+// window ends in the backward pass).  pair_fast proves, per lane, that the
+// pass is clamp-free (window_fast) and that no lane value leaves int16, so
+// the results equal the one-CB path's exactly; otherwise (and for a CB whose
+// partner has stopped) each lane runs the one-CB code on its stride-2 view.
+
+__device__ __forceinline__ unsigned prmt(unsigned a, unsigned b, unsigned sel) {
+  unsigned d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+// the two bytes of x's low half, sign-extended into the two 16-bit lanes
+__device__ __forceinline__ unsigned sext8x2(unsigned x) { return prmt(x, 0u, 0x9180u); }
+__device__ __forceinline__ int lane_lo(unsigned x) { return (int)(short)(x & 0xFFFFu); }
+__device__ __forceinline__ int lane_hi(unsigned x) { return (int)x >> 16; }
+__device__ __forceinline__ unsigned pack_lanes(int lo, int hi) {
+  return prmt((unsigned)lo, (unsigned)hi, 0x5410u);
+}
+
+__device__ __forceinline__ unsigned gval_p(int code, unsigned S, unsigned T, unsigned L) {
+  return code == 3 ? T : code == 2 ? S : code == 1 ? L : 0u;
+}
+__device__ __forceinline__ unsigned acs_p(unsigned x0, int c0, unsigned x1, int c1, unsigned S,
+                                          unsigned T, unsigned L) {
+  if (c1 == 0) return __viaddmax_s16x2(x0, gval_p(c0, S, T, L), x1);
+  if (c0 == 0) return __viaddmax_s16x2(x1, gval_p(c1, S, T, L), x0);
+  return __viaddmax_s16x2(x0, gval_p(c0, S, T, L), __vadd2(x1, gval_p(c1, S, T, L)));
+}
+__device__ __forceinline__ void alpha_step_p(const unsigned a[8], unsigned o[8], unsigned S,
+                                             unsigned L) {
+  const unsigned T = __vadd2(S, L);
+#pragma unroll
+  for (int n = 0; n < 8; n++)
+    o[n] = acs_p(a[pred(n, 0)], pcode(n, 0), a[pred(n, 1)], pcode(n, 1), S, T, L);
+}
+__device__ __forceinline__ void beta_step_p(unsigned b[8], unsigned S, unsigned L) {
+  const unsigned T = __vadd2(S, L);
+  unsigned m[8];
+#pragma unroll
+  for (int s = 0; s < 8; s++)
+    m[s] = acs_p(b[nxt(s, 0)], gcode(s, 0), b[nxt(s, 1)], gcode(s, 1), S, T, L);
+#pragma unroll
+  for (int s = 0; s < 8; s++) b[s] = m[s];
+}
+// subtract each lane's state-0 metric (a constant per lane: exact here)
+__device__ __forceinline__ void norm_p(unsigned v[8]) {
+#pragma unroll
+  for (int s = 1; s < 8; s++) v[s] = __vsub2(v[s], v[0]);
+  v[0] = 0u;
+}
+// Le of both lanes (Lambda - S, exact); Lambda = S + Le.
+__device__ __forceinline__ unsigned app_step_p(const unsigned a[8], const unsigned b[8], unsigned L) {
+  unsigned acc[4];
+  bool first[4] = {true, true, true, true};
+#pragma unroll
+  for (int s = 0; s < 8; s++)
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int c = gcode(s, u);
+      const int n = nxt(s, u);
+      if (first[c]) {
+        acc[c] = __vadd2(a[s], b[n]);
+        first[c] = false;
+      } else {
+        acc[c] = __viaddmax_s16x2(a[s], b[n], acc[c]);
+      }
+    }
+  return __vsub2(__viaddmax_s16x2(acc[3], L, acc[2]), __viaddmax_s16x2(acc[1], L, acc[0]));
+}
+
+// Largest |metric - metric of state 0 at the last normalisation| a lane can
+// reach within kSubP steps of a normalisation, from start metrics v (offset
+// form), |branch metric| <= g.  Within the sub-window that starts at the
+// window's start: upward at most the start maximum + 8 g; downward the start
+// minimum - 2 g for the first two steps, after which every state lies within
+// 3 g of the best one (each state pair is joined by one 3-step path), so at
+// least -11 g.  Sub-windows that start 3 or more steps into the window: 11 g.
+// short_first: the recursion normalises after only 1 or 2 steps (the
+// backward pass when the window's last sub-window is that short); the next
+// sub-window then starts with a spread of at most spread + 2 g, so it reaches
+// spread + 10 g.
+__device__ __forceinline__ int lane_reach(const int v[8], int g, bool short_first) {
+  const int hi = max8(v) - v[0], lo = v[0] - min8(v);
+  int r = max(max(hi + kSubP * g, lo + 2 * g), (kSubP + 3) * g);
+  if (short_first) r = max(r, hi + lo + (kSubP + 2) * g);
+  return r;
+}
+// The pass of one lane may run on 16-bit lanes: clamp-free (window_fast) and
+// every alpha + beta + Lp sum of Lambda within int16.  len: the window's steps.
+__device__ __forceinline__ bool pair_fast(const int a[8], const int b[8], int g, int len) {
+  const int last = len - kSubP * ((len - 1) / kSubP);
+  const bool short_first = len > kSubP && last < 3;
+  return window_fast(a, b, g) &&
+         lane_reach(a, g, false) + lane_reach(b, g, short_first) + g <= 32767;
+}
+
+// offset-form metrics of lanes A and B -> signed 16-bit lane pairs
+__device__ __forceinline__ void to_lanes(const int vA[8], const int vB[8], unsigned o[8]) {
+#pragma unroll
+  for (int s = 0; s < 8; s++) o[s] = pack_lanes(vA[s], vB[s]) ^ 0x80008000u;
+}
+// normalised lane pairs -> the two CBs' stored boundary metrics (offset form,
+// as pack_norm writes them)
+__device__ __forceinline__ void store_lanes(unsigned v[8], uint4* dA, uint4* dB) {
+  norm_p(v);
+  unsigned x[8];
+#pragma unroll
+  for (int s = 0; s < 8; s++) x[s] = v[s] ^ 0x80008000u;
+  *dA = make_uint4(prmt(x[0], x[1], 0x5410u), prmt(x[2], x[3], 0x5410u), prmt(x[4], x[5], 0x5410u),
+                   prmt(x[6], x[7], 0x5410u));
+  *dB = make_uint4(prmt(x[0], x[1], 0x7632u), prmt(x[2], x[3], 0x7632u), prmt(x[4], x[5], 0x7632u),
+                   prmt(x[6], x[7], 0x7632u));
+}
+
+struct WinP {
+  const uint16_t* __restrict__ sys;  // [transposed index]: sys of A | sys of B << 8
+  const uint16_t* __restrict__ par;  // [window index]: the pass's parity LLRs, A | B << 8
+  uint32_t* ext;                     // [transposed index]: a-priori of A | of B << 16
+  uint32_t* hardA;
+  uint32_t* hardB;
+  const uint4* __restrict__ qt;      // interleaved-pass address groups (DEC 1)
+  const uint2* __restrict__ qq;      // their natural positions
+  int P, p, len, pad, ng;            // ng: groups of 4 steps in the table (incl. 2 zero groups)
+};
+
+template <int DEC>
+__device__ __forceinline__ void load_step_p(const WinP& w, int j, int tq, unsigned& S,
+                                            unsigned& L, int& t) {
+  const int idx = j * w.P + w.p;
+  t = DEC == 0 ? idx : tq;
+  S = __vadd2(sext8x2(w.sys[t]), w.ext[t]);
+  L = sext8x2(w.par[idx]);
+}
+
+__device__ __forceinline__ int comp8(const uint4& g0, const uint4& g1, int jj) {
+  return comp4(jj < 4 ? g0 : g1, jj & 3);
+}
+__device__ __forceinline__ int comp8q(const uint2& q0, const uint2& q1, int jj) {
+  return comp2(jj < 4 ? q0 : q1, jj & 3);
+}
+
+// Backward processing of sub-window [j0, j0 + slen) of the pair: forward
+// metrics recomputed from the checkpoint, then Lambda / Le / beta walking
+// back.  HM: hard decisions of both lanes (DEC 1).
+template <int DEC, bool FULL, int HM>
+__device__ __forceinline__ void sub_window_back_p(const WinP& w, const uint4* ck, int j0, int slen,
+                                                  uint4 g0, uint4 g1, uint2 q0, uint2 q1,
+                                                  unsigned b[8], unsigned& mx, unsigned& mn) {
+  unsigned A[kSubP][8];
+  unsigned Sv[kSubP], Lv[kSubP];
+  int Tv[kSubP];
+  unsigned vprev = 0u;
+  {
+    const uint4 c0 = ck[0], c1 = ck[1];
+    A[0][0] = c0.x; A[0][1] = c0.y; A[0][2] = c0.z; A[0][3] = c0.w;
+    A[0][4] = c1.x; A[0][5] = c1.y; A[0][6] = c1.z; A[0][7] = c1.w;
+  }
+#pragma unroll
+  for (int jj = 0; jj < kSubP; jj++) {
+    if (FULL || jj < slen) {
+      load_step_p<DEC>(w, j0 + jj, DEC ? comp8(g0, g1, jj) : 0, Sv[jj], Lv[jj], Tv[jj]);
+      if (jj + 1 < kSubP && (FULL || jj + 1 < slen)) alpha_step_p(A[jj], A[jj + 1], Sv[jj], Lv[jj]);
+    }
+  }
+#pragma unroll
+  for (int jj = kSubP - 1; jj >= 0; jj--) {
+    if (FULL || jj < slen) {
+      const unsigned d = app_step_p(A[jj], b, Lv[jj]);
+      const int lo = lane_lo(d), hi = lane_hi(d);
+      const unsigned v = pack_lanes(scale_ext(lo), scale_ext(hi));
+      if (jj & 1) {
+        vprev = v;
+      } else {
+        mx = __vimax3_s16x2(mx, vprev, v);
+        mn = __vimin3_s16x2(mn, vprev, v);
+      }
+      w.ext[Tv[jj]] = v;
+      if (DEC == 1 && HM) {  // ORs a zero where Lambda >= 0
+        const unsigned lam = __vadd2(Sv[jj], d);
+        const int q = comp8q(q0, q1, jj) + w.pad;
+        const unsigned bit = 31u - (unsigned)(q & 31);
+        atomicOr(&w.hardA[q >> 5], ((lam >> 15) & 1u) << bit);
+        atomicOr(&w.hardB[q >> 5], (lam >> 31) << bit);
+      }
+      beta_step_p(b, Sv[jj], Lv[jj]);
+    }
+  }
+  norm_p(b);
+}
+
+// Both recursions of window p for the pair (start metrics a, b as lane
+// pairs, normalised).  Writes the checkpoints (thread-private ck), the
+// extrinsics, the hard decisions (HM), the boundary metrics of both CBs and
+// the packed max / min of the extrinsics written.
+template <int DEC, int HM>
+__device__ __forceinline__ void window_pass_p(const WinP& w, uint4* ck, unsigned a[8], unsigned b[8],
+                                              uint4* seedA_A, uint4* seedA_B, uint4* seedB_A,
+                                              uint4* seedB_B, unsigned& mx, unsigned& mn,
+                                              uint4 pf0, uint4 pf1) {
+  const int P = w.P, p = w.p, len = w.len;
+  const uint4* __restrict__ tq = DEC ? w.qt + p : nullptr;  // group g at tq[g * P]
+  const int nsub = (len + kSubP - 1) / kSubP;
+  const int glast = w.ng - 1;
+  // ---- forward, normalised and checkpointed every kSubP steps
+  uint4 g0 = pf0, g1 = pf1;
+#pragma unroll 1
+  for (int sw = 0; sw < nsub; sw++) {
+    norm_p(a);
+    ck[2 * sw] = make_uint4(a[0], a[1], a[2], a[3]);
+    ck[2 * sw + 1] = make_uint4(a[4], a[5], a[6], a[7]);
+    const uint4 c0 = g0, c1 = g1;
+    if (DEC) {  // the next sub-window's two groups, fetched one sub-window ahead
+      g0 = __ldg(tq + min(2 * sw + 2, glast) * P);
+      g1 = __ldg(tq + min(2 * sw + 3, glast) * P);
+    }
+    const int j0 = kSubP * sw;
+    if (j0 + kSubP <= len) {
+#pragma unroll
+      for (int jj = 0; jj < kSubP; jj += 2) {
+        unsigned S, L, o[8];
+        int t;
+        load_step_p<DEC>(w, j0 + jj, DEC ? comp8(c0, c1, jj) : 0, S, L, t);
+        alpha_step_p(a, o, S, L);
+        load_step_p<DEC>(w, j0 + jj + 1, DEC ? comp8(c0, c1, jj + 1) : 0, S, L, t);
+        alpha_step_p(o, a, S, L);
+      }
+    } else {
+      for (int j = j0; j < len; j++) {
+        unsigned S, L, o[8];
+        int t;
+        load_step_p<DEC>(w, j, DEC ? comp8(c0, c1, j - j0) : 0, S, L, t);
+        alpha_step_p(a, o, S, L);
+#pragma unroll
+        for (int s = 0; s < 8; s++) a[s] = o[s];
+      }
+    }
+  }
+  if (p + 1 < P) store_lanes(a, seedA_A + p + 1, seedA_B + p + 1);
+  // ---- backward, one sub-window at a time from the end
+  int sw = nsub - 1;
+  uint4 t0 = make_uint4(0u, 0u, 0u, 0u), t1 = t0;
+  uint2 n0 = make_uint2(0u, 0u), n1 = n0;
+  if (DEC) {
+    t0 = __ldg(tq + (2 * sw) * P);
+    t1 = __ldg(tq + (2 * sw + 1) * P);
+    if (HM) {
+      n0 = __ldg(w.qq + (2 * sw) * P + p);
+      n1 = __ldg(w.qq + (2 * sw + 1) * P + p);
+    }
+  }
+  const int last_len = len - kSubP * sw;
+  if (last_len < kSubP) {
+    const uint4 c0 = t0, c1 = t1;
+    const uint2 m0 = n0, m1 = n1;
+    if (DEC) {
+      const int gs = 2 * max(sw - 1, 0);
+      t0 = __ldg(tq + gs * P);
+      t1 = __ldg(tq + (gs + 1) * P);
+      if (HM) {
+        n0 = __ldg(w.qq + gs * P + p);
+        n1 = __ldg(w.qq + (gs + 1) * P + p);
+      }
+    }
+    sub_window_back_p<DEC, false, HM>(w, ck + 2 * sw, kSubP * sw, last_len, c0, c1, m0, m1, b, mx,
+                                      mn);
+    sw--;
+  }
+#pragma unroll 1
+  for (; sw >= 0; sw--) {
+    const uint4 c0 = t0, c1 = t1;
+    const uint2 m0 = n0, m1 = n1;
+    if (DEC) {
+      const int gs = 2 * max(sw - 1, 0);
+      t0 = __ldg(tq + gs * P);
+      t1 = __ldg(tq + (gs + 1) * P);
+      if (HM) {
+        n0 = __ldg(w.qq + gs * P + p);
+        n1 = __ldg(w.qq + (gs + 1) * P + p);
+      }
+    }
+    sub_window_back_p<DEC, true, HM>(w, ck + 2 * sw, kSubP * sw, kSubP, c0, c1, m0, m1, b, mx, mn);
+  }
+  if (p > 0) store_lanes(b, seedB_A + p - 1, seedB_B + p - 1);
+}
+
+// Start metrics of window p of one CB for a pass, as siso_pass reads them
+// but kept packed (offset form, pack8 layout): alpha from the known start,
+// zeros or the stored seed; beta likewise (the tail steps follow after the
+// barrier).  Clears the flag this pass writes and, for a checked pass, the
+// hard decisions.  Runs before the pass's barrier: other threads overwrite
+// the seeds during the pass.
+__device__ __forceinline__ uint4 start_init(int p, int first_p, bool first, const uint4* seed) {
+  const unsigned z = (unsigned)OFF | ((unsigned)OFF << 16);
+  if (p == first_p) {
+    const unsigned m = (unsigned)MINF_OFF | ((unsigned)MINF_OFF << 16);
+    return make_uint4((unsigned)OFF | ((unsigned)MINF_OFF << 16), m, m, m);
+  }
+  if (first) return make_uint4(z, z, z, z);
+  return seed[p];
+}
+template <int DEC>
+__device__ __forceinline__ void pass_start_p(const CbSlot& sl, int K, int P, int p, bool first,
+                                             bool hard, uint4& a, uint4& b, int& m_in) {
+  a = start_init(p, 0, first, sl.seed + DEC * P);
+  b = start_init(p, P - 1, first, sl.seed + (2 + DEC) * P);
+  m_in = sl.flags[5 - DEC];
+  if (p == 0) sl.flags[4 + DEC] = 0;  // written by this pass after the barrier
+  if (DEC == 1 && hard) {
+    const int nwords = (K + 31) / 32;
+    for (int w = p; w < nwords; w += P) sl.hard[w] = 0u;
+  }
+}
+
+// packed start metrics (offset form) -> int[8] with the tail steps of the
+// last window applied
+template <int DEC>
+__device__ __forceinline__ void lane_start(uint4 pa, uint4 pb, const int8_t* tail, bool last,
+                                           int a[8], int b[8]) {
+  unpack8(pa, a);
+  unpack8(pb, b);
+  if (last) {
+    const int8_t* t = tail + (DEC ? 6 : 0);
+#pragma unroll
+    for (int j = 2; j >= 0; j--) beta_tail_step(b, t[2 * j], t[2 * j + 1]);
+  }
+}
+
+// One lane of a pair slot through the one-CB code (stride-2 view): the
+// fallback when pair_fast fails, and the path of a CB whose partner stopped.
+// pa, pb: the lane's packed start metrics.  Not inlined: the pass gets its
+// own register allocation, apart from the item loop around it.
+template <int DEC>
+__device__ __noinline__ void lane_pass(const CbDesc* __restrict__ dp, uint8_t* base, int L, int p,
+                                       bool hard, uint4 pa, uint4 pb, int m_in, uint4 pf0,
+                                       uint4 pf1) {
+  const int K = dp->K, P = dp->P, W = dp->W;
+  const CbSlot sl = make_pair_slot(base, K, P, W, L);
+  int a[8], b[8];
+  lane_start<DEC>(pa, pb, sl.tail, p == P - 1, a, b);
+  Win w;
+  w.sys = sl.sys;
+  w.par = DEC ? sl.par2 : sl.par1;
+  w.ext = sl.ext;
+  w.hard = sl.hard;
+  w.hard_on = hard;
+  w.r4 = false;
+  w.qt = dp->qt;
+  w.qq = dp->qq;
+  w.K = K;
+  w.P = P;
+  w.W = W;
+  w.divM = dp->divM;
+  w.divS = dp->divS;
+  w.f2x2 = dp->f2x2;
+  w.p = p;
+  w.lo = p * W;
+  w.len = min(W, K - w.lo);
+  w.pad = ((K + 31) / 32) * 32 - K;
+  uint4* ck = sl.ck + p * sl.ck_stride;
+  uint4* seedA = sl.seed + DEC * P;
+  uint4* seedB = sl.seed + (2 + DEC) * P;
+  int mx = 0, mn = 0;
+  if (window_fast(a, b, 254 + m_in)) {
+    window_pass<DEC, false, false, true, 2>(w, dp, ck, seedA, seedB, a, b, mx, mn, pf0, pf1);
+  } else {
+    window_pass<DEC, true, false, true, 2>(w, dp, ck, seedA, seedB, a, b, mx, mn, pf0, pf1);
+    atomicAdd(&sl.flags[7], 1);
+  }
+  atomicMax(&sl.flags[4 + DEC], max(mx, -mn));
+}
+
+// The pass of window p of both lanes on 16-bit lanes (pair_fast holds for
+// both).  paX / pbX: packed start metrics of lane X (tail steps done).  Not
+// inlined: inside the item loop the inlined pass spills (measured slower).
+template <int DEC, int HM>
+__device__ __noinline__ void pair_pass(const CbDesc* __restrict__ dA, uint8_t* base, int p,
+                                       uint4 paA, uint4 pbA, uint4 paB, uint4 pbB, uint4 pf0,
+                                       uint4 pf1) {
+  const int K = dA->K, P = dA->P, W = dA->W;
+  const PairLayout l = pair_layout(K, P, W);
+  WinP w;
+  w.sys = (const uint16_t*)base;
+  w.par = (const uint16_t*)(base + (DEC ? 4 : 2) * W * P);
+  w.ext = (uint32_t*)(base + l.o_ext);
+  w.hardA = (uint32_t*)(base + l.o_hard);
+  w.hardB = (uint32_t*)(base + l.o_hard + l.hard_bytes);
+  w.qt = dA->qt;
+  w.qq = dA->qq;
+  w.P = P;
+  w.p = p;
+  w.len = min(W, K - p * W);
+  w.pad = ((K + 31) / 32) * 32 - K;
+  w.ng = (W + kSub - 1) / kSub + 2;
+  unsigned a[8], b[8];
+  a[0] = prmt(paA.x, paB.x, 0x5410u); a[1] = prmt(paA.x, paB.x, 0x7632u);
+  a[2] = prmt(paA.y, paB.y, 0x5410u); a[3] = prmt(paA.y, paB.y, 0x7632u);
+  a[4] = prmt(paA.z, paB.z, 0x5410u); a[5] = prmt(paA.z, paB.z, 0x7632u);
+  a[6] = prmt(paA.w, paB.w, 0x5410u); a[7] = prmt(paA.w, paB.w, 0x7632u);
+  b[0] = prmt(pbA.x, pbB.x, 0x5410u); b[1] = prmt(pbA.x, pbB.x, 0x7632u);
+  b[2] = prmt(pbA.y, pbB.y, 0x5410u); b[3] = prmt(pbA.y, pbB.y, 0x7632u);
+  b[4] = prmt(pbA.z, pbB.z, 0x5410u); b[5] = prmt(pbA.z, pbB.z, 0x7632u);
+  b[6] = prmt(pbA.w, pbB.w, 0x5410u); b[7] = prmt(pbA.w, pbB.w, 0x7632u);
+#pragma unroll
+  for (int s = 0; s < 8; s++) {
+    a[s] ^= 0x80008000u;  // offset form -> signed lanes
+    b[s] ^= 0x80008000u;
+  }
+  uint4* ck = (uint4*)(base + l.o_ck + p * l.ck_per_thread);
+  uint4* sAa = (uint4*)(base + l.o_seed) + DEC * P;
+  uint4* sBa = (uint4*)(base + l.o_seed + l.seed_bytes) + DEC * P;
+  unsigned mx = 0u, mn = 0u;
+  window_pass_p<DEC, HM>(w, ck, a, b, sAa, sBa, sAa + 2 * P, sBa + 2 * P, mx, mn, pf0, pf1);
+  int* flA = (int*)(base + l.o_flags);
+  atomicMax(&flA[4 + DEC], max(lane_lo(mx), -lane_lo(mn)));
+  atomicMax(&flA[16 + 4 + DEC], max(lane_hi(mx), -lane_hi(mn)));  // lane B: 64 bytes on
+}
+
+// One SISO pass of window p of both CBs of a pair item.  runA / runB: the
+// CB still iterates; hardA / hardB: its hard decisions are used (a CRC check
+// follows).  All threads of the CTA call it (it contains barriers).
+template <int DEC>
+__device__ __forceinline__ void siso_pass_pair(const CbDesc* __restrict__ dA,
+                                               const CbDesc* __restrict__ dB, uint8_t* base, int p,
+                                               bool runA, bool runB, bool first, bool hardA,
+                                               bool hardB) {
+  const int K = dA->K, P = dA->P, W = dA->W;
+  uint4 paA, pbA, paB, pbB;
+  int mA = 0, mB = 0;
+  uint4 pf0 = make_uint4(0u, 0u, 0u, 0u), pf1 = pf0;
+  if (DEC == 1 && (runA || runB)) {  // the first two address groups, fetched across the barrier
+    pf0 = __ldg(dA->qt + p);
+    pf1 = __ldg(dA->qt + P + p);
+  }
+  if (runA) pass_start_p<DEC>(make_pair_slot(base, K, P, W, 0), K, P, p, first, hardA, paA, pbA, mA);
+  if (runB) pass_start_p<DEC>(make_pair_slot(base, K, P, W, 1), K, P, p, first, hardB, paB, pbB, mB);
+  __syncthreads();
+  if (runA && runB) {
+    const bool last = p == P - 1;
+    const int len = min(W, K - p * W);
+    const int8_t* tailA = (const int8_t*)(base + pair_layout(K, P, W).o_tail);
+    int a[8], b[8];
+    lane_start<DEC>(paA, pbA, tailA, last, a, b);
+    bool ok = pair_fast(a, b, 254 + mA, len);
+    const uint4 tA = pack8(b);
+    lane_start<DEC>(paB, pbB, tailA + 16, last, a, b);
+    ok = ok && pair_fast(a, b, 254 + mB, len);
+    if (ok) {
+      if (DEC == 1 && (hardA || hardB))
+        pair_pass<DEC, 1>(dA, base, p, paA, tA, paB, pack8(b), pf0, pf1);
+      else
+        pair_pass<DEC, 0>(dA, base, p, paA, tA, paB, pack8(b), pf0, pf1);
+    } else {
+      lane_pass<DEC>(dA, base, 0, p, hardA, paA, pbA, mA, pf0, pf1);
+      lane_pass<DEC>(dB, base, 1, p, hardB, paB, pbB, mB, pf0, pf1);
+    }
+  } else if (runA) {
+    lane_pass<DEC>(dA, base, 0, p, hardA, paA, pbA, mA, pf0, pf1);
+  } else if (runB) {
+    lane_pass<DEC>(dB, base, 1, p, hardB, paB, pbB, mB, pf0, pf1);
+  }
+  __syncthreads();
+}
+
+// Stop rule of one CB after iteration it (thread p = 0 of the CB, after the
+// CRC shares of a checked iteration were combined in fl[2]): CRC pass, the
+// mutual-information rule, the iteration limit, or a purge of its TB.
+__device__ __forceinline__ void stop_rule(const DecParams& prm, const CbDesc* __restrict__ dp,
+                                          int* fl, int it, int my_max, bool check,
+                                          int* s_remaining) {
+  const bool ok = check && fl[2] == 0;
+  fl[2] = 0;
+  const int tb = dp->tb;
+  bool stop = ok || it == my_max;
+  if (dp->early_stop == 2) {
+    // mutual-information rule: stop once the mean changed by at most
+    // 2^-10 bit (from iteration 2); the CRC decides success
+    const int S = fl[8], dS = abs(S - fl[9]);
+    stop = (it >= 2 && (long long)dS * 1024 <= (long long)dp->K * 65536) || it == my_max;
+    fl[9] = S;
+    fl[8] = 0;
+  }
+  if (stop) {
+    fl[0] = 1;
+    fl[1] = ok ? it : my_max + 1;
+    fl[10] = it;
+    atomicSub(s_remaining, 1);
+    // a failed CB fails its TB: flag it now (the TB CRC step flags it
+    // again) so that purging CBs of the TB can stop
+    if (!ok && dp->crc_b) atomicOr(&prm.tb_crc[2 * tb + 1], 1u);
+  } else if (dp->purge && *(volatile uint32_t*)&prm.tb_crc[2 * tb + 1] != 0u) {
+    fl[0] = 1;
+    fl[1] = 0;
+    fl[6] = 1;
+    fl[10] = it;
+    atomicSub(s_remaining, 1);
+  }
+}
+
+// The hard-decision CRC share (and, for stop rule 2, the mutual-information
+// share) of thread p after a checked iteration.
+__device__ __forceinline__ void check_share(const DecParams& prm, const CbDesc& d,
+                                            const CbSlot& sl, int p, const uint32_t* tabA,
+                                            const uint32_t* tabB, const int* mi_tab) {
+  const uint32_t r = crc_share(d, sl, p, d.crc_b ? tabB : tabA, d.crc_b ? GB : GA,
+                               d.crc_b ? prm.xpowB : prm.xpowA, 0);
+  if (r) atomicXor((unsigned*)&sl.flags[2], r);
+  if (d.early_stop == 2) {
+    // stop rule 2: mutual information of the a-priori LLRs the next
+    // iteration would use (the scaled extrinsics of decoder 2, held in the
+    // ext array; its padding entries are 0 and add nothing)
+    int mi = 0;
+    for (int t = p; t < d.W * d.P; t += d.P)
+      mi += 65536 - mi_tab[min(abs((int)sl.ext[sl.str * t]), kMiTable - 1)];
+    atomicAdd(&sl.flags[8], mi);
+  }
+}
+
+// Debug copy of a CB's de-rate-matched streams (all threads of the CTA).
+__device__ void debug_streams(const DecParams& prm, const CbDesc& dg, const CbSlot& sg, int tid,
+                              int nthr) {
+  const int D = dg.K + 4;
+  int8_t* out = prm.dbg_d + 3 * (int64_t)dg.dbg_off;
+  for (int k = tid; k < D; k += nthr) {
+    if (k < dg.K) {
+      const int t = sg.str * tr_idx(k, dg);
+      out[k] = sg.sys[t];
+      out[D + k] = sg.par1[t];
+      out[2 * D + k] = sg.par2[t];
+    } else {
+      out[k] = sg.tail[3 * (k - dg.K)];
+      out[D + k] = sg.tail[3 * (k - dg.K) + 1];
+      out[2 * D + k] = sg.tail[3 * (k - dg.K) + 2];
+    }
+  }
+}
+
+// Phase 2, part 1 (thread p of the CB): payload bytes, the CB's CRC24A
+// contribution to its TB, debug copies of the final extrinsic and hard bits.
+__device__ void finish_share(const DecParams& prm, const CbDesc& d, const CbSlot& sl, int p,
+                             const uint32_t* tabA) {
+  const bool purged = sl.flags[6] != 0;
+  if (purged) return;
+  const TbDesc tb = prm.tbs[d.tb];
+  const int nw = (d.K + 31) / 32;
+  const int pad = nw * 32 - d.K;
+  const int nbytes = d.pay_bits / 8;
+  uint8_t* out = prm.out + tb.out_off;
+  for (int m = p; m < nbytes; m += d.P) {
+    const int tbbit = d.pay_off + 8 * m;
+    if (tbbit >= tb.A) break;
+    const int q = pad + d.F + 8 * m;
+    out[tbbit >> 3] = (uint8_t)(sl.hard[q >> 5] >> (24 - (q & 31)));
+  }
+  if (d.crc_b) {
+    const uint32_t r = crc_share(d, sl, p, tabA, GA, prm.xpowA, 1);
+    if (r) atomicXor((unsigned*)&sl.flags[3], r);
+  }
+  if (prm.dbg_ext) {
+    for (int k = p; k < d.K; k += d.P) {
+      prm.dbg_ext[d.dbg_off + k] = sl.ext[sl.str * tr_idx(k, d)];
+      const int q = pad + k;
+      prm.dbg_hard[d.dbg_off + k] = (uint8_t)((sl.hard[q >> 5] >> (31 - (q & 31))) & 1u);
+    }
+  }
+}
+
+// Phase 2, part 2 (thread p = 0 of the CB, after a barrier): per-CB results,
+// the TB CRC by linearity, the last CB of a TB to finish decides tb_ok.
+__device__ void finish_cb(const DecParams& prm, const CbDesc& d, const CbSlot& sl,
+                          int sorted_idx, const uint32_t* tabA) {
+  const bool purged = sl.flags[6] != 0;
+  const bool cb_ok = !purged && sl.flags[1] <= d.max_iter;
+  prm.cb_iters[sorted_idx] = (uint8_t)sl.flags[1];
+  if (prm.cb_runs) prm.cb_runs[sorted_idx] = (uint8_t)sl.flags[10];
+  prm.cb_ok[sorted_idx] = cb_ok ? 1 : 0;
+  if (prm.tb_sat && sl.flags[7]) atomicAdd(&prm.tb_sat[d.tb], (unsigned)sl.flags[7]);
+  const TbDesc tb = prm.tbs[d.tb];
+  if (tb.C == 1) {
+    prm.tb_ok[d.tb] = cb_ok ? 1 : 0;
+  } else {
+    uint32_t contrib = (uint32_t)sl.flags[3];
+    // shift past the TB bits that follow this CB's payload: 32 a + 8 b
+    const int na = d.n_after >> 5, nb = (d.n_after >> 3) & 3;
+    if (na) contrib = gf_mulmod(contrib, __ldg(&prm.xpowA[na]), GA);
+    for (int k = 0; k < nb; k++)
+      contrib = ((contrib << 8) & 0xFFFFFFu) ^ tabA[(contrib >> 16) & 0xFFu];
+    atomicXor(&prm.tb_crc[2 * d.tb], contrib);
+    if (!cb_ok) atomicOr(&prm.tb_crc[2 * d.tb + 1], 1u);
+    __threadfence();
+    const int done = atomicAdd(&prm.tb_done[d.tb], 1);
+    if (done == tb.C - 1) {
+      __threadfence();
+      const uint32_t x = atomicOr(&prm.tb_crc[2 * d.tb], 0u);
+      const uint32_t bad = atomicOr(&prm.tb_crc[2 * d.tb + 1], 0u);
+      prm.tb_ok[d.tb] = (x == 0u && bad == 0u) ? 1 : 0;
+    }
+  }
+}
+
+// A pair item: two CBs of equal (K, P) on threads 0..P-1, one pair slot.
+__device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkItem& wi, uint8_t* slots, int tid,
+                              const uint32_t* tabA, const uint32_t* tabB, const int* mi_tab,
+                              int* s_remaining, int* s_maxit) {
+  const CbDesc* cbs = prm.cbs + wi.cb0;
+  const CbDesc* dA = cbs;
+  const CbDesc* dB = cbs + 1;
+  const int K = dA->K, P = dA->P, W = dA->W;
+  const bool mine = tid < P;
+  const int p = tid;
+  const CbSlot sA = make_pair_slot(slots, K, P, W, 0);
+  const CbSlot sB = make_pair_slot(slots, K, P, W, 1);
+  // ---- phase 0: de-rate-matching of both CBs, one after the other (they
+  // share the staging area), and the pair's extrinsics cleared
+  {
+    const PairLayout l = pair_layout(K, P, W);
+    uint4* e16 = (uint4*)(slots + l.o_ext);
+    for (int k = tid; k < (4 * W * P + 15) / 16; k += kThreads) e16[k] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  stage_llrs(*dA, sA, prm.llr, tid, kThreads);
+  __syncthreads();
+  derm_cb<2>(*dA, sA, llr_src(*dA, sA, prm.llr), prm.soft, tid, kThreads);
+  __syncthreads();
+  stage_llrs(*dB, sB, prm.llr, tid, kThreads);
+  __syncthreads();
+  derm_cb<2>(*dB, sB, llr_src(*dB, sB, prm.llr), prm.soft, tid, kThreads);
+  if (tid == 0) {
+    *s_remaining = 2;
+    *s_maxit = max((int)dA->max_iter, (int)dB->max_iter);
+  }
+  __syncthreads();
+  if (prm.dbg_d) {
+    debug_streams(prm, *dA, sA, tid, kThreads);
+    debug_streams(prm, *dB, sB, tid, kThreads);
+  }
+  // ---- phase 1: turbo iterations of both CBs
+  const int maxit = *s_maxit;
+  for (int it = 1; it <= maxit; it++) {
+    const int maxA = dA->max_iter, maxB = dB->max_iter;
+    const bool runA = mine && sA.flags[0] == 0 && it <= maxA;
+    const bool runB = mine && sB.flags[0] == 0 && it <= maxB;
+    const bool first = (it == 1);
+    siso_pass_pair<0>(dA, dB, slots, p, runA, runB, first, false, false);
+    const bool checkA = runA && (dA->early_stop || it == maxA);
+    const bool checkB = runB && (dB->early_stop || it == maxB);
+    siso_pass_pair<1>(dA, dB, slots, p, runA, runB, first, checkA, checkB);
+    if (checkA) check_share(prm, *dA, sA, p, tabA, tabB, mi_tab);
+    if (checkB) check_share(prm, *dB, sB, p, tabA, tabB, mi_tab);
+    __syncthreads();
+    if (p == 0) {
+      if (runA) stop_rule(prm, dA, sA.flags, it, maxA, checkA, s_remaining);
+      if (runB) stop_rule(prm, dB, sB.flags, it, maxB, checkB, s_remaining);
+    }
+    __syncthreads();
+    if (*s_remaining == 0) break;
+  }
+  // ---- phase 2: results of both CBs
+  if (mine) {
+    finish_share(prm, *dA, sA, p, tabA);
+    finish_share(prm, *dB, sB, p, tabA);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    finish_cb(prm, *dA, sA, wi.cb0, tabA);
+    finish_cb(prm, *dB, sB, wi.cb0 + 1, tabA);
+  }
+}
+
+// A work item of one or more CBs, P threads each (windows across threads).
+template <bool R4, bool QT>
+__device__ __forceinline__ void run_single_item(const DecParams& prm, const WorkItem& wi,
+                                                uint8_t* slots, int tid, const uint32_t* tabA,
+                                                const uint32_t* tabB, const int* mi_tab,
+                                                int* s_remaining, int* s_maxit) {
+  const CbDesc* cbs = prm.cbs + wi.cb0;
+  const int P = cbs[0].P;
+  const int G = wi.n;
+  const int mycb = tid / P;
+  const int p = tid - mycb * P;
+  const bool mine = mycb < G;
+  const CbDesc* dp = cbs + (mine ? mycb : 0);
+
+  // ---- phase 0: de-rate-matching of every CB of the item (LLRs staged
+  // in shared memory first)
+  for (int g = 0; g < G; g++) {
+    const CbDesc& dg = cbs[g];
+    const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
+    stage_llrs(dg, sg, prm.llr, tid, kThreads);
+  }
+  __syncthreads();
+  for (int g = 0; g < G; g++) {
+    const CbDesc& dg = cbs[g];
+    const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
+    derm_cb<1>(dg, sg, llr_src(dg, sg, prm.llr), prm.soft, tid, kThreads);
+  }
+  if (tid == 0) {
+    *s_remaining = G;
+    int mx = 0;
+    for (int g = 0; g < G; g++) mx = max(mx, (int)cbs[g].max_iter);
+    *s_maxit = mx;
+  }
+  __syncthreads();
+  uint8_t* mybase = slots + (mine ? mycb : 0) * wi.smem_per_cb;
+  int* const fl = make_slot(mybase, dp->K, dp->P, dp->W).flags;
+  if (prm.dbg_d) {
+    for (int g = 0; g < G; g++) {
+      const CbDesc& dg = cbs[g];
+      debug_streams(prm, dg, make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W), tid,
+                    kThreads);
+    }
+  }
+
+  // ---- phase 1: turbo iterations (only the flags pointer stays live
+  // across the SISO passes; descriptor fields are re-read when needed)
+  const int maxit = *s_maxit;
+  for (int it = 1; it <= maxit; it++) {
+    const int my_max = mine ? (int)dp->max_iter : 0;
+    const bool run = mine && fl[0] == 0 && it <= my_max;
+    const bool first = (it == 1);
+    siso_pass<0, R4, QT>(dp, mybase, p, run, first, false);
+    const bool check = run && (dp->early_stop || it == my_max);
+    siso_pass<1, R4, QT>(dp, mybase, p, run, first, check);
+    if (check) {
+      const CbDesc& d = *dp;
+      check_share(prm, d, make_slot(mybase, d.K, d.P, d.W), p, tabA, tabB, mi_tab);
+    }
+    __syncthreads();
+    if (run && p == 0) stop_rule(prm, dp, fl, it, my_max, check, s_remaining);
+    __syncthreads();
+    if (*s_remaining == 0) break;
+  }
+
+  // ---- phase 2: results, payload bytes, TB CRC, debug copies
+  const CbDesc d = *dp;
+  const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
+  if (mine) finish_share(prm, d, sl, p, tabA);
+  __syncthreads();
+  if (mine && p == 0) finish_cb(prm, d, sl, wi.cb0 + mycb, tabA);
+}
+// The same, not inlined: the pair kernel runs one-CB items rarely, and the
+// pair path keeps the kernel's registers to itself.
+template <bool R4, bool QT>
+__device__ __noinline__ void run_single_item_call(const DecParams& prm, const WorkItem& wi,
+                                                  uint8_t* slots, int tid, const uint32_t* tabA,
+                                                  const uint32_t* tabB, const int* mi_tab,
+                                                  int* s_remaining, int* s_maxit) {
+  run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, s_remaining, s_maxit);
+}
+
 // R4 = false: the radix-2 kernel; R4 = true adds the radix-4 forward
 // recursion for CBs that select it (a separate instantiation, so the radix-2
 // kernel's code is not affected by the option).  QT: every CB carries an
 // address table for its interleaved pass (else the addresses are computed).
-template <bool R4, bool QT>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams prm) {
+// PAIR: the batch has CB-pair items (needs QT); the kernel is then built for
+// two CTAs per SM (more registers per thread for the packed path).
+template <bool R4, bool QT, bool PAIR>
+__global__ void __launch_bounds__(kThreads, PAIR ? kCtasPerSmPair : kCtasPerSm)
+    decode_kernel(DecParams prm) {
   __shared__ int s_item;
   __shared__ int s_remaining;
   __shared__ int s_maxit;
@@ -890,226 +1687,81 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) decode_kernel(DecParams 
     const int item = s_item;
     if (item >= prm.n_items) break;
     const WorkItem wi = prm.items[item];
-    const CbDesc* cbs = prm.cbs + wi.cb0;
-    const int P = cbs[0].P;
-    const int G = wi.n;
-    const int mycb = tid / P;
-    const int p = tid - mycb * P;
-    const bool mine = mycb < G;
-    const CbDesc* dp = cbs + (mine ? mycb : 0);
-
-    // ---- phase 0: de-rate-matching of every CB of the item (LLRs staged
-    // in shared memory first)
-    for (int g = 0; g < G; g++) {
-      const CbDesc& dg = cbs[g];
-      const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
-      stage_llrs(dg, sg, prm.llr, tid, kThreads);
+    if (PAIR && wi.mode == 1) {
+      run_pair_item(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining, &s_maxit);
+      continue;
     }
-    __syncthreads();
-    for (int g = 0; g < G; g++) {
-      const CbDesc& dg = cbs[g];
-      const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
-      derm_cb(dg, sg, llr_src(dg, sg, prm.llr), prm.soft, tid, kThreads);
-    }
-    if (tid == 0) {
-      s_remaining = G;
-      int mx = 0;
-      for (int g = 0; g < G; g++) mx = max(mx, (int)cbs[g].max_iter);
-      s_maxit = mx;
-    }
-    __syncthreads();
-    uint8_t* mybase = slots + (mine ? mycb : 0) * wi.smem_per_cb;
-    int* const fl = make_slot(mybase, dp->K, dp->P, dp->W).flags;
-    if (prm.dbg_d) {
-      for (int g = 0; g < G; g++) {
-        const CbDesc& dg = cbs[g];
-        const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
-        const int D = dg.K + 4;
-        int8_t* out = prm.dbg_d + 3 * (int64_t)dg.dbg_off;
-        for (int k = tid; k < D; k += kThreads) {
-          if (k < dg.K) {
-            const int t = tr_idx(k, dg);
-            out[k] = sg.sys[t];
-            out[D + k] = sg.par1[t];
-            out[2 * D + k] = sg.par2[t];
-          } else {
-            out[k] = sg.tail[3 * (k - dg.K)];
-            out[D + k] = sg.tail[3 * (k - dg.K) + 1];
-            out[2 * D + k] = sg.tail[3 * (k - dg.K) + 2];
-          }
-        }
-      }
-    }
-
-    // ---- phase 1: turbo iterations (only the flags pointer stays live
-    // across the SISO passes; descriptor fields are re-read when needed)
-    const int maxit = s_maxit;
-    for (int it = 1; it <= maxit; it++) {
-      const int my_max = mine ? (int)dp->max_iter : 0;
-      const bool run = mine && fl[0] == 0 && it <= my_max;
-      const bool first = (it == 1);
-      siso_pass<0, R4, QT>(dp, mybase, p, run, first, false);
-      const bool check = run && (dp->early_stop || it == my_max);
-      siso_pass<1, R4, QT>(dp, mybase, p, run, first, check);
-      if (check) {
-        const CbDesc& d = *dp;
-        const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
-        const uint32_t r = crc_share(d, sl, p, d.crc_b ? tabB : tabA, d.crc_b ? GB : GA,
-                                     d.crc_b ? prm.xpowB : prm.xpowA, 0);
-        if (r) atomicXor((unsigned*)&fl[2], r);
-        if (d.early_stop == 2) {
-          // stop rule 2: mutual information of the a-priori LLRs the next
-          // iteration would use (the scaled extrinsics of decoder 2, held in
-          // the ext array; its padding entries are 0 and add nothing)
-          int mi = 0;
-          for (int t = p; t < d.W * d.P; t += d.P)
-            mi += 65536 - mi_tab[min(abs((int)sl.ext[t]), kMiTable - 1)];
-          atomicAdd(&fl[8], mi);
-        }
-      }
-      __syncthreads();
-      if (run && p == 0) {
-        const bool ok = check && fl[2] == 0;
-        fl[2] = 0;
-        const int tb = dp->tb;
-        bool stop = ok || it == my_max;
-        if (dp->early_stop == 2) {
-          // mutual-information rule: stop once the mean changed by at most
-          // 2^-10 bit (from iteration 2); the CRC decides success
-          const int S = fl[8], dS = abs(S - fl[9]);
-          stop = (it >= 2 && (long long)dS * 1024 <= (long long)dp->K * 65536) || it == my_max;
-          fl[9] = S;
-          fl[8] = 0;
-        }
-        if (stop) {
-          fl[0] = 1;
-          fl[1] = ok ? it : my_max + 1;
-          fl[10] = it;
-          atomicSub(&s_remaining, 1);
-          // a failed CB fails its TB: flag it now (the TB CRC step flags it
-          // again) so that purging CBs of the TB can stop
-          if (!ok && dp->crc_b) atomicOr(&prm.tb_crc[2 * tb + 1], 1u);
-        } else if (dp->purge && *(volatile uint32_t*)&prm.tb_crc[2 * tb + 1] != 0u) {
-          fl[0] = 1;
-          fl[1] = 0;
-          fl[6] = 1;
-          fl[10] = it;
-          atomicSub(&s_remaining, 1);
-        }
-      }
-      __syncthreads();
-      if (s_remaining == 0) break;
-    }
-
-    // ---- phase 2: results, payload bytes, TB CRC, debug copies
-    const CbDesc d = *dp;
-    const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
-    const int sorted_idx = wi.cb0 + (mine ? mycb : 0);
-    const bool purged = mine && sl.flags[6] != 0;
-    const bool cb_ok = mine && !purged && sl.flags[1] <= d.max_iter;
-    if (mine && !purged) {
-      const TbDesc tb = prm.tbs[d.tb];
-      const int nw = (d.K + 31) / 32;
-      const int pad = nw * 32 - d.K;
-      const int nbytes = d.pay_bits / 8;
-      uint8_t* out = prm.out + tb.out_off;
-      for (int m = p; m < nbytes; m += d.P) {
-        const int tbbit = d.pay_off + 8 * m;
-        if (tbbit >= tb.A) break;
-        const int q = pad + d.F + 8 * m;
-        out[tbbit >> 3] = (uint8_t)(sl.hard[q >> 5] >> (24 - (q & 31)));
-      }
-      if (d.crc_b) {
-        const uint32_t r = crc_share(d, sl, p, tabA, GA, prm.xpowA, 1);
-        if (r) atomicXor((unsigned*)&sl.flags[3], r);
-      }
-      if (prm.dbg_ext) {
-        for (int k = p; k < d.K; k += d.P) {
-          prm.dbg_ext[d.dbg_off + k] = sl.ext[tr_idx(k, d)];
-          const int q = pad + k;
-          prm.dbg_hard[d.dbg_off + k] = (uint8_t)((sl.hard[q >> 5] >> (31 - (q & 31))) & 1u);
-        }
-      }
-    }
-    __syncthreads();
-    if (mine && p == 0) {
-      prm.cb_iters[sorted_idx] = (uint8_t)sl.flags[1];
-      if (prm.cb_runs) prm.cb_runs[sorted_idx] = (uint8_t)sl.flags[10];
-      prm.cb_ok[sorted_idx] = cb_ok ? 1 : 0;
-      if (prm.tb_sat && sl.flags[7]) atomicAdd(&prm.tb_sat[d.tb], (unsigned)sl.flags[7]);
-      const TbDesc tb = prm.tbs[d.tb];
-      if (tb.C == 1) {
-        prm.tb_ok[d.tb] = cb_ok ? 1 : 0;
-      } else {
-        uint32_t contrib = (uint32_t)sl.flags[3];
-        // shift past the TB bits that follow this CB's payload: 32 a + 8 b
-        const int na = d.n_after >> 5, nb = (d.n_after >> 3) & 3;
-        if (na) contrib = gf_mulmod(contrib, __ldg(&prm.xpowA[na]), GA);
-        for (int k = 0; k < nb; k++)
-          contrib = ((contrib << 8) & 0xFFFFFFu) ^ tabA[(contrib >> 16) & 0xFFu];
-        atomicXor(&prm.tb_crc[2 * d.tb], contrib);
-        if (!cb_ok) atomicOr(&prm.tb_crc[2 * d.tb + 1], 1u);
-        __threadfence();
-        const int done = atomicAdd(&prm.tb_done[d.tb], 1);
-        if (done == tb.C - 1) {
-          __threadfence();
-          const uint32_t x = atomicOr(&prm.tb_crc[2 * d.tb], 0u);
-          const uint32_t bad = atomicOr(&prm.tb_crc[2 * d.tb + 1], 0u);
-          prm.tb_ok[d.tb] = (x == 0u && bad == 0u) ? 1 : 0;
-        }
-      }
-    }
+    if (PAIR)
+      run_single_item_call<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining,
+                                   &s_maxit);
+    else
+      run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining, &s_maxit);
   }
 }
 
 }  // namespace
 
-int decode_max_smem() { return kSmemBudget + kSmemFixed; }
+int decode_max_smem() {
+  return (kSmemBudgetPair > kSmemBudget ? kSmemBudgetPair : kSmemBudget) + kSmemFixed;
+}
 
-template <bool R4, bool QT>
+template <bool R4, bool QT, bool PAIR>
 cudaError_t set_attr_one() {
-  return cudaFuncSetAttribute(decode_kernel<R4, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              decode_max_smem());
+  return cudaFuncSetAttribute(decode_kernel<R4, QT, PAIR>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, decode_max_smem());
 }
 static cudaError_t set_attr() {
-  cudaError_t e = set_attr_one<false, false>();
-  if (e == cudaSuccess) e = set_attr_one<false, true>();
-  if (e == cudaSuccess) e = set_attr_one<true, false>();
-  if (e == cudaSuccess) e = set_attr_one<true, true>();
+  static cudaError_t e = [] {
+    cudaError_t r = set_attr_one<false, false, false>();
+    if (r == cudaSuccess) r = set_attr_one<false, true, false>();
+    if (r == cudaSuccess) r = set_attr_one<true, false, false>();
+    if (r == cudaSuccess) r = set_attr_one<true, true, false>();
+    if (r == cudaSuccess) r = set_attr_one<false, true, true>();
+    if (r == cudaSuccess) r = set_attr_one<true, true, true>();
+    return r;
+  }();
   return e;
 }
 
-template <bool R4, bool QT>
+template <bool R4, bool QT, bool PAIR>
 int occupancy_one(int smem) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_kernel<R4, QT>, kThreads, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_kernel<R4, QT, PAIR>, kThreads,
+                                                    smem) != cudaSuccess)
     return 0;
   return n;
 }
 
-// Resident CTAs per SM at this dynamic shared memory: the smallest over the
-// kernel's instantiations (all are built for kCtasPerSm).
-int decode_occupancy(int smem) {
+// Resident CTAs per SM at this dynamic shared memory for the instantiation a
+// launch with these flags uses (see launch_decode).
+int decode_occupancy(int smem, bool radix4_any, bool qtab_all, bool pair_any) {
   if (set_attr() != cudaSuccess) return 0;
-  const int a = occupancy_one<false, false>(smem), b = occupancy_one<false, true>(smem);
-  const int c = occupancy_one<true, false>(smem), d = occupancy_one<true, true>(smem);
-  const int ab = a < b ? a : b, cd = c < d ? c : d;
-  return ab < cd ? ab : cd;
+  if (pair_any && qtab_all)
+    return radix4_any ? occupancy_one<true, true, true>(smem) : occupancy_one<false, true, true>(smem);
+  if (radix4_any)
+    return qtab_all ? occupancy_one<true, true, false>(smem) : occupancy_one<true, false, false>(smem);
+  return qtab_all ? occupancy_one<false, true, false>(smem) : occupancy_one<false, false, false>(smem);
 }
 
 cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s) {
   if (smem > decode_max_smem()) return cudaErrorInvalidValue;
-  if (p.radix4_any) {
-    if (p.qtab_all)
-      decode_kernel<true, true><<<grid, kThreads, smem, s>>>(p);
+  if (p.pair_any && !p.qtab_all) return cudaErrorInvalidValue;
+  if (set_attr() != cudaSuccess) return cudaErrorInvalidValue;
+  if (p.pair_any) {
+    if (p.radix4_any)
+      decode_kernel<true, true, true><<<grid, kThreads, smem, s>>>(p);
     else
-      decode_kernel<true, false><<<grid, kThreads, smem, s>>>(p);
+      decode_kernel<false, true, true><<<grid, kThreads, smem, s>>>(p);
+  } else if (p.radix4_any) {
+    if (p.qtab_all)
+      decode_kernel<true, true, false><<<grid, kThreads, smem, s>>>(p);
+    else
+      decode_kernel<true, false, false><<<grid, kThreads, smem, s>>>(p);
   } else {
     if (p.qtab_all)
-      decode_kernel<false, true><<<grid, kThreads, smem, s>>>(p);
+      decode_kernel<false, true, false><<<grid, kThreads, smem, s>>>(p);
     else
-      decode_kernel<false, false><<<grid, kThreads, smem, s>>>(p);
+      decode_kernel<false, false, false><<<grid, kThreads, smem, s>>>(p);
   }
   return cudaGetLastError();
 }

@@ -15,7 +15,8 @@
 // usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--threads T] FILE UES SECONDS
 //                     RETX_FRACTION SEED CELLS...
 // TABLE: a window-count table (188 numbers) installed with crnt_tune_set,
-// optionally followed by a radix table (188 numbers, crnt_tune_radix_set);
+// optionally followed by a radix table (188 numbers, crnt_tune_radix_set)
+// and a CTA-shape table (188 numbers, crnt_tune_shape_set);
 // --purge: every TB asks for purge on failure (CRNT_F_PURGE);
 // --poisson: exponential inter-arrival times of mean 1 ms per cell instead of
 // the 1 ms period with jitter; --threads T: submitter threads, cells dealt
@@ -203,9 +204,17 @@ int main(int argc, char** argv) {
       if (fscanf(t, "%d", &v) != 1) break;
       radix[nr] = (uint8_t)v;
     }
+    uint8_t shape[CRNT_NUM_K];
+    int ns = 0;  // and an optional CTA-shape table
+    for (; nr == CRNT_NUM_K && ns < CRNT_NUM_K; ns++) {
+      int v = 0;
+      if (fscanf(t, "%d", &v) != 1) break;
+      shape[ns] = (uint8_t)v;
+    }
     fclose(t);
     if (crnt_tune_set(table, CRNT_NUM_K) != CRNT_OK) return 2;
     if (nr == CRNT_NUM_K && crnt_tune_radix_set(radix, CRNT_NUM_K) != CRNT_OK) return 2;
+    if (ns == CRNT_NUM_K && crnt_tune_shape_set(shape, CRNT_NUM_K) != CRNT_OK) return 2;
     argv += 2;
     argc -= 2;
   }

@@ -304,7 +304,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     wi.cb0 = k;
     wi.n = 0;
     wi.smem_per_cb = slot;
-    wi.pad0 = 0;
+    wi.mode = 0;
     while (i < ncb && wi.n < gmax) {
       const CbDesc& c = h_all[h_order[i]];
       if (c.K != h.K || c.P != h.P) break;
@@ -318,7 +318,9 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     max_slot = std::max(max_slot, wi.n * slot);
   }
   const int smem = kSmemFixed + max_slot;
-  const int per_sm = decode_occupancy(smem);
+  bool radix4_any = false;
+  for (int i = 0; i < ncb; i++) radix4_any |= h_cbs[i].radix4 != 0;
+  const int per_sm = decode_occupancy(smem, radix4_any, false, false);
   if (per_sm < 1) return CRNT_EDEVICE;
   const int grid = std::min(nitems, per_sm * g_num_sms[dev]);
 

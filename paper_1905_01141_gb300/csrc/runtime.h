@@ -181,6 +181,10 @@ const uint32_t* dmap_get(crnt_ctx* ctx, int K, int P, int F);
 // (the autotuner's candidates).
 uint8_t radix4_of(int K);
 extern thread_local int t_radix_override;
+// CTA shape for CB size K from the shape table (1 one CB per thread, 2 CB
+// pairs); t_shape_override > 0 replaces it for plans built on this thread.
+uint8_t shape_of(int K);
+extern thread_local int t_shape_override;
 // Window count used for CB size K when a TB requests P (0 = table / built-in).
 int clamp_p(int K, int P);
 void serving_stop(crnt_ctx* ctx);

@@ -7,9 +7,14 @@
 // LLR values on the clamp-free path, so the inputs are zeros.  Candidates:
 // minimum window lengths w in {w_lo, 32, 40, 48, 56, 64, 80, 96} (w_lo: the
 // shortest allowed, which also uses the most threads), each giving
-// P = floor(K / w) windows of ceil(K / P) >= w steps.  At the window count
-// it keeps, the tuner also times the radix-4 forward recursion (the same
-// decoded values) and selects it for that K when it is more than 1 % faster.
+// P = floor(K / w) windows of ceil(K / P) >= w steps, timed in both CTA
+// shapes -- one CB per thread, and CB pairs in 16-bit lanes -- and, for CB
+// pairs only, P = ceil(K / w) windows of at most w steps, which for these w
+// (multiples of 8) fill the pair path's 8-step sub-windows.  Each candidate
+// counts with its faster shape; the kept window count takes its faster
+// shape.  At that count the tuner also times the radix-4 forward recursion
+// (one CB per thread), selecting it when it is more than 1 % faster than
+// both.  Shape and radix never change a decoded value, only the speed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +27,7 @@
 namespace crnt {
 extern std::atomic<uint8_t> g_tuned[lte::kNumK];
 extern std::atomic<uint8_t> g_radix[lte::kNumK];
+extern std::atomic<uint8_t> g_shape[lte::kNumK];
 
 namespace {
 
@@ -99,6 +105,24 @@ int crnt_tune_radix_set(const uint8_t* radix_by_k, uint32_t n) {
   return CRNT_OK;
 }
 
+int crnt_tune_shape_get(uint8_t* shape_by_k, uint32_t n) {
+  if (!shape_by_k) return CRNT_EINVAL;
+  for (uint32_t i = 0; i < n && i < (uint32_t)lte::kNumK; i++)
+    shape_by_k[i] = g_shape[i].load(std::memory_order_relaxed) == 2 ? 2 : 1;
+  return CRNT_OK;
+}
+
+int crnt_tune_shape_set(const uint8_t* shape_by_k, uint32_t n) {
+  if (!shape_by_k || n != (uint32_t)lte::kNumK) return CRNT_EINVAL;
+  for (int i = 0; i < lte::kNumK; i++) {
+    const uint8_t v = shape_by_k[i];
+    if (v > 2) return CRNT_EINVAL;
+  }
+  for (int i = 0; i < lte::kNumK; i++)
+    g_shape[i].store(shape_by_k[i] == 2 ? 2 : 1, std::memory_order_relaxed);
+  return CRNT_OK;
+}
+
 int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
   if (!ctx) return CRNT_EINVAL;
   if (w_min == 0) w_min = 32;
@@ -109,7 +133,8 @@ int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
   // thread slot (two waves of CTAs), at most 64 MiB of LLRs
   struct Cand {
     int K, P, n;
-    float rate;
+    bool one;                  // timed with one CB per thread as well as in pairs
+    float rate, rate1, rate2;  // best, one CB per thread, CB pairs (0: not timed)
   };
   std::vector<std::vector<Cand>> cands(lte::kNumK);
   const size_t slots = (size_t)kCtasPerSm * ctx->num_sms;
@@ -118,19 +143,31 @@ int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
     const int K = lte::k_of(i);
     const int pmax = std::max(1, std::min(K / 8, (int)CRNT_MAX_P));
     const int w_lo = std::max((int)w_min, (K + pmax - 1) / pmax);
+    // one CB per thread: P = floor(K / w), windows of >= w steps; CB pairs
+    // also P = ceil(K / w) for w a multiple of the pair path's checkpoint
+    // interval, windows of <= w steps that fill whole sub-windows (ragged
+    // sub-windows cost the pair path more than it saves)
     const int ws[] = {w_lo, 32, 40, 48, 56, 64, 80, 96};
-    for (int w : ws) {
+    for (int k = 0; k < 2 * 8; k++) {
+      const int w = ws[k % 8];
+      const bool one = k < 8;
       if (w < w_lo) continue;
-      const int P = clamp_p(K, std::max(1, K / w));  // windows of >= w steps
-      bool dup = false;
-      for (const Cand& c : cands[i]) dup |= c.P == P;
-      if (dup) continue;
+      const int P = one ? clamp_p(K, std::max(1, K / w)) : clamp_p(K, (K + w - 1) / w);
       const int W = (K + P - 1) / P;
+      if (!one && W < (int)w_min) continue;
+      bool dup = false;
+      for (Cand& c : cands[i])
+        if (c.P == P) {
+          dup = true;
+          c.one |= one;
+        }
+      if (dup) continue;
       const int slot = align16(dec_cb_smem(K, (K + W - 1) / W, W));
       const int g = std::max(1, std::min(kThreads / P, kSmemBudget / slot));
-      size_t n = 2 * slots * (size_t)g;
+      // two waves in either shape (a pair CTA holds two CBs)
+      size_t n = 2 * std::max(slots * (size_t)g, (size_t)(kCtasPerSmPair * 2 * ctx->num_sms));
       n = std::min(n, (size_t)(64u << 20) / (size_t)(3 * K + 12));
-      cands[i].push_back(Cand{K, P, (int)n, 0.0f});
+      cands[i].push_back(Cand{K, P, (int)n, one, 0.0f, 0.0f, 0.0f});
       max_llr = std::max(max_llr, n * (size_t)(3 * K + 12));
       max_out = std::max(max_out, n * (size_t)((K - 24) / 8) + 16);
     }
@@ -143,33 +180,48 @@ int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
       cudaMemset(d_llr, 0, max_llr) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = CRNT_ENOMEM;
-  uint8_t table[lte::kNumK], radix[lte::kNumK];
+  uint8_t table[lte::kNumK], radix[lte::kNumK], shape[lte::kNumK];
   memset(table, 0, sizeof table);
   memset(radix, 2, sizeof radix);
+  memset(shape, 1, sizeof shape);
   {
     crnt_plan plan;  // re-planned per candidate; its buffers only grow
     for (int i = 0; i < lte::kNumK && rc == CRNT_OK; i++) {
       float best = 0.0f;
       t_radix_override = 0;
       for (Cand& c : cands[i]) {
-        float ms = 0.0f;
-        rc = time_batch(ctx, &plan, c.K, c.P, c.n, d_llr, d_out, e0, e1, &ms);
+        for (int sh = 1; sh <= 2 && rc == CRNT_OK; sh++) {
+          const int W = (c.K + c.P - 1) / c.P;
+          if (sh == 1 && !c.one) continue;
+          if (sh == 2 && dec_pair_smem(c.K, (c.K + W - 1) / W, W) > kSmemBudgetPair) continue;
+          t_shape_override = sh;
+          float ms = 0.0f;
+          rc = time_batch(ctx, &plan, c.K, c.P, c.n, d_llr, d_out, e0, e1, &ms);
+          (sh == 1 ? c.rate1 : c.rate2) = (float)c.n * (float)c.K / ms;
+        }
         if (rc) break;
-        c.rate = (float)c.n * (float)c.K / ms;
+        c.rate = std::max(c.rate1, c.rate2);
         best = std::max(best, c.rate);
       }
+      t_shape_override = -1;
       if (rc) break;
       // the longest windows among the candidates within 1 % of the fastest
       const Cand* pick = nullptr;
       for (const Cand& c : cands[i])
         if (c.rate >= 0.99f * best && (!pick || c.P < pick->P)) pick = &c;
       table[i] = (uint8_t)pick->P;
-      // the radix-4 forward recursion at that window count
+      if (pick->rate2 > pick->rate1) shape[i] = 2;
+      // the radix-4 forward recursion (one CB per thread) at that window count
       float ms4 = 0.0f;
       t_radix_override = 1;
+      t_shape_override = 1;
       rc = time_batch(ctx, &plan, pick->K, pick->P, pick->n, d_llr, d_out, e0, e1, &ms4);
+      t_shape_override = -1;
       if (rc) break;
-      if ((float)pick->n * (float)pick->K / ms4 > 1.01f * pick->rate) radix[i] = 4;
+      if ((float)pick->n * (float)pick->K / ms4 > 1.01f * pick->rate) {
+        radix[i] = 4;
+        shape[i] = 1;
+      }
     }
     t_radix_override = -1;
   }
@@ -181,6 +233,7 @@ int crnt_autotune(crnt_ctx* ctx, uint32_t w_min, uint8_t* P_by_k) {
   for (int i = 0; i < lte::kNumK; i++) {
     g_tuned[i].store(table[i], std::memory_order_relaxed);
     g_radix[i].store(radix[i], std::memory_order_relaxed);
+    g_shape[i].store(shape[i], std::memory_order_relaxed);
   }
   if (P_by_k) memcpy(P_by_k, table, sizeof table);
   return CRNT_OK;

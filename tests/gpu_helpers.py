@@ -20,6 +20,20 @@ def make_tb(orc, A, G, Qm, seed, rv=0, ebn0=None, snr=None, noiseless=False, amp
     return a, llr
 
 
+def batch(orc, specs):
+    """TB parameter dicts and LLRs from specs (dicts of TB parameters plus
+    seed and one of ebn0 / snr / noiseless (with amp))."""
+    tbs, llrs = [], []
+    for s in specs:
+        s = dict(s)
+        seed = s.pop("seed")
+        kw = {k: s.pop(k) for k in ("ebn0", "snr", "noiseless", "amp") if k in s}
+        a, llr = make_tb(orc, s["A"], s["G"], s.get("Qm", 2), seed, rv=s.get("rv", 0), **kw)
+        tbs.append(s)
+        llrs.append(llr)
+    return tbs, llrs
+
+
 def run_gpu(crnt, ctx, tbs, llr_cat, debug=True):
     """Decode a batch through crnt_plan_launch_debug; returns host copies."""
     import torch

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_helpers import check_batch, make_tb, oracle_tb, run_gpu
+from gpu_helpers import batch, check_batch, make_tb, oracle_tb, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -20,18 +20,6 @@ def ctx(crnt_lib):
     c = crnt_lib.Context(0)
     yield c
     c.close()
-
-
-def batch(orc, specs):
-    tbs, llrs = [], []
-    for s in specs:
-        s = dict(s)
-        seed = s.pop("seed")
-        kw = {k: s.pop(k) for k in ("ebn0", "snr", "noiseless", "amp") if k in s}
-        a, llr = make_tb(orc, s["A"], s["G"], s.get("Qm", 2), seed, rv=s.get("rv", 0), **kw)
-        tbs.append(s)
-        llrs.append(llr)
-    return tbs, llrs
 
 
 @pytest.mark.parametrize("P", [1, 8, 64, 128])
