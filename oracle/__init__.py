@@ -77,6 +77,11 @@ def lib():
                 "orc_decode_tb": (I, [P, I, I, I, I, I, I, I, I, I, P, P, P]),
                 "orc_scale_ext": (I, [I]),
                 "orc_mi_table": (I, [P, I]),
+                "orc_gold": (I, [ctypes.c_uint32, I, P]),
+                "orc_pusch_cinit": (ctypes.c_uint32, [I, I, I, I]),
+                "orc_channel_interleave": (I, [P, I, I, I, P]),
+                "orc_pusch_rx": (I, [P, I, I, I, ctypes.c_uint32, P]),
+                "orc_pusch_tx": (I, [P, I, I, I, ctypes.c_uint32, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -286,3 +291,42 @@ def decode_tb(llr, A, G, Qm=2, NL=1, rv=0, P=1, max_iter=6, early_stop=True, sof
                cb_iters=[res.cb_iters[r] for r in range(C)],
                cb_crc_ok=[bool(res.cb_crc_ok[r]) for r in range(C)])
     return a, out, soft
+
+
+# ---------------------------------------------------------------- PUSCH front stage
+def gold(c_init, n):
+    """First n bits of the length-31 Gold sequence of c_init (uint8 array)."""
+    c = np.zeros(max(1, n), dtype=np.uint8)
+    if lib().orc_gold(int(c_init), n, _p(c)):
+        raise RuntimeError("orc_gold failed")
+    return c[:n]
+
+
+def pusch_cinit(rnti, q, ns, cell):
+    return int(lib().orc_pusch_cinit(rnti, q, ns, cell))
+
+
+def channel_interleave(e, QmNL, ncol=12):
+    e = _u8(e)
+    tx = np.zeros(len(e), dtype=np.uint8)
+    if lib().orc_channel_interleave(_p(e), len(e), QmNL, ncol, _p(tx)):
+        raise RuntimeError("G is not a multiple of Qm NL ncol")
+    return tx
+
+
+def pusch_rx(rx, QmNL, c_init, ncol=12):
+    """Descramble and de-interleave received LLRs into the e-sequence."""
+    rx = _i8(rx)
+    e = np.zeros(len(rx), dtype=np.int8)
+    if lib().orc_pusch_rx(_p(rx), len(rx), QmNL, ncol, int(c_init), _p(e)):
+        raise RuntimeError("G is not a multiple of Qm NL ncol")
+    return e
+
+
+def pusch_tx(e, QmNL, c_init, ncol=12):
+    """Interleave and scramble coded bits (transmitter order)."""
+    e = _u8(e)
+    tx = np.zeros(len(e), dtype=np.uint8)
+    if lib().orc_pusch_tx(_p(e), len(e), QmNL, ncol, int(c_init), _p(tx)):
+        raise RuntimeError("G is not a multiple of Qm NL ncol")
+    return tx

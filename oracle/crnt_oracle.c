@@ -26,7 +26,9 @@
  * to be a permutation, but conformance of the values to 3GPP is
  * "parity unpinned".  The tail-bit multiplexing order (TS 36.212 Sec.
  * 5.1.3.2.2) is likewise restated, checked only for self-consistency
- * (noiseless round trips): "parity unpinned" against 3GPP.
+ * (noiseless round trips): "parity unpinned" against 3GPP.  So are the
+ * PUSCH scrambling sequence and channel interleaver at the end of this file
+ * (TS 36.211 / 36.212 restated): pinned by their algebra only.
  */
 #include <stdint.h>
 #include <math.h>
@@ -797,5 +799,101 @@ int orc_decode_tb(const int8_t* llr, int A, int G, int Qm, int NL, int rv, int P
     res->tb_crc_ok = tb_ok && all_ok;
     memcpy(a, b, (size_t)A);
     free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* The steps on either side of the decoder's input (Sec. IV-B          */
+/* "Decoding function": the demultiplexer hands the decoder the        */
+/* descrambled, de-interleaved LLRs of each code word).  PUSCH         */
+/* scrambling (TS 36.211 Sec. 5.3.1) and the uplink channel            */
+/* interleaver for data without control information (TS 36.212 Sec.    */
+/* 5.2.2.8).  Restated from the specifications, which this repository  */
+/* does not contain: conformance of the sequence values is "parity     */
+/* unpinned"; the pins are algebraic (primitive polynomials, jump-     */
+/* ahead, linearity, involution, bijection, a hand-worked interleaver  */
+/* case).                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Length-31 Gold sequence of TS 36.211 Sec. 7.2, bit-serial:
+ *   x1(n+31) = x1(n+3) + x1(n),                      x1(0) = 1, x1(1..30) = 0;
+ *   x2(n+31) = x2(n+3) + x2(n+2) + x2(n+1) + x2(n),  x2(i) = bit i of c_init;
+ *   c(n) = x1(n + Nc) + x2(n + Nc), Nc = 1600, all mod 2. */
+int orc_gold(uint32_t c_init, int n, uint8_t* c)
+{
+    const int Nc = 1600;
+    if (n < 0) return -1;
+    int total = Nc + n + 31;
+    uint8_t* x1 = malloc((size_t)total);
+    uint8_t* x2 = malloc((size_t)total);
+    for (int i = 0; i < 31; i++) {
+        x1[i] = (uint8_t)(i == 0);
+        x2[i] = (uint8_t)((c_init >> i) & 1u);
+    }
+    for (int i = 0; i + 31 < total; i++) {
+        x1[i + 31] = x1[i + 3] ^ x1[i];
+        x2[i + 31] = x2[i + 3] ^ x2[i + 2] ^ x2[i + 1] ^ x2[i];
+    }
+    for (int k = 0; k < n; k++) c[k] = x1[k + Nc] ^ x2[k + Nc];
+    free(x1);
+    free(x2);
+    return 0;
+}
+
+/* PUSCH scrambling initialisation (TS 36.211 Sec. 5.3.1):
+ * c_init = n_RNTI 2^14 + q 2^13 + floor(n_s / 2) 2^9 + N_ID^cell. */
+uint32_t orc_pusch_cinit(int rnti, int q, int ns, int cell)
+{
+    return (uint32_t)rnti * 16384u + (uint32_t)q * 8192u + (uint32_t)(ns / 2) * 512u +
+           (uint32_t)cell;
+}
+
+/* Channel interleaver, data only: the G bits form H' = G / (Qm NL) column
+ * vectors of Qm NL bits, written row by row into a matrix of C_mux = ncol
+ * columns and R' = H' / ncol rows, read out column by column:
+ *   tx[(c R' + r) QmNL + b] = e[(r ncol + c) QmNL + b]. */
+int orc_channel_interleave(const uint8_t* e, int G, int QmNL, int ncol, uint8_t* tx)
+{
+    if (QmNL < 1 || ncol < 1 || G % (QmNL * ncol)) return -1;
+    int H = G / QmNL, R = H / ncol;
+    for (int r = 0; r < R; r++)
+        for (int c = 0; c < ncol; c++)
+            for (int b = 0; b < QmNL; b++)
+                tx[(c * R + r) * QmNL + b] = e[(r * ncol + c) * QmNL + b];
+    return 0;
+}
+
+/* Receiver side of one code word: descramble the received LLRs (a bit sent
+ * as b ^ c(i) has its LLR's sign flipped where c(i) = 1; -128 reads as
+ * -127), then undo the channel interleaver, giving the e-sequence LLRs the
+ * de-rate-matcher takes. */
+int orc_pusch_rx(const int8_t* rx, int G, int QmNL, int ncol, uint32_t c_init, int8_t* e)
+{
+    if (QmNL < 1 || ncol < 1 || G % (QmNL * ncol)) return -1;
+    uint8_t* c = malloc((size_t)G + 1);
+    int8_t* d = malloc((size_t)G + 1);
+    orc_gold(c_init, G, c);
+    for (int i = 0; i < G; i++) {
+        int v = rx[i] < -127 ? -127 : rx[i];
+        d[i] = (int8_t)(c[i] ? -v : v);
+    }
+    int H = G / QmNL, R = H / ncol;
+    for (int r = 0; r < R; r++)
+        for (int col = 0; col < ncol; col++)
+            for (int b = 0; b < QmNL; b++)
+                e[(r * ncol + col) * QmNL + b] = d[(col * R + r) * QmNL + b];
+    free(c);
+    free(d);
+    return 0;
+}
+
+/* Transmitter side (test inputs): interleave the coded bits, then scramble. */
+int orc_pusch_tx(const uint8_t* e, int G, int QmNL, int ncol, uint32_t c_init, uint8_t* tx)
+{
+    if (orc_channel_interleave(e, G, QmNL, ncol, tx)) return -1;
+    uint8_t* c = malloc((size_t)G + 1);
+    orc_gold(c_init, G, c);
+    for (int i = 0; i < G; i++) tx[i] ^= c[i];
+    free(c);
     return 0;
 }
