@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define CRNT_VERSION 1
+#define CRNT_VERSION 2
 
 #define CRNT_OK 0
 #define CRNT_EINVAL (-1)    /* malformed argument */
@@ -61,7 +61,7 @@ typedef struct crnt_config {
     uint32_t deadline_us;    /* serving: deadline for miss accounting [1000] */
 } crnt_config;
 
-/* Per-TB parameters (32 bytes). */
+/* Per-TB parameters (40 bytes). */
 typedef struct crnt_tb_params {
     uint32_t A;          /* TB size in bits without CRC24A, multiple of 8, 16..75376 */
     uint32_t G;          /* rate-matched bits (= LLRs) of the TB, multiple of Qm*NL */
@@ -81,7 +81,14 @@ typedef struct crnt_tb_params {
     uint32_t cell, ue, harq_pid; /* HARQ process key (flags bit 0 set) */
     uint32_t flags;      /* bit 0 (CRNT_F_HARQ): combine into the library-owned
                             soft buffer of (cell, ue, harq_pid); bit 1
-                            (CRNT_F_PURGE): purge on failure, see below */
+                            (CRNT_F_PURGE): purge on failure, see below; bit 2
+                            (CRNT_F_PUSCH): received PUSCH order, see below */
+    uint32_t c_init;     /* CRNT_F_PUSCH: scrambling initialisation, 31 bits
+                            (TS 36.211 5.3.1: n_RNTI 2^14 + q 2^13 +
+                            floor(n_s / 2) 2^9 + N_ID^cell) */
+    uint16_t n_symb;     /* CRNT_F_PUSCH: channel-interleaver columns C_mux, the
+                            SC-FDMA data symbols of the subframe [0 = 12] */
+    uint16_t pad0;
 } crnt_tb_params;
 
 #define CRNT_F_HARQ 1u
@@ -92,6 +99,16 @@ typedef struct crnt_tb_params {
  * writes no payload bytes (they are left as they were).  Which CBs stop
  * depends on timing; TBs that decode are never affected. */
 #define CRNT_F_PURGE 2u
+/* Received PUSCH order (the demultiplexing ahead of the decoder, Sec. IV-B
+ * Fig. 4): the TB's G LLRs (or, for the encoder, its G output bits) are the
+ * code word as sent on the channel -- channel-interleaved for data without
+ * control information (TS 36.212 5.2.2.8: G / (Qm NL) symbols written row by
+ * row into n_symb columns, read column by column) and scrambled with the
+ * length-31 Gold sequence of c_init (TS 36.211 5.3.1 / 7.2; a set sequence
+ * bit flips an LLR's sign).  The decoder descrambles and de-interleaves
+ * before de-rate-matching; the encoder interleaves and scrambles after rate
+ * matching.  G must be a multiple of Qm NL n_symb and at most 196608. */
+#define CRNT_F_PUSCH 4u
 
 /* Per-TB result (96 bytes). */
 typedef struct crnt_tb_result {
@@ -241,7 +258,9 @@ int crnt_plan_create(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_
 int crnt_plan_get_info(const crnt_plan* plan, crnt_plan_info* info);
 /* Enqueue the decode of the planned batch on a CUDA stream (NULL = default):
  * llr (device, llr_bytes) in, out (device, out_bytes) out.  Asynchronous,
- * allocates nothing and may be captured in a CUDA graph.  The optional debug
+ * allocates nothing and may be captured in a CUDA graph.  A batch with
+ * CRNT_F_PUSCH TBs first runs the front stage (descramble, de-interleave)
+ * into the plan's scratch, allocated by crnt_plan_create.  The optional debug
  * arrays (device, may be NULL) receive per CB at offset o = sum of (K+4) of
  * the CBs before it in TB order: dbg_d[3o ..] the de-rate-matched streams
  * d0|d1|d2 (K+4 int8 each), dbg_ext[o ..] the final exchanged extrinsic
@@ -282,7 +301,8 @@ int crnt_decode_tb(crnt_ctx* ctx, const int8_t* llr, const crnt_tb_params* tb, u
  * `stream` (NULL = default) on the current device and returns after that
  * stream has finished the decode, also when it fails.  Limits: n <= 64 TBs
  * and at most 832 code blocks in total, else CRNT_ENOMEM ("exceeds the
- * static workspace"); no HARQ combining (CRNT_F_HARQ gives CRNT_EINVAL);
+ * static workspace"); no HARQ combining and no PUSCH front stage
+ * (CRNT_F_HARQ or CRNT_F_PUSCH gives CRNT_EINVAL);
  * purge on failure and all stop rules work as elsewhere.  Without a context
  * there are no per-(K, P) tables, so the kernel computes its interleaver
  * addresses and circular-buffer walk (same results).  The first call on a
@@ -296,9 +316,9 @@ int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, const int8_t
 /* ---- downlink encode (Sec. IV-B "Encoding function", Fig. 3) ------------ */
 /* Encode n TBs: CRC24A, segmentation with CRC24B and filler, turbo encode
  * (2 RSC + QPP, trellis termination), sub-block interleave and bit
- * selection from k0(rv).  bits: concatenated A/8 bytes per TB (host or
- * device); e_out: concatenated G bytes (one coded bit per byte, host or
- * device).  Device and page-locked host buffers are used in place by the
+ * selection from k0(rv), and for CRNT_F_PUSCH TBs the channel interleaver
+ * and scrambling.  bits: concatenated A/8 bytes per TB (host or device);
+ * e_out: concatenated G bytes (one coded bit per byte, host or device).  Device and page-locked host buffers are used in place by the
  * kernel; pageable host buffers are staged.  Blocking. */
 int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, const uint8_t* bits,
                       uint8_t* e_out);

@@ -22,6 +22,7 @@ MAX_CB = 16
 MAX_P = 128
 F_HARQ = 1
 F_PURGE = 2
+F_PUSCH = 4
 
 
 class CrntError(RuntimeError):
@@ -41,7 +42,9 @@ class TbParams(ctypes.Structure):
                 ("Qm", ctypes.c_uint8), ("NL", ctypes.c_uint8), ("rv", ctypes.c_uint8),
                 ("max_iter", ctypes.c_uint8), ("early_stop", ctypes.c_uint8),
                 ("new_data", ctypes.c_uint8), ("cell", ctypes.c_uint32), ("ue", ctypes.c_uint32),
-                ("harq_pid", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("harq_pid", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("c_init", ctypes.c_uint32), ("n_symb", ctypes.c_uint16),
+                ("pad0", ctypes.c_uint16)]
 
 
 class TbResult(ctypes.Structure):
@@ -164,10 +167,10 @@ def qpp_params(K):
 
 
 def make_params(A, G, Qm=2, NL=1, rv=0, max_iter=6, P=0, early_stop=1, new_data=1, cell=0,
-                ue=0, harq_pid=0, flags=0):
+                ue=0, harq_pid=0, flags=0, c_init=0, n_symb=0):
     return TbParams(A=A, G=G, P=P, Qm=Qm, NL=NL, rv=rv, max_iter=max_iter,
                     early_stop=early_stop, new_data=new_data, cell=cell, ue=ue,
-                    harq_pid=harq_pid, flags=flags)
+                    harq_pid=harq_pid, flags=flags, c_init=c_init, n_symb=n_symb)
 
 
 def params_array(tbs):

@@ -15,7 +15,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcrnt.so")
 LOADGEN = os.path.join(OUT, "crnt_loadgen")
 PROBE = os.path.join(OUT, "libcrnt_probe.so")
-UNITS = ["decode.cu", "encode.cu", "crnt_api.cu", "serve.cu", "noalloc.cu", "tune.cu"]
+UNITS = ["decode.cu", "encode.cu", "crnt_api.cu", "serve.cu", "noalloc.cu", "tune.cu",
+         "pusch.cu"]
 PROBE_UNIT = "peak.cu"
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -393,6 +393,12 @@ int validate(const crnt_tb_params& t, lte::Seg* seg) {
   if (t.G == 0 || t.G % (t.Qm * t.NL)) return CRNT_EINVAL;
   if (!lte::segment((int)t.A + 24, seg) || seg->C > CRNT_MAX_CB) return CRNT_EINVAL;
   if (lte::e_r((int)t.G, t.Qm, t.NL, seg->C, 0) < 1) return CRNT_EINVAL;
+  if (t.flags & CRNT_F_PUSCH) {
+    const int ncol = pusch_cols(t);
+    if (ncol > 14 || t.c_init >> 31 || t.G > (uint32_t)(kPuschChunk * kPuschMaxChunks) ||
+        t.G % (uint32_t)(t.Qm * t.NL * ncol))
+      return CRNT_EINVAL;
+  }
   return CRNT_OK;
 }
 
@@ -460,6 +466,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   int64_t llr_off = 0, out_off = 0, dbg_off = 0;
   uint64_t steps = 0, info_bits = 0;
   uint32_t ncb = 0;
+  bool pusch_any = false;
   for (uint32_t t = 0; t < n; t++) {
     const crnt_tb_params& tp = tbs[t];
     lte::Seg& s = pl->segs[t];
@@ -492,6 +499,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     pr.E_lo = tp.NL * tp.Qm * (Gp / s.C);
     pr.E_hi = tp.NL * tp.Qm * ((Gp + s.C - 1) / s.C);
     pr.llr = llr_base ? llr_base[t] : llr_off;
+    pusch_any |= (tp.flags & CRNT_F_PUSCH) != 0;
     pr.dbg = dbg_off;
     pr.cb0 = ncb;
     TbDesc& td = pl->tdesc[t];
@@ -519,6 +527,33 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     info_bits += tp.A;
   }
   std::sort(pl->keyed.begin(), pl->keyed.end());
+  // With TBs in received PUSCH order the front stage writes every TB's
+  // e-sequence into the plan's scratch, concatenated in TB order, and the
+  // decoder reads it there.
+  pl->pusch = pusch_any;
+  pl->n_pch = 0;
+  if (pusch_any) {
+    pl->ptb.resize(n);
+    pl->pch.clear();
+    int64_t e = 0;
+    for (uint32_t t = 0; t < n; t++) {
+      const crnt_tb_params& tp = tbs[t];
+      PuschTb& q = pl->ptb[t];
+      q.in_off = pl->pre[t].llr;
+      q.out_off = e;
+      q.G = (int32_t)tp.G;
+      q.mode = (tp.flags & CRNT_F_PUSCH) ? 1 : 0;
+      q.qmnl = tp.Qm * tp.NL;
+      q.ncol = q.mode ? pusch_cols(tp) : 1;
+      q.rows = q.G / (q.qmnl * q.ncol);
+      q.c_init = tp.c_init;
+      pl->pre[t].llr = e;
+      for (int c = 0; c * kPuschChunk < q.G; c++) pl->pch.push_back(PuschChunk{(int32_t)t, c * kPuschChunk});
+      e += tp.G;
+    }
+    pl->n_pch = (int)pl->pch.size();
+    if (!pl->d_rx.ensure((size_t)e + 16)) return CRNT_ENOMEM;
+  }
 
   // ---- one device buffer: descriptors | zeroed per-launch state | results
   // | work items.  The state (queue head, error word, TB accumulators) and
@@ -531,7 +566,9 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   const size_t off_res = off_zero + pl->scratch_zero;
   pl->res_bytes = (3 * (size_t)ncb + n + 15) & ~size_t(15);
   const size_t off_items = off_res + pl->res_bytes;
-  const size_t max_desc = off_items + sizeof(WorkItem) * ncb;
+  const size_t off_ptb = al256(off_items + sizeof(WorkItem) * ncb);
+  const size_t off_pch = off_ptb + (pusch_any ? al256(sizeof(PuschTb) * n) : 0);
+  const size_t max_desc = off_pch + (pusch_any ? sizeof(PuschChunk) * pl->pch.size() : 0);
   // The previous upload from h_desc must have completed before the staging
   // buffer is rewritten, and no launch may still read the device buffers if
   // they are about to grow.  Waiting on the upload's event (not the whole
@@ -697,6 +734,13 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   memcpy(h + off_tbs, pl->tdesc.data(), b_tbs);
   memset(h + off_zero, 0, pl->scratch_zero);
   pl->desc_bytes = off_items + sizeof(WorkItem) * pl->items.size();
+  if (pusch_any) {
+    memcpy(h + off_ptb, pl->ptb.data(), sizeof(PuschTb) * n);
+    memcpy(h + off_pch, pl->pch.data(), sizeof(PuschChunk) * pl->pch.size());
+    pl->desc_bytes = max_desc;
+  }
+  pl->off_ptb = off_ptb;
+  pl->off_pch = off_pch;
   if (cudaMemcpyAsync(pl->d_desc.p, h, pl->desc_bytes, cudaMemcpyHostToDevice, stream) !=
           cudaSuccess ||
       cudaEventRecord(pl->desc_ev, stream) != cudaSuccess)
@@ -754,6 +798,16 @@ int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, 
           cudaSuccess)
     return CRNT_EDEVICE;
   pl->state_fresh = false;
+  if (pl->pusch) {
+    // front stage: received order -> e-sequence in the plan's scratch
+    const uint8_t* dd = (const uint8_t*)pl->d_desc.p;
+    if (!pl->ctx->gold ||
+        launch_pusch(false, (const PuschTb*)(dd + pl->off_ptb), (const PuschChunk*)(dd + pl->off_pch),
+                     pl->n_pch, gold_tables_view(pl->ctx->gold), llr, (int8_t*)pl->d_rx.p,
+                     s) != cudaSuccess)
+      return CRNT_EDEVICE;
+    p.llr = (const int8_t*)pl->d_rx.p;
+  }
   if (launch_decode(p, (int)pl->info.grid, pl->smem, s) != cudaSuccess) return CRNT_EDEVICE;
   return CRNT_OK;
 }
@@ -918,6 +972,15 @@ int crnt_create(crnt_ctx** out, const crnt_config* cfg) {
     crnt_destroy(c);
     return CRNT_EDEVICE;
   }
+  // jump-ahead tables of the PUSCH scrambling sequence (37 KB)
+  {
+    const std::vector<uint32_t> g = gold_tables_host();
+    if (cudaMalloc(&c->gold, 4 * g.size()) != cudaSuccess ||
+        cudaMemcpy(c->gold, g.data(), 4 * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      crnt_destroy(c);
+      return CRNT_EDEVICE;
+    }
+  }
   // the per-(K, P) tables (interleaved-pass addresses, de-rate-matching
   // maps) of the window counts P = 0 requests get, now (others on first
   // use); without them the decoder computes addresses and walks the buffer
@@ -956,6 +1019,7 @@ int crnt_destroy(crnt_ctx* ctx) {
   if (ctx->xpowA) cudaFree(ctx->xpowA);
   if (ctx->xpowB) cudaFree(ctx->xpowB);
   if (ctx->mi_tab) cudaFree(ctx->mi_tab);
+  if (ctx->gold) cudaFree(ctx->gold);
   if (ctx->qtabs) {
     for (void* p : ctx->qtabs->chunks) cudaFree(p);
     if (ctx->qtabs->stream) cudaStreamDestroy(ctx->qtabs->stream);
@@ -1154,23 +1218,32 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   // pass 1: validate, count CBs and bytes
   std::vector<lte::Seg>& segs = ctx->enc_segs;
   segs.resize(n);
-  size_t ncb = 0;
+  size_t ncb = 0, nch = 0;
   int64_t ioff = 0, eoff = 0;
+  bool pusch_any = false;
   for (uint32_t t = 0; t < n; t++) {
     int rc = validate(tbs[t], &segs[t]);
     if (rc) return rc;
     ncb += (size_t)segs[t].C;
     ioff += tbs[t].A / 8;
     eoff += tbs[t].G;
+    pusch_any |= (tbs[t].flags & CRNT_F_PUSCH) != 0;
+    nch += (tbs[t].G + kPuschChunk - 1) / kPuschChunk;
   }
   // device or page-locked buffers are used in place; pageable ones staged
   const uint8_t* bits_view = (const uint8_t*)device_view(bits);
   uint8_t* out_view = (uint8_t*)device_view(e_out);
   const size_t b_cbs = sizeof(EncCb) * ncb, b_off = 8 * (size_t)n, b_A = 4 * (size_t)n;
-  const size_t o_off = al256(b_cbs), o_A = o_off + al256(b_off), o_bits = o_A + al256(b_A);
+  const size_t o_off = al256(b_cbs), o_A = o_off + al256(b_off);
+  // with TBs in PUSCH order: the transmit stage's descriptors, and the coded
+  // bits first go to the e-sequence scratch enc_e
+  const size_t o_ptb = o_A + al256(b_A);
+  const size_t o_pch = o_ptb + (pusch_any ? al256(sizeof(PuschTb) * n) : 0);
+  const size_t o_bits = o_pch + (pusch_any ? al256(sizeof(PuschChunk) * nch) : 0);
   const size_t total = o_bits + (bits_view ? 0 : (size_t)ioff);
   if (!ctx->stage_in.ensure(total) || !ctx->enc_host.ensure(o_bits)) return CRNT_ENOMEM;
   if (!out_view && !ctx->stage_out.ensure((size_t)eoff)) return CRNT_ENOMEM;
+  if (pusch_any && (!ctx->gold || !ctx->enc_e.ensure((size_t)eoff + 16))) return CRNT_ENOMEM;
   // pass 2: descriptors straight into page-locked staging
   uint8_t* h = (uint8_t*)ctx->enc_host.p;
   EncCb* hc = (EncCb*)h;
@@ -1209,6 +1282,25 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
     }
     ioff += tbs[t].A / 8;
   }
+  if (pusch_any) {
+    PuschTb* q = (PuschTb*)(h + o_ptb);
+    PuschChunk* ch = (PuschChunk*)(h + o_pch);
+    int64_t e = 0;
+    size_t m = 0;
+    for (uint32_t t = 0; t < n; t++) {
+      const crnt_tb_params& tp = tbs[t];
+      q[t].in_off = e;
+      q[t].out_off = e;
+      q[t].G = (int32_t)tp.G;
+      q[t].mode = (tp.flags & CRNT_F_PUSCH) ? 1 : 0;
+      q[t].qmnl = tp.Qm * tp.NL;
+      q[t].ncol = q[t].mode ? pusch_cols(tp) : 1;
+      q[t].rows = q[t].G / (q[t].qmnl * q[t].ncol);
+      q[t].c_init = tp.c_init;
+      for (int c = 0; c * kPuschChunk < q[t].G; c++) ch[m++] = PuschChunk{(int32_t)t, c * kPuschChunk};
+      e += tp.G;
+    }
+  }
   cudaStream_t st = ctx->stream;
   uint8_t* base = (uint8_t*)ctx->stage_in.p;
   if (cudaMemcpyAsync(base, h, o_bits, cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -1221,12 +1313,18 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   p.tb_in_off = (const int64_t*)(base + o_off);
   p.tb_A = (const int32_t*)(base + o_A);
   p.tb_bits = bits_view ? bits_view : base + o_bits;
-  p.e_out = out_view ? out_view : (uint8_t*)ctx->stage_out.p;
+  uint8_t* final_out = out_view ? out_view : (uint8_t*)ctx->stage_out.p;
+  p.e_out = pusch_any ? (uint8_t*)ctx->enc_e.p : final_out;
   p.xpowA = ctx->xpowA;
   p.xpowB = ctx->xpowB;
   if (launch_encode(p, (int)ncb, st) != cudaSuccess) return CRNT_EDEVICE;
+  if (pusch_any &&
+      launch_pusch(true, (const PuschTb*)(base + o_ptb), (const PuschChunk*)(base + o_pch),
+                   (int)nch, gold_tables_view(ctx->gold), (const int8_t*)ctx->enc_e.p,
+                   (int8_t*)final_out, st) != cudaSuccess)
+    return CRNT_EDEVICE;
   if (!out_view &&
-      cudaMemcpyAsync(e_out, p.e_out, (size_t)eoff, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      cudaMemcpyAsync(e_out, final_out, (size_t)eoff, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return CRNT_EDEVICE;
   if (cudaStreamSynchronize(st) != cudaSuccess) return CRNT_EDEVICE;
   return CRNT_OK;

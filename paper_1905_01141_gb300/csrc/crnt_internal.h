@@ -134,6 +134,34 @@ struct EncParams {
   const uint32_t* xpowB;      // x^(32 s) mod gCRC24B
 };
 
+// PUSCH front stage (pusch.cu): one CTA of kPuschThreads handles kPuschChunk
+// positions of one TB (32 scrambling bits per thread); TBs of G up to
+// kPuschChunk x kPuschMaxChunks bits.
+constexpr int kPuschThreads = 128;
+constexpr int kPuschChunk = 32 * kPuschThreads;
+constexpr int kPuschMaxChunks = 48;
+constexpr int kGoldWords = kPuschMaxChunks * 32 + 2 * 31 * kPuschThreads;
+
+struct PuschTb {
+  int64_t in_off;   // byte offset of the TB's input (transmitted order, or e-sequence for TX)
+  int64_t out_off;  // byte offset of its output
+  int32_t G, qmnl, ncol, rows;  // bits, bits per symbol vector, interleaver columns, rows
+  uint32_t c_init;  // scrambling initialisation (31 bits)
+  int32_t mode;     // 1: descramble + de-interleave (TX: interleave + scramble); 0: copy
+};
+struct PuschChunk {
+  int32_t tb, n0;   // TB index and first position of the chunk (multiple of kPuschChunk)
+};
+struct GoldTables {
+  const uint32_t* x1c;  // [kPuschMaxChunks] x1 state at step 1600 + kPuschChunk c
+  const uint32_t* a2c;  // [kPuschMaxChunks][31] columns of the x2 jump to that step
+  const uint32_t* t1;   // [kPuschThreads][31] columns of the x1 jump by 32 t
+  const uint32_t* t2;   // [kPuschThreads][31] columns of the x2 jump by 32 t
+};
+cudaError_t launch_pusch(bool tx, const PuschTb* tbs, const PuschChunk* chunks, int n_chunks,
+                         GoldTables g, const int8_t* in, int8_t* out, cudaStream_t s);
+GoldTables gold_tables_view(const uint32_t* d);
+
 // Kernel launchers (decode.cu / encode.cu).  The decode kernel instantiation
 // is chosen from p.radix4_any, p.qtab_all and p.pair_any.
 cudaError_t launch_decode(const DecParams& p, int grid, int smem, cudaStream_t s);

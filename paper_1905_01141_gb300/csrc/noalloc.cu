@@ -223,7 +223,8 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     lte::Seg& sg = h_segs[t];
     rc = validate(tp, &sg);
     if (rc) return rc;
-    if (tp.flags & CRNT_F_HARQ) return CRNT_EINVAL;  // no soft-buffer arena here
+    if (tp.flags & CRNT_F_HARQ) return CRNT_EINVAL;   // no soft-buffer arena here
+    if (tp.flags & CRNT_F_PUSCH) return CRNT_EINVAL;  // no front-stage scratch here
     if (ncb + sg.C > kStaticCbs) return CRNT_ENOMEM;
     TbDesc& td = h_tbs[t];
     memset(&td, 0, sizeof td);

@@ -89,12 +89,14 @@ struct crnt_ctx {
   uint32_t* xpowA = nullptr;
   uint32_t* xpowB = nullptr;
   int32_t* mi_tab = nullptr;  // [kMiTable] table of the mutual-information stop rule
+  uint32_t* gold = nullptr;   // [kGoldWords] jump-ahead tables of the PUSCH scrambling sequence
   crnt::QTabs* qtabs = nullptr;  // interleaved-pass address tables
   crnt::HarqPool harq;
   std::mutex harq_mu;     // guards harq
   std::mutex stage_mu;    // guards the staging buffers and the cached plan
   crnt::Buf stage_in, stage_out;
   crnt::Buf enc_host{true};             // page-locked encoder descriptor staging
+  crnt::Buf enc_e;                       // encoder's e-sequence ahead of the PUSCH transmit stage
   std::vector<crnt::lte::Seg> enc_segs;  // encoder planning scratch
   // crnt_decode_batch splits a batch into up to kBatchChunks chunks, each
   // with a reused plan and its own stream, so that planning and copying a
@@ -142,6 +144,15 @@ struct crnt_plan {
   }
   size_t desc_bytes = 0, zero_off = 0, scratch_zero = 0, res_bytes = 0;
   crnt::DecParams prm{};
+  // PUSCH front stage (TBs with CRNT_F_PUSCH): per-TB and per-chunk
+  // descriptors (also in d_desc at off_ptb / off_pch) and the e-sequence
+  // scratch the decoder then reads
+  bool pusch = false;
+  std::vector<crnt::PuschTb> ptb;
+  std::vector<crnt::PuschChunk> pch;
+  int n_pch = 0;
+  size_t off_ptb = 0, off_pch = 0;
+  crnt::Buf d_rx;
 };
 
 namespace crnt {
@@ -188,5 +199,10 @@ extern thread_local int t_shape_override;
 // Window count used for CB size K when a TB requests P (0 = table / built-in).
 int clamp_p(int K, int P);
 void serving_stop(crnt_ctx* ctx);
+// The jump-ahead tables of the PUSCH scrambling sequence (kGoldWords words,
+// layout of GoldTables), built on the host.
+std::vector<uint32_t> gold_tables_host();
+// Interleaver columns of a TB with CRNT_F_PUSCH (n_symb, 0 = 12).
+inline int pusch_cols(const crnt_tb_params& t) { return t.n_symb ? t.n_symb : 12; }
 int64_t now_ns();
 }  // namespace crnt

@@ -188,3 +188,19 @@ def tti_batch(seed, n_tb=320, amin=16, amax=75376):
         snr_th = 10.0 * math.log10(2.0 ** (r_eff * Qm) - 1.0) + gap
         out.append(dict(A=a, G=G, Qm=Qm, snr_db=snr_th + 6.0 * float(snr_u[t]) - 3.0))
     return out
+
+
+def pusch_batch(seed, n_tb=320, amin=16, amax=75376):
+    """Shapes of a TTI whose TBs arrive in PUSCH order: the TTI shapes with G
+    rounded up to whole PRBs (144 resource elements of 12 SC-FDMA data
+    symbols: G a multiple of 144 Qm, at most 100 PRBs), plus a seeded 31-bit
+    scrambling initialisation per TB (c_init) and the interleaver's 12
+    columns."""
+    out = []
+    cinit = randint(seed, 9, n_tb, 0, (1 << 31) - 1)
+    for t, s in enumerate(tti_batch(seed, n_tb=n_tb, amin=amin, amax=amax)):
+        per = 144 * s["Qm"]
+        G = min(100 * per, per * int(math.ceil(s["G"] / per)))
+        out.append(dict(A=s["A"], G=G, Qm=s["Qm"], snr_db=s["snr_db"], c_init=int(cinit[t]),
+                        n_symb=12))
+    return out

@@ -30,10 +30,11 @@ def test_exports_every_declared_symbol(crnt_lib):
 
 
 def test_struct_sizes(crnt_lib):
-    assert ctypes.sizeof(crnt_lib.TbParams) == 32
+    assert ctypes.sizeof(crnt_lib.TbParams) == 40
     assert ctypes.sizeof(crnt_lib.TbResult) == 96
     assert ctypes.sizeof(crnt_lib.CbLayout) == 40
-    assert crnt_lib.version() == 1
+    assert ctypes.sizeof(crnt_lib.PlanInfo) == 64
+    assert crnt_lib.version() == 2
     assert crnt_lib.strerror(-1) == "invalid argument"
 
 
@@ -208,3 +209,18 @@ def test_load_generator_built_and_checks_its_arguments(crnt_lib):
     r = subprocess.run([crnt_build.LOADGEN, "--threads", "2", "--poisson", "/nonexistent", "8",
                         "1", "0.1", "1", "4"], capture_output=True, text=True, timeout=60)
     assert r.returncode == 2
+
+
+def test_pusch_parameters_validated(crnt_lib):
+    # CRNT_F_PUSCH: G a multiple of Qm NL n_symb, n_symb at most 14, 31-bit
+    # c_init, G at most 196608 (host-side check, no GPU)
+    F = crnt_lib.F_PUSCH
+    for tb in (dict(A=1000, G=1202, Qm=2, flags=F),
+               dict(A=1000, G=1440, Qm=2, n_symb=15, flags=F),
+               dict(A=1000, G=1440, Qm=2, c_init=1 << 31, flags=F),
+               dict(A=75376, G=196608 + 144 * 2, Qm=2, n_symb=1, flags=F)):
+        with pytest.raises(crnt_lib.CrntError) as ei:
+            crnt_lib.tb_layout(tb)
+        assert ei.value.code == crnt_lib.EINVAL
+    assert len(crnt_lib.tb_layout(dict(A=1000, G=1440, Qm=2, flags=F))) == 1
+    assert len(crnt_lib.tb_layout(dict(A=1000, G=1202, Qm=2))) == 1  # no flag: any G

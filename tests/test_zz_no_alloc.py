@@ -94,9 +94,10 @@ def test_static_decode_rejects_beyond_its_limits(crnt_lib):
     with pytest.raises(crnt_lib.CrntError) as ei:
         crnt_lib.decode_batch_static([dict(A=16, G=132)] * 65, llr, out)
     assert ei.value.code == crnt_lib.ENOMEM
-    with pytest.raises(crnt_lib.CrntError) as ei:
-        crnt_lib.decode_batch_static([dict(A=16, G=132, flags=crnt_lib.F_HARQ)], llr, out)
-    assert ei.value.code == crnt_lib.EINVAL
+    for flags in (crnt_lib.F_HARQ, crnt_lib.F_PUSCH):
+        with pytest.raises(crnt_lib.CrntError) as ei:
+            crnt_lib.decode_batch_static([dict(A=16, G=144, flags=flags)], llr, out)
+        assert ei.value.code == crnt_lib.EINVAL
     # pageable host buffers: refused before anything is launched
     llr_h = np.zeros(132, dtype=np.int8)
     out_h = np.zeros(2, dtype=np.uint8)
