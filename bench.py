@@ -392,6 +392,7 @@ def run_ours(args):
             "payload_matches_truth": truth}
 
     if not args.no_extras and rank == 0:
+        line["steady"] = steady_leg(plan, llr_d, out_d, flush, stream, info, local)
         line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
         line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
         tt = (None if args.no_autotune
@@ -403,6 +404,8 @@ def run_ours(args):
                                               cells_list=(24, 32, 40, 48, 56, 64, 72),
                                               tune_table=tt, poisson=True)
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
+        line["captor"] = captor_leg(crnt, ctx, tbs, llr_d, dev)
+        line["pusch"] = pusch_leg(crnt, ctx, dev, args.seed, flush)
         line["radix4_forward"] = radix_leg(crnt, ctx, tbs, llr_d, flush, dev)
         line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
         if not args.no_cpu_baseline and ws == 1:
@@ -451,6 +454,118 @@ def radix_leg(crnt, ctx, tbs, llr_d, flush, dev, steps=60):
         crnt.tune_radix_set(old)
     out["outputs_identical"] = outs[0] == outs[1]
     out["radix4_vs_installed"] = out["installed"]["ms_per_launch"] / out["radix4_all_K"]["ms_per_launch"]
+    return out
+
+
+def steady_leg(plan, llr_d, out_d, flush, stream, info, device, steps=1500):
+    """The timed step repeated for about a second (L2 flushed before each
+    launch, CUDA events around each), with nvidia-smi clocks sampled over it:
+    mean, median and p99 device time per TTI."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    clk = ClockSampler(device)
+    torch.cuda.synchronize()
+    clk.start()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            plan.launch(llr_d, out_d, stream.cuda_stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    mean = sum(ms) / len(ms)
+    return {"steps": steps, "ms_mean": mean, "ms_median": ms[len(ms) // 2],
+            "ms_p99": ms[int(0.99 * (len(ms) - 1))], "gbit_s": info["info_bits"] / mean / 1e6,
+            "clocks": clocks}
+
+
+def captor_leg(crnt, ctx, tbs, llr_d, dev):
+    """The paper's performance captor on the TTI workload with early stop on:
+    per-CB delays from the kernel's %globaltimer stamps -- pre-processing
+    (queue to de-rate-matched), channel coding (the turbo iterations),
+    post-processing (payload and TB CRC) -- and the histogram of iterations
+    run."""
+    import torch
+    p = [dict(t, early_stop=1) for t in tbs]
+    plan = ctx.plan(p)
+    plan.set_timing(True)
+    st = torch.cuda.Stream(device=dev)
+    od = torch.zeros(plan.info["out_bytes"], dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(st):
+        plan.launch(llr_d, od, st.cuda_stream)
+        plan.launch(llr_d, od, st.cuda_stream)
+    tm = plan.timing(st.cuda_stream)
+    plan.close()
+    pre = (tm["t_derm_ns"] - tm["t_start_ns"]) / 1e3
+    cod = (tm["t_iter_ns"] - tm["t_derm_ns"]) / 1e3
+    post = (tm["t_done_ns"] - tm["t_iter_ns"]) / 1e3
+    hist = np.bincount(tm["iterations"], minlength=7)[1:].tolist()
+    return {"cbs": int(len(tm)), "launch_span_us": float((tm["t_done_ns"].max()
+                                                          - tm["t_start_ns"].min()) / 1e3),
+            "mean_us": {"pre_processing": float(pre.mean()), "channel_coding": float(cod.mean()),
+                        "post_processing": float(post.mean())},
+            "share": {k: float(v.sum() / (pre.sum() + cod.sum() + post.sum()))
+                      for k, v in (("pre_processing", pre), ("channel_coding", cod),
+                                   ("post_processing", post))},
+            "iterations_histogram_1_to_6": hist,
+            "what": "per CB, from the GPU %globaltimer stamps of its work item; TTI workload "
+                    "with early stop on"}
+
+
+def pusch_leg(crnt, ctx, dev, seed, flush, steps=50):
+    """The TTI in received PUSCH order (shapes rounded to whole PRBs, each TB
+    scrambled with its own c_init and channel-interleaved over 12 columns):
+    encoded by the library's encoder in transmit order, decoded with the
+    front stage (descrambling, de-interleaving) ahead of the fused decode;
+    device time per TTI next to the same TBs decoded from the e-sequence
+    order, and the payload check."""
+    import torch
+    shapes = synth.pusch_batch(seed + 7, n_tb=320)
+    base = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=6, early_stop=0) for s in shapes]
+    pus = [dict(b, flags=crnt.F_PUSCH, c_init=s["c_init"], n_symb=s["n_symb"])
+           for b, s in zip(base, shapes)]
+    pay = np.concatenate([np.packbits(synth.bits(seed + 7, 5000 + t, s["A"]))
+                          for t, s in enumerate(shapes)])
+    out = {}
+    st = torch.cuda.Stream(device=dev)
+    for name, tbs in (("e_sequence_order", base), ("pusch_order", pus)):
+        coded = np.zeros(sum(s["G"] for s in shapes), dtype=np.uint8)
+        ctx.encode_batch(tbs, pay, coded)
+        llr = channel(shapes, coded, seed + 7)
+        plan = ctx.plan(tbs)
+        ld = torch.from_numpy(llr).to(dev)
+        od = torch.zeros(plan.info["out_bytes"], dtype=torch.uint8, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                flush.zero_()
+                plan.launch(ld, od, st.cuda_stream)
+            for a, b in ev:
+                flush.zero_()
+                a.record(st)
+                plan.launch(ld, od, st.cuda_stream)
+                b.record(st)
+        torch.cuda.synchronize()
+        res = plan.results(st.cuda_stream)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        oh = od.cpu().numpy()
+        off = np.cumsum([0] + [t["A"] // 8 for t in tbs])
+        good = [t for t, r in enumerate(res) if r["tb_crc_ok"]]
+        same = sum(int(np.array_equal(oh[off[t]:off[t + 1]], pay[off[t]:off[t + 1]]))
+                   for t in good)
+        out[name] = {"ms_per_tti": ms, "gbit_s": plan.info["info_bits"] / ms / 1e6,
+                     "crc_ok": len(good), "crc_ok_payload_equal": same,
+                     "launches_per_tti": 2 if name == "pusch_order" else 1}
+        plan.close()
+    out["front_stage_us"] = (out["pusch_order"]["ms_per_tti"]
+                             - out["e_sequence_order"]["ms_per_tti"]) * 1e3
+    out["what"] = ("320 TBs (TTI shapes, G rounded to PRBs), L2 flushed before each launch; "
+                   "the PUSCH-order decode runs the descramble/de-interleave kernel and the "
+                   "fused decode")
     return out
 
 

@@ -59,6 +59,10 @@ typedef struct crnt_config {
     uint64_t mem_budget;     /* device bytes for soft buffers + in-flight work [8 GiB] */
     uint32_t max_inflight;   /* serving: TBs on the device at once [4096] */
     uint32_t deadline_us;    /* serving: deadline for miss accounting [1000] */
+    uint32_t pair_min_cbs;   /* CB pairs (shape table) only in batches of at least
+                                this many CBs [two waves of one-CB CTAs: 6 x SMs];
+                                1 = in every batch */
+    uint32_t pad0;
 } crnt_config;
 
 /* Per-TB parameters (40 bytes). */
@@ -270,6 +274,29 @@ int crnt_plan_launch_debug(crnt_plan* plan, const int8_t* llr, uint8_t* out, voi
                            int8_t* dbg_d, int16_t* dbg_ext, uint8_t* dbg_hard);
 /* Wait for the stream and fill res[n] (host).  CRNT_EDEVICE on a CUDA error. */
 int crnt_plan_results(crnt_plan* plan, crnt_tb_result* res, void* stream);
+
+/* Per-CB timestamps of a launch (the paper's performance captor, Sec. IV-B:
+ * the delay of each CB split into pre-processing -- de-rate-matching --,
+ * channel coding -- the turbo iterations -- and post-processing -- hard
+ * decisions into the TB, the TB CRC), taken on the GPU's %globaltimer
+ * (nanoseconds).  The stamps belong to the CB's work item, so CBs decoded
+ * together by one CTA share them. */
+typedef struct crnt_cb_timing {
+    uint32_t tb, r;        /* TB index in the plan, CB index in the TB */
+    uint64_t t_start_ns;   /* a CTA took the CB's work item from the queue */
+    uint64_t t_derm_ns;    /* its LLRs were de-rate-matched */
+    uint64_t t_iter_ns;    /* its turbo iterations ended */
+    uint64_t t_done_ns;    /* its payload bits and results were written */
+    uint8_t iterations;    /* iterations run */
+    uint8_t pad[7];
+} crnt_cb_timing;
+/* Record the timestamps in every later launch of the plan (enable = 1; the
+ * first call allocates their device and page-locked buffers, 32 + 32 bytes
+ * per CB) or stop recording (0). */
+int crnt_plan_set_timing(crnt_plan* plan, int enable);
+/* After a launch with timing on: wait for the stream and fill out[n_cb]
+ * (host), CBs in TB order.  CRNT_EINVAL if timing is off or n < n_cb. */
+int crnt_plan_timing(crnt_plan* plan, crnt_cb_timing* out, uint32_t n, void* stream);
 int crnt_plan_destroy(crnt_plan* plan);
 
 /* Blocking decode of n TBs.  llr: concatenated G LLRs of every TB (host or

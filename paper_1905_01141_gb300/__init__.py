@@ -34,7 +34,8 @@ class CrntError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("harq_slots", ctypes.c_uint32),
                 ("mem_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
-                ("deadline_us", ctypes.c_uint32)]
+                ("deadline_us", ctypes.c_uint32), ("pair_min_cbs", ctypes.c_uint32),
+                ("pad0", ctypes.c_uint32)]
 
 
 class TbParams(ctypes.Structure):
@@ -65,6 +66,13 @@ class TbResult(ctypes.Structure):
                     sat_passes=self.sat_passes,
                     ticket=self.ticket, t_submit_ns=self.t_submit_ns,
                     t_start_ns=self.t_start_ns, t_done_ns=self.t_done_ns)
+
+
+class CbTiming(ctypes.Structure):
+    _fields_ = [("tb", ctypes.c_uint32), ("r", ctypes.c_uint32), ("t_start_ns", ctypes.c_uint64),
+                ("t_derm_ns", ctypes.c_uint64), ("t_iter_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64), ("iterations", ctypes.c_uint8),
+                ("pad", ctypes.c_uint8 * 7)]
 
 
 class CbLayout(ctypes.Structure):
@@ -101,6 +109,8 @@ SIGNATURES = {
     "crnt_plan_launch_debug": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "crnt_plan_results": (ctypes.c_int, [_P, _P, _P]),
     "crnt_plan_destroy": (ctypes.c_int, [_P]),
+    "crnt_plan_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "crnt_plan_timing": (ctypes.c_int, [_P, _P, _U32, _P]),
     "crnt_decode_batch": (ctypes.c_int, [_P, _P, _U32, _P, _P, _P]),
     "crnt_decode_tb": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "crnt_encode_batch": (ctypes.c_int, [_P, _P, _U32, _P, _P]),
@@ -261,10 +271,12 @@ def tune_shape_set(table):
 class Context:
     """A library context on one CUDA device."""
 
-    def __init__(self, device=0, harq_slots=0, mem_budget=0, max_inflight=0, deadline_us=0):
+    def __init__(self, device=0, harq_slots=0, mem_budget=0, max_inflight=0, deadline_us=0,
+                 pair_min_cbs=0):
         L = load()
         cfg = Config(device=device, harq_slots=harq_slots, mem_budget=mem_budget,
-                     max_inflight=max_inflight, deadline_us=deadline_us)
+                     max_inflight=max_inflight, deadline_us=deadline_us,
+                     pair_min_cbs=pair_min_cbs)
         h = ctypes.c_void_p()
         _check(L.crnt_create(ctypes.byref(h), ctypes.byref(cfg)), "crnt_create")
         self.h = h
@@ -392,6 +404,18 @@ class Plan:
         res = (TbResult * len(self.params))()
         _check(load().crnt_plan_results(self.h, res, stream or None), "crnt_plan_results")
         return [r.as_dict() for r in res]
+
+    def set_timing(self, enable=True):
+        """crnt_plan_set_timing: record per-CB timestamps in later launches."""
+        _check(load().crnt_plan_set_timing(self.h, int(enable)), "crnt_plan_set_timing")
+
+    def timing(self, stream=0):
+        """crnt_plan_timing: per-CB timestamps of the last launch (numpy
+        structured array, CBs in TB order)."""
+        n = self.info["n_cb"]
+        out = (CbTiming * n)()
+        _check(load().crnt_plan_timing(self.h, out, n, stream or None), "crnt_plan_timing")
+        return np.ctypeslib.as_array(out)
 
     def close(self):
         if self.h:

@@ -537,19 +537,10 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     pl->pch.clear();
     int64_t e = 0;
     for (uint32_t t = 0; t < n; t++) {
-      const crnt_tb_params& tp = tbs[t];
-      PuschTb& q = pl->ptb[t];
-      q.in_off = pl->pre[t].llr;
-      q.out_off = e;
-      q.G = (int32_t)tp.G;
-      q.mode = (tp.flags & CRNT_F_PUSCH) ? 1 : 0;
-      q.qmnl = tp.Qm * tp.NL;
-      q.ncol = q.mode ? pusch_cols(tp) : 1;
-      q.rows = q.G / (q.qmnl * q.ncol);
-      q.c_init = tp.c_init;
+      pusch_tb(tbs[t], pl->pre[t].llr, e, &pl->ptb[t]);
+      pusch_tiles(pl->ptb[t], (int)t, pl->pch);
       pl->pre[t].llr = e;
-      for (int c = 0; c * kPuschChunk < q.G; c++) pl->pch.push_back(PuschChunk{(int32_t)t, c * kPuschChunk});
-      e += tp.G;
+      e += tbs[t].G;
     }
     pl->n_pch = (int)pl->pch.size();
     if (!pl->d_rx.ensure((size_t)e + 16)) return CRNT_ENOMEM;
@@ -661,7 +652,13 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   // pair kernel reads them) and the CB uses the radix-2 recursion; an odd
   // CB left over runs alone.  Otherwise as many CBs as the CTA's threads
   // and shared memory allow.
-  const bool allow_pairs = qtab_all && ncb > 1;
+  // Pairs shorten a batch that fills at least two waves of CTAs in either
+  // shape; a smaller batch (one subframe, a few TBs) finishes sooner with
+  // one CB per thread (more CTAs in flight, one CB each), so it runs that
+  // way -- the shape never changes a decoded value.
+  const int pair_min_cbs =
+      ctx->cfg.pair_min_cbs ? (int)ctx->cfg.pair_min_cbs : 2 * kCtasPerSm * ctx->num_sms;
+  const bool allow_pairs = qtab_all && (int)ncb >= pair_min_cbs;
   int max_item_bytes = 0;
   bool pair_any = false;
   WorkItem wi{0, 0, 0, 0};
@@ -701,6 +698,8 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   if (wi.n) close_item();
   pl->n_cb = ncb;
   pl->smem = kSmemFixed + max_item_bytes;
+  if (pl->timing && (!pl->d_time.ensure(32 * (size_t)ncb) || !pl->h_time.ensure(32 * (size_t)ncb)))
+    return CRNT_ENOMEM;
   static std::mutex occ_mu;
   static std::map<int, int> occ_cache;  // (dynamic smem, kernel flags) -> resident CTAs per SM
   int per_sm;
@@ -791,6 +790,7 @@ int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, 
   p.dbg_d = dbg_d;
   p.dbg_ext = dbg_ext;
   p.dbg_hard = dbg_hard;
+  p.cb_time = pl->timing ? (uint64_t*)pl->d_time.p : nullptr;
   // the queue head and the TB accumulators start at zero: the upload of
   // plan_build wrote zeros, a later launch of the same plan clears them
   if (!(state_uploaded && pl->state_fresh) &&
@@ -1081,6 +1081,42 @@ int crnt_plan_results(crnt_plan* plan, crnt_tb_result* res, void* stream) {
   return CRNT_OK;
 }
 
+int crnt_plan_set_timing(crnt_plan* plan, int enable) {
+  if (!plan) return CRNT_EINVAL;
+  cudaSetDevice(plan->ctx->device);
+  if (enable && (!plan->d_time.ensure(32 * (size_t)plan->n_cb + 32) ||
+                 !plan->h_time.ensure(32 * (size_t)plan->n_cb + 32)))
+    return CRNT_ENOMEM;
+  plan->timing = enable != 0;
+  return CRNT_OK;
+}
+
+int crnt_plan_timing(crnt_plan* plan, crnt_cb_timing* out, uint32_t n, void* stream) {
+  if (!plan || !out || !plan->timing || n < plan->n_cb) return CRNT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ncb = plan->n_cb;
+  if (plan_fetch_results(plan, s) != CRNT_OK ||
+      cudaMemcpyAsync(plan->h_time.p, plan->d_time.p, 32 * ncb, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CRNT_EDEVICE;
+  const uint64_t* t = (const uint64_t*)plan->h_time.p;
+  const uint8_t* runs = (const uint8_t*)plan->h_res.p + plan->scratch_zero + 2 * ncb;
+  for (size_t i = 0; i < ncb; i++) {
+    const int tb = plan->cb_tb[i], r = plan->cb_r[i];
+    crnt_cb_timing& o = out[plan->tdesc[tb].cb0 + r];
+    memset(&o, 0, sizeof o);
+    o.tb = (uint32_t)tb;
+    o.r = (uint32_t)r;
+    o.t_start_ns = t[4 * i];
+    o.t_derm_ns = t[4 * i + 1];
+    o.t_iter_ns = t[4 * i + 2];
+    o.t_done_ns = t[4 * i + 3];
+    o.iterations = runs[i];
+  }
+  return CRNT_OK;
+}
+
 int crnt_plan_destroy(crnt_plan* plan) {
   if (!plan) return CRNT_EINVAL;
   cudaSetDevice(plan->ctx->device);
@@ -1218,7 +1254,7 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   // pass 1: validate, count CBs and bytes
   std::vector<lte::Seg>& segs = ctx->enc_segs;
   segs.resize(n);
-  size_t ncb = 0, nch = 0;
+  size_t ncb = 0;
   int64_t ioff = 0, eoff = 0;
   bool pusch_any = false;
   for (uint32_t t = 0; t < n; t++) {
@@ -1228,8 +1264,21 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
     ioff += tbs[t].A / 8;
     eoff += tbs[t].G;
     pusch_any |= (tbs[t].flags & CRNT_F_PUSCH) != 0;
-    nch += (tbs[t].G + kPuschChunk - 1) / kPuschChunk;
   }
+  // the transmit stage's descriptors and tiles
+  std::vector<PuschTb>& eq = ctx->enc_ptb;
+  std::vector<PuschChunk>& ech = ctx->enc_pch;
+  eq.resize(pusch_any ? n : 0);
+  ech.clear();
+  if (pusch_any) {
+    int64_t e = 0;
+    for (uint32_t t = 0; t < n; t++) {
+      pusch_tb(tbs[t], e, e, &eq[t]);
+      pusch_tiles(eq[t], (int)t, ech);
+      e += tbs[t].G;
+    }
+  }
+  const size_t nch = ech.size();
   // device or page-locked buffers are used in place; pageable ones staged
   const uint8_t* bits_view = (const uint8_t*)device_view(bits);
   uint8_t* out_view = (uint8_t*)device_view(e_out);
@@ -1283,23 +1332,8 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
     ioff += tbs[t].A / 8;
   }
   if (pusch_any) {
-    PuschTb* q = (PuschTb*)(h + o_ptb);
-    PuschChunk* ch = (PuschChunk*)(h + o_pch);
-    int64_t e = 0;
-    size_t m = 0;
-    for (uint32_t t = 0; t < n; t++) {
-      const crnt_tb_params& tp = tbs[t];
-      q[t].in_off = e;
-      q[t].out_off = e;
-      q[t].G = (int32_t)tp.G;
-      q[t].mode = (tp.flags & CRNT_F_PUSCH) ? 1 : 0;
-      q[t].qmnl = tp.Qm * tp.NL;
-      q[t].ncol = q[t].mode ? pusch_cols(tp) : 1;
-      q[t].rows = q[t].G / (q[t].qmnl * q[t].ncol);
-      q[t].c_init = tp.c_init;
-      for (int c = 0; c * kPuschChunk < q[t].G; c++) ch[m++] = PuschChunk{(int32_t)t, c * kPuschChunk};
-      e += tp.G;
-    }
+    memcpy(h + o_ptb, eq.data(), sizeof(PuschTb) * n);
+    memcpy(h + o_pch, ech.data(), sizeof(PuschChunk) * nch);
   }
   cudaStream_t st = ctx->stream;
   uint8_t* base = (uint8_t*)ctx->stage_in.p;

@@ -101,6 +101,8 @@ struct DecParams {
   uint8_t* cb_runs;       // [n_cbs] iterations run (may be null)
   uint8_t* tb_ok;         // [n_tbs]
   uint32_t* tb_sat;       // [n_tbs] window passes on the saturating path (may be null)
+  uint64_t* cb_time;      // optional: [4 n_cbs] by sorted CB index, %globaltimer ns at
+                          // dequeue, de-rate-matched, iterations done, results written
   const uint32_t* xpowA;  // x^(32 s) mod gCRC24A, s < 2400
   const uint32_t* xpowB;  // x^(32 s) mod gCRC24B, s < 200
   const int32_t* mi_tab;  // [kMiTable] mutual-information table (stop rule 2)
@@ -134,8 +136,9 @@ struct EncParams {
   const uint32_t* xpowB;      // x^(32 s) mod gCRC24B
 };
 
-// PUSCH front stage (pusch.cu): one CTA of kPuschThreads handles kPuschChunk
-// positions of one TB (32 scrambling bits per thread); TBs of G up to
+// PUSCH front stage (pusch.cu): one CTA of kPuschThreads handles one tile of
+// whole interleaver rows of a TB; the scrambling sequence's jump-ahead
+// tables have a coarse step of kPuschChunk positions, so TBs of G up to
 // kPuschChunk x kPuschMaxChunks bits.
 constexpr int kPuschThreads = 128;
 constexpr int kPuschChunk = 32 * kPuschThreads;
@@ -150,8 +153,14 @@ struct PuschTb {
   int32_t mode;     // 1: descramble + de-interleave (TX: interleave + scramble); 0: copy
 };
 struct PuschChunk {
-  int32_t tb, n0;   // TB index and first position of the chunk (multiple of kPuschChunk)
+  int32_t tb, n0;   // TB index and first interleaver row of the tile
 };
+// One front-stage tile: whole interleaver rows, at most kPuschTile bytes.
+constexpr int kPuschTile = 8192;
+__host__ __device__ inline int pusch_tile_rows(int qmnl, int ncol) {
+  const int r = kPuschTile / (qmnl * ncol);
+  return r > 0 ? r : 1;
+}
 struct GoldTables {
   const uint32_t* x1c;  // [kPuschMaxChunks] x1 state at step 1600 + kPuschChunk c
   const uint32_t* a2c;  // [kPuschMaxChunks][31] columns of the x2 jump to that step

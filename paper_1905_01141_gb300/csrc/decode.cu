@@ -1368,6 +1368,18 @@ __device__ __forceinline__ void siso_pass_pair(const CbDesc* __restrict__ dA,
   __syncthreads();
 }
 
+// The GPU's global nanosecond timer (the performance captor's clock).
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Timestamp k of the CBs cb0 .. cb0 + n - 1 (thread 0 of the item).
+__device__ __forceinline__ void stamp(const DecParams& prm, int cb0, int n, int k, uint64_t t) {
+  if (prm.cb_time)
+    for (int g = 0; g < n; g++) prm.cb_time[4 * (cb0 + g) + k] = t;
+}
+
 // Stop rule of one CB after iteration it (thread p = 0 of the CB, after the
 // CRC shares of a checked iteration were combined in fl[2]): CRC pass, the
 // mutual-information rule, the iteration limit, or a purge of its TB.
@@ -1516,6 +1528,7 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
   const int p = tid;
   const CbSlot sA = make_pair_slot(slots, K, P, W, 0);
   const CbSlot sB = make_pair_slot(slots, K, P, W, 1);
+  if (tid == 0) stamp(prm, wi.cb0, 2, 0, gtime());
   // ---- phase 0: de-rate-matching of both CBs, one after the other (they
   // share the staging area), and the pair's extrinsics cleared
   {
@@ -1535,6 +1548,7 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
     *s_maxit = max((int)dA->max_iter, (int)dB->max_iter);
   }
   __syncthreads();
+  if (tid == 0) stamp(prm, wi.cb0, 2, 1, gtime());
   if (prm.dbg_d) {
     debug_streams(prm, *dA, sA, tid, kThreads);
     debug_streams(prm, *dB, sB, tid, kThreads);
@@ -1561,6 +1575,7 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
     if (*s_remaining == 0) break;
   }
   // ---- phase 2: results of both CBs
+  if (tid == 0) stamp(prm, wi.cb0, 2, 2, gtime());
   if (mine) {
     finish_share(prm, *dA, sA, p, tabA);
     finish_share(prm, *dB, sB, p, tabA);
@@ -1569,6 +1584,7 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
   if (tid == 0) {
     finish_cb(prm, *dA, sA, wi.cb0, tabA);
     finish_cb(prm, *dB, sB, wi.cb0 + 1, tabA);
+    stamp(prm, wi.cb0, 2, 3, gtime());
   }
 }
 
@@ -1585,6 +1601,7 @@ __device__ __forceinline__ void run_single_item(const DecParams& prm, const Work
   const int p = tid - mycb * P;
   const bool mine = mycb < G;
   const CbDesc* dp = cbs + (mine ? mycb : 0);
+  if (tid == 0) stamp(prm, wi.cb0, G, 0, gtime());
 
   // ---- phase 0: de-rate-matching of every CB of the item (LLRs staged
   // in shared memory first)
@@ -1606,6 +1623,7 @@ __device__ __forceinline__ void run_single_item(const DecParams& prm, const Work
     *s_maxit = mx;
   }
   __syncthreads();
+  if (tid == 0) stamp(prm, wi.cb0, G, 1, gtime());
   uint8_t* mybase = slots + (mine ? mycb : 0) * wi.smem_per_cb;
   int* const fl = make_slot(mybase, dp->K, dp->P, dp->W).flags;
   if (prm.dbg_d) {
@@ -1637,11 +1655,16 @@ __device__ __forceinline__ void run_single_item(const DecParams& prm, const Work
   }
 
   // ---- phase 2: results, payload bytes, TB CRC, debug copies
+  if (tid == 0) stamp(prm, wi.cb0, G, 2, gtime());
   const CbDesc d = *dp;
   const CbSlot sl = make_slot(mybase, d.K, d.P, d.W);
   if (mine) finish_share(prm, d, sl, p, tabA);
   __syncthreads();
   if (mine && p == 0) finish_cb(prm, d, sl, wi.cb0 + mycb, tabA);
+  if (prm.cb_time) {
+    __syncthreads();
+    if (tid == 0) stamp(prm, wi.cb0, G, 3, gtime());
+  }
 }
 // The same, not inlined: the pair kernel runs one-CB items rarely, and the
 // pair path keeps the kernel's registers to itself.

@@ -268,9 +268,11 @@ int main(int argc, char** argv) {
   cfg.max_inflight = 65536;
   crnt_ctx* ctx = nullptr;
   if (crnt_create(&ctx, &cfg) != CRNT_OK) return 3;
-  // warm-up pass (not reported): the serving loop's buffers come up here
-  run_point(ctx, par, ptr, ues, std::min(16, max_cells), 0.3, retx, seed + 1, extra_flags,
-            poisson, nthreads);
+  // warm-up passes (not reported): the serving loop's buffers, the HARQ
+  // arena and every kernel the mix uses come up here
+  for (int w = 0; w < 2; w++)
+    run_point(ctx, par, ptr, ues, std::min(16 << w, max_cells), 0.3, retx, seed + 1 + w,
+              extra_flags, poisson, nthreads);
   for (int a = 6; a < argc; a++) {
     const int cells = atoi(argv[a]);
     const Point p =
@@ -280,7 +282,9 @@ int main(int argc, char** argv) {
            "\"gbit_s\": %.4f}\n",
            p.cells, p.tbs, p.subframes, p.refused, p.errors, p.p50, p.p99, p.miss, p.gbit);
     fflush(stdout);
-    if (p.p99 > 20000.0) break;  // far past saturation
+    // far past saturation: most subframes late by more than 20 ms at p99 (an
+    // isolated host stall can push p99 up at light load without that)
+    if (p.p99 > 20000.0 && p.miss > 0.5) break;
   }
   crnt_destroy(ctx);
   return 0;

@@ -5,16 +5,17 @@
 // code word's LLRs in the paper's Fig. 4 (Sec. IV-B "Decoding function") --
 // and, for the encoder, the transmit direction (interleave, scramble).
 //
-// One CTA handles 4096 positions of one TB's transmitted sequence.  Its 128
-// threads first produce the 4096 scrambling bits c(n0 .. n0 + 4095), 32 per
-// thread: the 31-bit register state of each component at step n holds
-// x(n .. n + 30), so a thread's word is the xor of the two states at its
-// start plus one recurrence step for bit 31.  The states come from jump-ahead
-// tables built once per context (GF(2) matrix powers of the two register
-// updates): per chunk of 4096 steps the x1 state and the columns of the x2
-// jump, per thread offset 32 t the columns of both jumps.  Then the threads
-// move the chunk's LLRs (bits) between transmitted order and the e-sequence
-// order, flipping signs (bits) where c = 1.
+// One CTA handles a tile of whole rows of a TB's interleaver matrix (up to
+// kPuschTile bytes): in transmitted order that is one segment per column, in
+// e-sequence order one contiguous range, so both sides are read and written
+// contiguously and the transposition happens in shared memory.  The tile's
+// scrambling words -- 32 sequence bits each -- come first: the 31-bit
+// register state of each component at step n holds x(n .. n + 30), so a word
+// is the xor of the two states at its position plus one recurrence step for
+// bit 31.  The states come from jump-ahead tables built once per context
+// (GF(2) matrix powers of the two register updates): per 4096 steps the x1
+// state and the columns of the x2 jump, per 32 t steps within them the
+// columns of both jumps.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -83,49 +84,99 @@ __device__ __forceinline__ uint32_t jump(const uint32_t* __restrict__ cols, uint
   return r;
 }
 
-// TX = false: in holds a TB's received LLRs in transmitted order, out gets
-// the e-sequence (descrambled: -128 reads as -127, the sign flips where c =
-// 1; de-interleaved).  TX = true: in holds coded bits (0/1 per byte) in
-// e-sequence order, out gets them interleaved and scrambled.  Mode-0 TBs are
+// Register states at sequence position n (a multiple of 32): the 31-bit
+// state of each component holds x(m .. m + 30) for m = n + 1600, reached by
+// the table jumps.
+__device__ __forceinline__ void gold_state(const GoldTables& g, uint32_t c_init, int n,
+                                           uint32_t& s1, uint32_t& s2) {
+  const int c = n / kPuschChunk, t = (n - c * kPuschChunk) >> 5;
+  s1 = jump(g.t1 + 31 * t, __ldg(g.x1c + c));
+  s2 = jump(g.t2 + 31 * t, jump(g.a2c + 31 * c, c_init));
+}
+// new bits of the two recurrences from a state, bit j = x(m + 31 + j) (j < 28)
+__device__ __forceinline__ uint32_t next1(uint32_t s) { return (s >> 3) ^ s; }
+__device__ __forceinline__ uint32_t next2(uint32_t s) { return (s >> 3) ^ (s >> 2) ^ (s >> 1) ^ s; }
+// The scrambling word at the states' position (bit j = c(n + j), bit 31 one
+// recurrence step on), then both states advanced by 32 positions (28 + 4).
+__device__ __forceinline__ uint32_t gold_word_step(uint32_t& s1, uint32_t& s2) {
+  const uint32_t w = (s1 ^ s2) | (((next1(s1) ^ next2(s2)) & 1u) << 31);
+  s1 = (s1 >> 28) | ((next1(s1) & 0x0FFFFFFFu) << 3);
+  s2 = (s2 >> 28) | ((next2(s2) & 0x0FFFFFFFu) << 3);
+  s1 = (s1 >> 4) | ((next1(s1) & 0xFu) << 27);
+  s2 = (s2 >> 4) | ((next2(s2) & 0xFu) << 27);
+  return w;
+}
+constexpr int kGoldParts = 4;  // threads per column segment building its words
+
+// One tile: rows [r0, r0 + nr) of a TB's interleaver matrix, all ncol
+// columns.  In transmitted order the tile is ncol segments (column c: symbols
+// c R + r0 ..), in e-sequence order one contiguous range (symbols r0 ncol ..).
+// TX = false: in holds received LLRs (transmitted order); the segments are
+// read, descrambled (-128 reads as -127, the sign flips where c = 1) and
+// transposed in shared memory, the range written out.  TX = true: in holds
+// coded bits in e-sequence order; the range is read and the segments written
+// interleaved and scrambled.  Mode-0 TBs (one column of one-byte symbols) are
 // copied unchanged.
 template <bool TX>
 __global__ void __launch_bounds__(kPuschThreads) pusch_kernel(const PuschTb* __restrict__ tbs,
                                                               const PuschChunk* __restrict__ chunks,
                                                               GoldTables g, const int8_t* in,
                                                               int8_t* out) {
-  __shared__ uint32_t cbits[kPuschChunk / 32];
+  __shared__ int8_t tile[kPuschTile];
+  __shared__ uint32_t gw[kPuschTile / 32 + 2 * 16];
   const PuschChunk ch = chunks[blockIdx.x];
   const PuschTb t = tbs[ch.tb];
-  const int n0 = ch.n0;
-  const int len = min(kPuschChunk, t.G - n0);
+  const int qmnl = t.qmnl, ncol = t.ncol, R = t.rows;
+  const int r0 = ch.n0;
+  const int nr = min(pusch_tile_rows(qmnl, ncol), R - r0);
+  const int seg = nr * qmnl;           // bytes of one column segment
+  const int wpc = (seg + 31) / 32 + 1;  // scrambling words kept per column
   const int tid = threadIdx.x;
-  if (t.mode) {
-    const int c = n0 / kPuschChunk;
-    const uint32_t s1 = jump(g.t1 + 31 * tid, __ldg(g.x1c + c));
-    const uint32_t s2 = jump(g.t2 + 31 * tid, jump(g.a2c + 31 * c, t.c_init));
-    const uint32_t b1 = ((s1 >> 3) ^ s1) & 1u;
-    const uint32_t b2 = ((s2 >> 3) ^ (s2 >> 2) ^ (s2 >> 1) ^ s2) & 1u;
-    cbits[tid] = (s1 ^ s2) | ((b1 ^ b2) << 31);  // bit j: c(n0 + 32 tid + j)
+  if (t.mode) {  // the segments' scrambling words: one jump per thread, then steps
+    for (int k = tid; k < ncol * kGoldParts; k += kPuschThreads) {
+      const int c = k / kGoldParts, part = k - c * kGoldParts;
+      const int w0 = part * wpc / kGoldParts, w1 = (part + 1) * wpc / kGoldParts;
+      int n = ((((c * R + r0) * qmnl) >> 5) + w0) << 5;
+      uint32_t s1 = 0u, s2 = 0u;
+      if (w0 < w1 && n < t.G) gold_state(g, t.c_init, n, s1, s2);
+      for (int w = w0; w < w1; w++, n += 32) {
+        const uint32_t word = gold_word_step(s1, s2);
+        gw[c * wpc + w] = n < t.G ? word : 0u;
+      }
+    }
   }
   __syncthreads();
+  const int e0 = r0 * ncol * qmnl;  // the tile's first e-sequence position
+  const int tb = nr * ncol * qmnl;   // its bytes
   const int8_t* src = in + t.in_off;
   int8_t* dst = out + t.out_off;
-  for (int k = tid; k < len; k += kPuschThreads) {
-    const int i = n0 + k;  // transmitted position
-    int j = i;             // e-sequence position
-    bool flip = false;
-    if (t.mode) {
-      const int s = i / t.qmnl, b = i - s * t.qmnl;
-      const int col = s / t.rows, row = s - col * t.rows;
-      j = (row * t.ncol + col) * t.qmnl + b;
-      flip = (cbits[k >> 5] >> (k & 31)) & 1u;
+  if (TX) {
+    for (int k = tid; k < tb; k += kPuschThreads) tile[k] = src[e0 + k];
+    __syncthreads();
+  }
+  // offset k of a segment -> row k / qmnl by a multiply-shift (exact for k <
+  // 2^20 / (qmnl - 1), far above a segment's at most kPuschTile bytes)
+  const uint32_t rcp = qmnl > 1 ? ((1u << 20) + (uint32_t)qmnl - 1u) / (uint32_t)qmnl : 0u;
+  for (int c = 0; c < ncol; c++) {
+    const int p0 = (c * R + r0) * qmnl;  // the segment's first transmitted position
+    const uint32_t* gc = gw + c * wpc - (p0 >> 5);
+    for (int k = tid; k < seg; k += kPuschThreads) {
+      const int sr = qmnl > 1 ? (int)(((uint32_t)k * rcp) >> 20) : k;
+      const int b = k - sr * qmnl;
+      const int i = p0 + k;
+      const int e = (sr * ncol + c) * qmnl + b;
+      const uint32_t flip = t.mode ? (gc[i >> 5] >> (i & 31)) & 1u : 0u;
+      if (TX) {
+        dst[i] = (int8_t)(tile[e] ^ (int8_t)flip);
+      } else {
+        const int v = max((int)src[i], -127);
+        tile[e] = (int8_t)(flip ? -v : v);
+      }
     }
-    if (TX) {
-      dst[i] = (int8_t)(src[j] ^ (flip ? 1 : 0));
-    } else {
-      const int v = max((int)src[i], -127);
-      dst[j] = (int8_t)(flip ? -v : v);
-    }
+  }
+  if (!TX) {
+    __syncthreads();
+    for (int k = tid; k < tb; k += kPuschThreads) dst[e0 + k] = tile[k];
   }
 }
 
@@ -167,6 +218,22 @@ GoldTables gold_tables_view(const uint32_t* d) {
   g.t1 = g.a2c + 31 * kPuschMaxChunks;
   g.t2 = g.t1 + 31 * kPuschThreads;
   return g;
+}
+
+void pusch_tiles(const PuschTb& q, int tb, std::vector<PuschChunk>& out) {
+  const int rt = pusch_tile_rows(q.qmnl, q.ncol);
+  for (int r0 = 0; r0 < q.rows; r0 += rt) out.push_back(PuschChunk{(int32_t)tb, r0});
+}
+
+void pusch_tb(const crnt_tb_params& tp, int64_t in_off, int64_t out_off, PuschTb* q) {
+  q->in_off = in_off;
+  q->out_off = out_off;
+  q->G = (int32_t)tp.G;
+  q->mode = (tp.flags & CRNT_F_PUSCH) ? 1 : 0;
+  q->qmnl = q->mode ? tp.Qm * tp.NL : 1;  // mode 0: a copy, one column of bytes
+  q->ncol = q->mode ? pusch_cols(tp) : 1;
+  q->rows = q->G / (q->qmnl * q->ncol);
+  q->c_init = tp.c_init;
 }
 
 cudaError_t launch_pusch(bool tx, const PuschTb* tbs, const PuschChunk* chunks, int n_chunks,

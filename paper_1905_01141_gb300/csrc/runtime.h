@@ -97,6 +97,8 @@ struct crnt_ctx {
   crnt::Buf stage_in, stage_out;
   crnt::Buf enc_host{true};             // page-locked encoder descriptor staging
   crnt::Buf enc_e;                       // encoder's e-sequence ahead of the PUSCH transmit stage
+  std::vector<crnt::PuschTb> enc_ptb;    // its per-TB descriptors
+  std::vector<crnt::PuschChunk> enc_pch; // and tiles
   std::vector<crnt::lte::Seg> enc_segs;  // encoder planning scratch
   // crnt_decode_batch splits a batch into up to kBatchChunks chunks, each
   // with a reused plan and its own stream, so that planning and copying a
@@ -153,6 +155,9 @@ struct crnt_plan {
   int n_pch = 0;
   size_t off_ptb = 0, off_pch = 0;
   crnt::Buf d_rx;
+  // performance captor (crnt_plan_set_timing): 4 timestamps per sorted CB
+  bool timing = false;
+  crnt::Buf d_time, h_time{true};
 };
 
 namespace crnt {
@@ -204,5 +209,9 @@ void serving_stop(crnt_ctx* ctx);
 std::vector<uint32_t> gold_tables_host();
 // Interleaver columns of a TB with CRNT_F_PUSCH (n_symb, 0 = 12).
 inline int pusch_cols(const crnt_tb_params& t) { return t.n_symb ? t.n_symb : 12; }
+// Front-stage descriptor of a TB (mode 0, a plain copy, without CRNT_F_PUSCH)
+// and its tiles appended to out.
+void pusch_tb(const crnt_tb_params& tp, int64_t in_off, int64_t out_off, PuschTb* q);
+void pusch_tiles(const PuschTb& q, int tb, std::vector<PuschChunk>& out);
 int64_t now_ns();
 }  // namespace crnt

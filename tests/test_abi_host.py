@@ -31,9 +31,11 @@ def test_exports_every_declared_symbol(crnt_lib):
 
 def test_struct_sizes(crnt_lib):
     assert ctypes.sizeof(crnt_lib.TbParams) == 40
+    assert ctypes.sizeof(crnt_lib.Config) == 32
     assert ctypes.sizeof(crnt_lib.TbResult) == 96
     assert ctypes.sizeof(crnt_lib.CbLayout) == 40
     assert ctypes.sizeof(crnt_lib.PlanInfo) == 64
+    assert ctypes.sizeof(crnt_lib.CbTiming) == 48
     assert crnt_lib.version() == 2
     assert crnt_lib.strerror(-1) == "invalid argument"
 

@@ -384,3 +384,51 @@ def test_int_issue_probe(crnt_lib):
     assert rates[0] >= 1.5
     v = ctypes.c_double()
     assert L.crnt_int_issue_probe(0, 4, ctypes.byref(v)) == crnt_lib.EINVAL
+
+
+@pytest.fixture(scope="module")
+def ctx_pairs(crnt_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = crnt_lib.Context(0, pair_min_cbs=1)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_cb_timestamps(orc, crnt_lib, ctx_pairs, shape):
+    # the performance captor: per CB four %globaltimer stamps in order, all
+    # inside the launch, iterations equal to the results' iterations run
+    old = crnt_lib.tune_shape_get()
+    crnt_lib.tune_shape_set([shape] * crnt_lib.NUM_K)
+    try:
+        shapes = synth.tti_batch(seed=31, n_tb=24, amax=40000)
+        specs = [dict(A=s["A"], G=s["G"], Qm=s["Qm"], P=0, max_iter=6, early_stop=1,
+                      seed=1100 + i, snr=s["snr_db"]) for i, s in enumerate(shapes)]
+        tbs, llrs = batch(orc, specs)
+        plan = ctx_pairs.plan(tbs)
+        plan.set_timing(True)
+        dev = torch.device("cuda")
+        llr_d = torch.from_numpy(np.concatenate(llrs)).to(dev)
+        out_d = torch.zeros(plan.info["out_bytes"], dtype=torch.uint8, device=dev)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        plan.launch(llr_d, out_d, s.cuda_stream)
+        e1.record(s)
+        tm = plan.timing(s.cuda_stream)
+        res = plan.results(s.cuda_stream)
+        torch.cuda.synchronize()
+        assert len(tm) == plan.info["n_cb"]
+        assert (plan.info["pair_items"] > 0) == (shape == 2)
+        assert (tm["t_start_ns"] <= tm["t_derm_ns"]).all()
+        assert (tm["t_derm_ns"] <= tm["t_iter_ns"]).all()
+        assert (tm["t_iter_ns"] <= tm["t_done_ns"]).all()
+        span_us = (tm["t_done_ns"].max() - tm["t_start_ns"].min()) / 1e3
+        assert 0 < span_us <= e0.elapsed_time(e1) * 1e3 + 5
+        runs = [x for r in res for x in r["cb_iters_run"]]
+        assert list(tm["iterations"]) == runs
+        assert list(tm["tb"]) == [t for t, r in enumerate(res) for _ in range(r["C"])]
+        plan.close()
+    finally:
+        crnt_lib.tune_shape_set(old)

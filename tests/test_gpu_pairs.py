@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 def ctx(crnt_lib):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    c = crnt_lib.Context(0)
+    c = crnt_lib.Context(0, pair_min_cbs=1)  # pairs in batches of any size
     yield c
     c.close()
 
