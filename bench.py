@@ -638,7 +638,8 @@ def subframe_latency(crnt, ctx, dev):
 
 def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 44, 48, 52, 56, 64, 72, 80,
                                               96),
-                seconds=1.5, tune_table=None, purge=False, poisson=False):
+                seconds=1.5, tune_table=None, purge=False, poisson=False, threads=None,
+                extra_args=()):
     """Serving loop under cell load, driven by the native open-loop load
     generator (crnt_loadgen, a client of crnt_submit / crnt_poll): every cell
     submits one subframe (8 UEs, TB mix of the TTI workload) per 1 ms period
@@ -679,6 +680,9 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 44, 48, 52, 5
             cmd += ["--purge"]
         if poisson:
             cmd += ["--poisson"]
+        if threads:
+            cmd += ["--threads", str(threads)]
+        cmd += list(extra_args)
         cmd += [path, str(ues), str(seconds), "0.1", str(seed)] + [str(c) for c in cells_list]
         out = sp.run(cmd, capture_output=True, text=True, timeout=600)
     rows = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]

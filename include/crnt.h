@@ -58,11 +58,15 @@ typedef struct crnt_config {
     uint32_t harq_slots;     /* HARQ soft-buffer slots kept on the device [4096] */
     uint64_t mem_budget;     /* device bytes for soft buffers + in-flight work [8 GiB] */
     uint32_t max_inflight;   /* serving: TBs on the device at once [4096] */
-    uint32_t deadline_us;    /* serving: deadline for miss accounting [1000] */
+    uint32_t deadline_us;    /* serving: latency target from crnt_submit to the
+                                result [1000] */
     uint32_t pair_min_cbs;   /* CB pairs (shape table) only in batches of at least
                                 this many CBs [two waves of one-CB CTAs: 6 x SMs];
                                 1 = in every batch */
-    uint32_t pad0;
+    uint32_t admission;      /* serving: 0 = refuse a subframe whose predicted
+                                completion passes deadline_us (and beyond the
+                                in-flight and memory limits) [0]; 1 = only the
+                                in-flight and memory limits */
 } crnt_config;
 
 /* Per-TB parameters (40 bytes). */
@@ -272,6 +276,19 @@ int crnt_plan_get_info(const crnt_plan* plan, crnt_plan_info* info);
 int crnt_plan_launch(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream);
 int crnt_plan_launch_debug(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream,
                            int8_t* dbg_d, int16_t* dbg_ext, uint8_t* dbg_hard);
+/* As crnt_plan_launch, but no CTA reads an LLR before the 32-bit word at
+ * `ready` (device memory, or page-locked host memory) is non-zero, so a
+ * decode can be enqueued before its LLRs have arrived (ahead of a fronthaul
+ * transfer into llr): the writer stores the LLRs, then the non-zero word
+ * with release semantics.  Each CTA's first thread polls the word (acquire
+ * load, system scope) for at most timeout_us microseconds (1 ..
+ * 10 000 000) measured on %globaltimer.  When a CTA's wait expires, the
+ * CTAs stop (those that saw the word non-zero first may have decoded some
+ * CBs) and crnt_plan_results reports CRNT_ETIMEDOUT for every TB of the
+ * batch; the plan and the context stay usable.  CRNT_EINVAL for plans with
+ * CRNT_F_PUSCH TBs. */
+int crnt_plan_launch_gated(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream,
+                           const uint32_t* ready, uint32_t timeout_us);
 /* Wait for the stream and fill res[n] (host).  CRNT_EDEVICE on a CUDA error. */
 int crnt_plan_results(crnt_plan* plan, crnt_tb_result* res, void* stream);
 
@@ -370,6 +387,29 @@ int crnt_poll(crnt_ctx* ctx, crnt_tb_result* done, const uint8_t** bits, uint32_
               uint32_t timeout_us);
 /* Forget the soft buffer of a HARQ process.  CRNT_ENOTFOUND if unknown. */
 int crnt_harq_release(crnt_ctx* ctx, uint32_t cell, uint32_t ue, uint32_t harq_pid);
+
+/* Serving counters since the context's serving loop started (all zero
+ * before the first crnt_submit).  Cumulative: take differences to measure
+ * an interval.  A subframe is one crnt_submit call. */
+typedef struct crnt_serve_stats {
+    uint64_t submit_calls;     /* crnt_submit calls that reached admission */
+    uint64_t refused_calls;    /* of which refused with CRNT_EAGAIN */
+    uint64_t refused_deadline; /* of the refused: predicted completion past deadline_us */
+    uint64_t offered_tbs;      /* TBs in those calls */
+    uint64_t admitted_tbs;
+    uint64_t done_tbs;         /* results handed to the done queue */
+    uint64_t late_tbs;         /* of which finished later than submit + deadline_us */
+    uint64_t batches;          /* decode launches of the serving worker */
+    uint64_t worker_plan_ns;   /* worker time building plans */
+    uint64_t worker_launch_ns; /* worker time in launch calls */
+    uint64_t worker_harvest_ns;/* worker time collecting finished batches */
+    uint64_t worker_ns;        /* wall time since the loop started */
+    uint64_t submit_copy_ns;   /* submitting threads' time copying LLRs */
+    double model_a_us;         /* admission model: latency with nothing ahead */
+    double model_rate;         /* admission model: trellis step-iterations per us */
+    double model_sigma_us;     /* admission model: spread of its residuals */
+} crnt_serve_stats;
+int crnt_serve_stats_get(crnt_ctx* ctx, crnt_serve_stats* out);
 
 #ifdef __cplusplus
 }

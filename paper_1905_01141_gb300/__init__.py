@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("harq_slots", ctypes.c_uint32),
                 ("mem_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("deadline_us", ctypes.c_uint32), ("pair_min_cbs", ctypes.c_uint32),
-                ("pad0", ctypes.c_uint32)]
+                ("admission", ctypes.c_uint32)]
 
 
 class TbParams(ctypes.Structure):
@@ -75,6 +75,17 @@ class CbTiming(ctypes.Structure):
                 ("pad", ctypes.c_uint8 * 7)]
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("submit_calls", "refused_calls", "refused_deadline", "offered_tbs",
+                 "admitted_tbs", "done_tbs", "late_tbs", "batches", "worker_plan_ns",
+                 "worker_launch_ns", "worker_harvest_ns", "worker_ns", "submit_copy_ns")] + \
+               [(n, ctypes.c_double) for n in ("model_a_us", "model_rate", "model_sigma_us")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class CbLayout(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("K", "F", "E", "k0", "Ncb", "llr_offset", "soft_offset", "crc_b", "P", "W")]
@@ -107,6 +118,7 @@ SIGNATURES = {
     "crnt_plan_get_info": (ctypes.c_int, [_P, _P]),
     "crnt_plan_launch": (ctypes.c_int, [_P, _P, _P, _P]),
     "crnt_plan_launch_debug": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "crnt_plan_launch_gated": (ctypes.c_int, [_P, _P, _P, _P, _P, _U32]),
     "crnt_plan_results": (ctypes.c_int, [_P, _P, _P]),
     "crnt_plan_destroy": (ctypes.c_int, [_P]),
     "crnt_plan_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -118,6 +130,7 @@ SIGNATURES = {
     "crnt_submit": (ctypes.c_int, [_P, _P, _P, _U32, _P]),
     "crnt_poll": (ctypes.c_int, [_P, _P, _P, _U32, _U32]),
     "crnt_harq_release": (ctypes.c_int, [_P, _U32, _U32, _U32]),
+    "crnt_serve_stats_get": (ctypes.c_int, [_P, _P]),
     "crnt_decode_batch_static": (ctypes.c_int, [_P, _U32, _P, _P, _P, _P]),
     "crnt_tune_get": (ctypes.c_int, [_P, _U32]),
     "crnt_tune_set": (ctypes.c_int, [_P, _U32]),
@@ -272,11 +285,11 @@ class Context:
     """A library context on one CUDA device."""
 
     def __init__(self, device=0, harq_slots=0, mem_budget=0, max_inflight=0, deadline_us=0,
-                 pair_min_cbs=0):
+                 pair_min_cbs=0, admission=0):
         L = load()
         cfg = Config(device=device, harq_slots=harq_slots, mem_budget=mem_budget,
                      max_inflight=max_inflight, deadline_us=deadline_us,
-                     pair_min_cbs=pair_min_cbs)
+                     pair_min_cbs=pair_min_cbs, admission=admission)
         h = ctypes.c_void_p()
         _check(L.crnt_create(ctypes.byref(h), ctypes.byref(cfg)), "crnt_create")
         self.h = h
@@ -371,6 +384,12 @@ class Context:
     def harq_release(self, cell, ue, pid):
         return load().crnt_harq_release(self.h, cell, ue, pid)
 
+    def serve_stats(self):
+        """The serving loop's counters (crnt_serve_stats_get) as a dict."""
+        st = ServeStats()
+        _check(load().crnt_serve_stats_get(self.h, ctypes.byref(st)), "crnt_serve_stats_get")
+        return st.as_dict()
+
 
 class Plan:
     """A planned batch: one persistent launch per call of ``launch``."""
@@ -393,6 +412,14 @@ class Plan:
             rc = load().crnt_plan_launch_debug(self.h, _ptr(llr), _ptr(out), stream or None,
                                                _ptr(dbg_d), _ptr(dbg_ext), _ptr(dbg_hard))
         _check(rc, "crnt_plan_launch")
+
+    def launch_gated(self, llr, out, ready, timeout_us, stream=0):
+        """crnt_plan_launch_gated: the decode reads no LLR before the uint32
+        at ``ready`` (a device or page-locked host address, or a tensor) is
+        non-zero, waiting at most timeout_us."""
+        rc = load().crnt_plan_launch_gated(self.h, _ptr(llr), _ptr(out), stream or None,
+                                           _ptr(ready), timeout_us)
+        _check(rc, "crnt_plan_launch_gated")
 
     def results_raw(self, stream=0):
         """Results as a numpy structured array (fields of crnt_tb_result)."""

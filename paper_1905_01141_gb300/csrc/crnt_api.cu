@@ -448,18 +448,123 @@ const KTmpl* auto_tmpl(int K) {
 
 }  // namespace
 
-// Two passes.  Pass 1 validates every TB, fixes its offsets and the sort key
-// of each CB; pass 2 writes the CB descriptors in sorted (work-item) order
-// straight into the pinned staging buffer, from closed forms of the per-CB
-// offsets inside a TB.
+// Everything about one TB that does not depend on the batch it joins
+// (tb_prepare), then the batch (plan_assemble).  Pass 1 of the batch fixes
+// each TB's offsets and the sort key of each CB; pass 2 copies the CB
+// descriptors in sorted (work-item) order straight into the pinned staging
+// buffer and adds the TB's offsets.
+int tb_prepare(crnt_ctx* ctx, const crnt_tb_params& tp, TbPrep* out) {
+  lte::Seg& s = out->s;
+  int rc = validate(tp, &s);
+  if (rc) return rc;
+  TbPre& pr = out->pr;
+  pr.llr = pr.dbg = 0;
+  pr.cb0 = 0;
+  pr.soft = -1;
+  for (int h = 0; h < 2; h++) {
+    const int K = h ? s.Kp : s.Km;
+    KTmpl& tm = h ? pr.tp : pr.tm;
+    if (h == 0 && s.Cm == 0) continue;
+    if (tp.P == 0) {
+      const KTmpl* a = auto_tmpl(K);
+      if (!a) return CRNT_EINVAL;
+      tm = *a;
+    } else if (!make_tmpl(K, tp.P, &tm)) {
+      return CRNT_EINVAL;
+    }
+    if (tm.slot > kSmemBudget) return CRNT_EINVAL;
+  }
+  if (((pr.tp.ND + s.F) >> 5) + 1 > pr.tp.R ||
+      (s.Cm && ((pr.tm.ND + s.F) >> 5) + 1 > pr.tm.R))
+    return CRNT_EINVAL;
+  // the soft buffer is bound last: a TB refused above binds none
+  if (tp.flags & CRNT_F_HARQ) {
+    rc = harq_bind(ctx, tp, &pr.soft);
+    if (rc) return rc;
+  }
+  const int Gp = (int)tp.G / (tp.NL * tp.Qm);
+  pr.n_lo = s.C - Gp % s.C;
+  pr.E_lo = tp.NL * tp.Qm * (Gp / s.C);
+  pr.E_hi = tp.NL * tp.Qm * ((Gp + s.C - 1) / s.C);
+  out->p_used = (uint16_t)pr.tp.P;
+  // CB descriptors in r order: LLR and debug offsets from the TB's own
+  // first LLR byte and debug element, TB index 0
+  for (int r = 0; r < s.C; r++) {
+    const KTmpl& tm = r < s.Cm ? pr.tm : pr.tp;
+    const int F = r == 0 ? s.F : 0;
+    const int nm = std::min(r, s.Cm), np = r - nm;  // earlier CBs of size K-, K+
+    const int sumK = nm * s.Km + np * s.Kp;
+    const int sumNcb = nm * (s.Cm ? pr.tm.ncb : 0) + np * pr.tp.ncb;
+    const int eoff = r <= pr.n_lo ? r * pr.E_lo : pr.n_lo * pr.E_lo + (r - pr.n_lo) * pr.E_hi;
+    const int pay_off = sumK - (r > 0 ? s.F : 0) - r * s.L;
+    CbDesc& d = out->cb[r];
+    d.K = tm.K;
+    d.F = F;
+    d.E = r < pr.n_lo ? pr.E_lo : pr.E_hi;
+    d.k0 = lte::k0(tm.K, tp.rv);
+    d.P = tm.P;
+    d.W = tm.W;
+    d.divM = tm.divM;
+    d.divS = tm.divS;
+    d.f1 = tm.f1;
+    d.f2 = tm.f2;
+    d.f2x2 = tm.f2x2;
+    d.f2sub = tm.f2sub;
+    d.f2jump = tm.f2jump;
+    d.R = tm.R;
+    d.ND = tm.ND;
+    d.Nv = 3 * (tm.K + 4) - 2 * F;
+    if (F == 0) {
+      d.maskB = tm.maskB0;
+      d.mask2 = tm.mask2;
+      d.rank0 = tm.rank0[tp.rv];
+    } else {
+      rm_masks(tm.ND, F, &d.maskB, &d.mask2);
+      d.rank0 = rank_of_k0(tm.K, F, tp.rv, d.maskB, d.mask2);
+    }
+    d.tb = 0;
+    d.r = r;
+    d.llr_off = eoff;
+    d.soft_off = pr.soft >= 0 ? pr.soft + sumNcb : -1;
+    d.pay_bits = tm.K - F - s.L;
+    d.pay_off = pay_off;
+    d.n_after = ((int)tp.A + 24) - pay_off - d.pay_bits;
+    d.dbg_off = sumK + 4 * r;
+    d.crc_b = s.C > 1;
+    d.max_iter = tp.max_iter;
+    d.early_stop = tp.early_stop;  // 0 none, 1 CRC, 2 mutual information
+    d.new_data = tp.new_data ? 1 : 0;
+    d.purge = (tp.flags & CRNT_F_PURGE) && s.C > 1 ? 1 : 0;
+    d.radix4 = radix4_of(tm.K);
+    d.qt = qtab_get(ctx, tm.K, tm.P);
+    d.qq = qtab_q(d.qt, tm.K, tm.P);
+    d.dm = dmap_get(ctx, tm.K, tm.P, F);
+    memset(d.pad0, 0, sizeof d.pad0);
+  }
+  return CRNT_OK;
+}
+
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
                cudaStream_t stream, const int64_t* llr_base) {
+  if (pl->prep.size() < n) pl->prep.resize(n);
+  pl->prep_ptr.resize(n);
+  for (uint32_t t = 0; t < n; t++) {
+    const int rc = tb_prepare(ctx, tbs[t], &pl->prep[t]);
+    if (rc) return rc;
+    pl->prep_ptr[t] = &pl->prep[t];
+  }
+  return plan_assemble(ctx, tbs, pl->prep_ptr.data(), n, pl, stream, llr_base, nullptr);
+}
+
+int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const* preps,
+                  uint32_t n, crnt_plan* pl, cudaStream_t stream, const int64_t* llr_base,
+                  const int64_t* out_base) {
   pl->ctx = ctx;
   pl->tbs.assign(tbs, tbs + n);
   pl->segs.resize(n);
   pl->p_used.resize(n);
   pl->tdesc.resize(n);
-  pl->pre.resize(n);
+  pl->base.resize(n);
   pl->keyed.clear();
   pl->owner.clear();
   pl->items.clear();
@@ -469,56 +574,31 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   bool pusch_any = false;
   for (uint32_t t = 0; t < n; t++) {
     const crnt_tb_params& tp = tbs[t];
-    lte::Seg& s = pl->segs[t];
-    int rc = validate(tp, &s);
-    if (rc) return rc;
-    TbPre& pr = pl->pre[t];
-    pr.soft = -1;
-    if (tp.flags & CRNT_F_HARQ) {
-      rc = harq_bind(ctx, tp, &pr.soft);
-      if (rc) return rc;
-    }
-    for (int h = 0; h < 2; h++) {
-      const int K = h ? s.Kp : s.Km;
-      KTmpl& tm = h ? pr.tp : pr.tm;
-      if (h == 0 && s.Cm == 0) continue;
-      if (tp.P == 0) {
-        const KTmpl* a = auto_tmpl(K);
-        if (!a) return CRNT_EINVAL;
-        tm = *a;
-      } else if (!make_tmpl(K, tp.P, &tm)) {
-        return CRNT_EINVAL;
-      }
-      if (tm.slot > kSmemBudget) return CRNT_EINVAL;
-    }
-    if (((pr.tp.ND + s.F) >> 5) + 1 > pr.tp.R ||
-        (s.Cm && ((pr.tm.ND + s.F) >> 5) + 1 > pr.tm.R))
-      return CRNT_EINVAL;
-    const int Gp = (int)tp.G / (tp.NL * tp.Qm);
-    pr.n_lo = s.C - Gp % s.C;
-    pr.E_lo = tp.NL * tp.Qm * (Gp / s.C);
-    pr.E_hi = tp.NL * tp.Qm * ((Gp + s.C - 1) / s.C);
-    pr.llr = llr_base ? llr_base[t] : llr_off;
+    const TbPrep& pp = *preps[t];
+    const lte::Seg& s = pp.s;
+    pl->segs[t] = s;
+    pl->p_used[t] = pp.p_used;
+    TbBase& b = pl->base[t];
+    b.llr = llr_base ? llr_base[t] : llr_off;
+    b.dbg = dbg_off;
+    b.cb0 = ncb;
     pusch_any |= (tp.flags & CRNT_F_PUSCH) != 0;
-    pr.dbg = dbg_off;
-    pr.cb0 = ncb;
     TbDesc& td = pl->tdesc[t];
-    td.out_off = out_off;
+    td.out_off = out_base ? out_base[t] : out_off;
     td.A = (int)tp.A;
     td.C = s.C;
     td.cb0 = (int)ncb;
     td.pad0 = 0;
-    pl->p_used[t] = (uint16_t)pr.tp.P;
     for (int r = 0; r < s.C; r++) {
-      const KTmpl& tm = r < s.Cm ? pr.tm : pr.tp;
-      const uint64_t cost = (uint64_t)(tm.W * tp.max_iter);  // < 2^17
+      const CbDesc& c = pp.cb[r];
+      const uint64_t cost = (uint64_t)(c.W * c.max_iter);  // < 2^17
       // descending W max_iter, then K, then P; ascending (t, r) -- one
       // integer sorted ascending
-      pl->keyed.push_back(((0x1FFFFull - cost) << 46) | ((uint64_t)(0x1FFF - tm.K) << 33) |
-                          ((uint64_t)(0xFF - tm.P) << 25) | (uint64_t)(ncb + r));
+      pl->keyed.push_back(((0x1FFFFull - cost) << 46) | ((uint64_t)(0x1FFF - c.K) << 33) |
+                          ((uint64_t)(0xFF - c.P) << 25) | (uint64_t)(ncb + r));
       pl->owner.push_back(t);
-      dbg_off += tm.K + 4;
-      steps += tm.K;
+      dbg_off += c.K + 4;
+      steps += c.K;
     }
     ncb += s.C;
     if (ncb >= (1u << 25)) return CRNT_EINVAL;
@@ -537,9 +617,9 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     pl->pch.clear();
     int64_t e = 0;
     for (uint32_t t = 0; t < n; t++) {
-      pusch_tb(tbs[t], pl->pre[t].llr, e, &pl->ptb[t]);
+      pusch_tb(tbs[t], pl->base[t].llr, e, &pl->ptb[t]);
       pusch_tiles(pl->ptb[t], (int)t, pl->pch);
-      pl->pre[t].llr = e;
+      pl->base[t].llr = e;
       e += tbs[t].G;
     }
     pl->n_pch = (int)pl->pch.size();
@@ -586,62 +666,15 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
   for (uint32_t i = 0; i < ncb; i++) {
     const uint32_t g = (uint32_t)(pl->keyed[i] & 0x1FFFFFF);
     const uint32_t t = pl->owner[g];
-    const crnt_tb_params& tp = tbs[t];
-    const lte::Seg& s = pl->segs[t];
-    const TbPre& pr = pl->pre[t];
-    const int r = (int)(g - pr.cb0);
-    const KTmpl& tm = r < s.Cm ? pr.tm : pr.tp;
-    const int F = r == 0 ? s.F : 0;
-    const int nm = std::min(r, s.Cm), np = r - nm;  // earlier CBs of size K-, K+
-    const int sumK = nm * s.Km + np * s.Kp;
-    const int sumNcb = nm * (s.Cm ? pr.tm.ncb : 0) + np * pr.tp.ncb;
-    const int eoff = r <= pr.n_lo ? r * pr.E_lo : pr.n_lo * pr.E_lo + (r - pr.n_lo) * pr.E_hi;
-    const int pay_off = sumK - (r > 0 ? s.F : 0) - r * s.L;
+    const TbBase& b = pl->base[t];
+    const int r = (int)(g - b.cb0);
     CbDesc& d = hc[i];
-    d.K = tm.K;
-    d.F = F;
-    d.E = r < pr.n_lo ? pr.E_lo : pr.E_hi;
-    d.k0 = lte::k0(tm.K, tp.rv);
-    d.P = tm.P;
-    d.W = tm.W;
-    d.divM = tm.divM;
-    d.divS = tm.divS;
-    d.f1 = tm.f1;
-    d.f2 = tm.f2;
-    d.f2x2 = tm.f2x2;
-    d.f2sub = tm.f2sub;
-    d.f2jump = tm.f2jump;
-    d.R = tm.R;
-    d.ND = tm.ND;
-    d.Nv = 3 * (tm.K + 4) - 2 * F;
-    if (F == 0) {
-      d.maskB = tm.maskB0;
-      d.mask2 = tm.mask2;
-      d.rank0 = tm.rank0[tp.rv];
-    } else {
-      rm_masks(tm.ND, F, &d.maskB, &d.mask2);
-      d.rank0 = rank_of_k0(tm.K, F, tp.rv, d.maskB, d.mask2);
-    }
+    d = preps[t]->cb[r];
     d.tb = (int)t;
-    d.r = r;
-    d.llr_off = pr.llr + eoff;
-    d.soft_off = pr.soft >= 0 ? pr.soft + sumNcb : -1;
-    d.pay_bits = tm.K - F - s.L;
-    d.pay_off = pay_off;
-    d.n_after = ((int)tp.A + 24) - pay_off - d.pay_bits;
-    d.dbg_off = (int32_t)(pr.dbg + sumK + 4 * r);
-    d.crc_b = s.C > 1;
-    d.max_iter = tp.max_iter;
-    d.early_stop = tp.early_stop;  // 0 none, 1 CRC, 2 mutual information
-    d.new_data = tp.new_data ? 1 : 0;
-    d.purge = (tp.flags & CRNT_F_PURGE) && s.C > 1 ? 1 : 0;
-    d.radix4 = radix4_of(tm.K);
+    d.llr_off += b.llr;
+    d.dbg_off = (int32_t)(d.dbg_off + b.dbg);
     radix4_any |= d.radix4 != 0;
-    d.qt = qtab_get(ctx, tm.K, tm.P);
-    d.qq = qtab_q(d.qt, tm.K, tm.P);
-    d.dm = dmap_get(ctx, tm.K, tm.P, F);
     qtab_all &= d.qt != nullptr;
-    memset(d.pad0, 0, sizeof d.pad0);
     pl->cb_tb[i] = (int)t;
     pl->cb_r[i] = r;
   }
@@ -782,8 +815,12 @@ bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs) {
 }
 
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
-                int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded) {
+                int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded, const uint32_t* gate,
+                uint32_t gate_us) {
+  if (gate && pl->pusch) return CRNT_EINVAL;
   DecParams p = pl->prm;
+  p.gate = gate;
+  p.gate_us = gate_us;
   p.llr = llr;
   p.out = out;
   p.soft = pl->ctx->harq.arena;
@@ -1070,6 +1107,14 @@ int crnt_plan_launch_debug(crnt_plan* plan, const int8_t* llr, uint8_t* out, voi
 
 int crnt_plan_launch(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream) {
   return crnt_plan_launch_debug(plan, llr, out, stream, nullptr, nullptr, nullptr);
+}
+
+int crnt_plan_launch_gated(crnt_plan* plan, const int8_t* llr, uint8_t* out, void* stream,
+                           const uint32_t* ready, uint32_t timeout_us) {
+  if (!plan || !llr || !out || !ready || timeout_us < 1 || timeout_us > 10000000u)
+    return CRNT_EINVAL;
+  return plan_launch(plan, llr, out, (cudaStream_t)stream, nullptr, nullptr, nullptr, false,
+                     ready, timeout_us);
 }
 
 int crnt_plan_results(crnt_plan* plan, crnt_tb_result* res, void* stream) {

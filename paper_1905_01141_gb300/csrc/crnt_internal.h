@@ -82,7 +82,7 @@ struct WorkItem {
 // Per-batch device state written by the kernel.
 struct DecState {
   int32_t head;       // work-queue head
-  int32_t err;        // first error code seen by a CTA (0 = none)
+  int32_t err;        // 1: the wait on the launch's gate expired (0 = none)
 };
 
 struct DecParams {
@@ -112,6 +112,8 @@ struct DecParams {
   int32_t radix4_any;     // some CB selects the radix-4 forward recursion
   int32_t qtab_all;       // every CB has an interleaved-pass address table
   int32_t pair_any;       // some work item is a CB pair (needs qtab_all)
+  const uint32_t* gate;   // optional: no LLR is read before *gate != 0
+  uint32_t gate_us;       // bound of that wait (us); on expiry state->err is set
 };
 
 // Encoder launch description: one CB per CTA.

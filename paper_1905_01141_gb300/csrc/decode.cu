@@ -1676,6 +1676,29 @@ __device__ __noinline__ void run_single_item_call(const DecParams& prm, const Wo
   run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, s_remaining, s_maxit);
 }
 
+// The launch gate (crnt_plan_launch_gated): thread 0 of a CTA polls the
+// ready word with system-scope acquire loads until it is non-zero -- the
+// LLRs written before it are then visible to this CTA, whose other threads
+// pass the barrier after it -- or until gate_us microseconds of %globaltimer
+// (and at most 2^24 polls of at least a microsecond each) have passed.
+// Expiry is recorded once in state->err, where later CTAs see it and stop
+// without waiting again.  Returns 0 when open, 1 when expired.
+__device__ __noinline__ int gate_wait(const DecParams& prm) {
+  volatile int32_t* err = &prm.state->err;
+  if (*err) return 1;
+  const uint64_t t0 = gtime(), limit = (uint64_t)prm.gate_us * 1000ull;
+  for (uint32_t it = 0; it < (1u << 24); it++) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.u32 %0, [%1];" : "=r"(v) : "l"(prm.gate) : "memory");
+    if (v) return 0;
+    if (*err) return 1;
+    if (gtime() - t0 > limit) break;
+    __nanosleep(1000);
+  }
+  atomicCAS(&prm.state->err, 0, 1);
+  return 1;
+}
+
 // R4 = false: the radix-2 kernel; R4 = true adds the radix-4 forward
 // recursion for CBs that select it (a separate instantiation, so the radix-2
 // kernel's code is not affected by the option).  QT: every CB carries an
@@ -1703,6 +1726,11 @@ __global__ void __launch_bounds__(kThreads, PAIR ? kCtasPerSmPair : kCtasPerSm)
     (i < 256 ? tabA : tabB)[i & 255] = r & 0xFFFFFFu;
   }
 
+  if (prm.gate) {
+    if (tid == 0) s_item = gate_wait(prm);
+    __syncthreads();
+    if (s_item) return;  // expired: nothing of the batch is decoded
+  }
   for (;;) {
     __syncthreads();
     if (tid == 0) s_item = atomicAdd(&prm.state->head, 1);

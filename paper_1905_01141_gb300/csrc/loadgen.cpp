@@ -12,15 +12,23 @@
 // n int64 LLR offsets, then the LLR bytes.  TB u of cell c is entry
 // (c * ues + u) mod n.  Output: one JSON object per cell count on stdout.
 //
-// usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--threads T] FILE UES SECONDS
-//                     RETX_FRACTION SEED CELLS...
+// usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--admit-by-count] [--threads T]
+//                     FILE UES SECONDS RETX_FRACTION SEED CELLS...
 // TABLE: a window-count table (188 numbers) installed with crnt_tune_set,
 // optionally followed by a radix table (188 numbers, crnt_tune_radix_set)
 // and a CTA-shape table (188 numbers, crnt_tune_shape_set);
 // --purge: every TB asks for purge on failure (CRNT_F_PURGE);
 // --poisson: exponential inter-arrival times of mean 1 ms per cell instead of
-// the 1 ms period with jitter; --threads T: submitter threads, cells dealt
-// round-robin (default 4; each copies its cells' LLRs in crnt_submit).
+// the 1 ms period with jitter; --admit-by-count: the library admits by its
+// in-flight and memory limits only, not by predicted completion;
+// --threads T: submitter threads, cells dealt round-robin (default 4; each
+// copies its cells' LLRs in crnt_submit).
+// Each output line also splits the latency into its parts (p50, p99 in us):
+// scheduled arrival -> submit call, submit -> launch of the TB's batch,
+// launch -> result collected; and gives the library's serving counters over
+// the point (crnt_serve_stats_get): offered and admitted TBs, subframes
+// refused for their predicted completion, batches, the serving worker's time
+// shares, the submitting threads' copy time in cores, the admission model.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -58,7 +66,17 @@ struct Point {
   int cells = 0;
   long tbs = 0, subframes = 0, refused = 0, errors = 0;
   double p50 = 0, p99 = 0, miss = 0, gbit = 0;
+  // latency parts (p50, p99 in us): scheduled arrival -> submit call,
+  // submit -> launch of its batch, launch -> result collected
+  double part[3][2] = {};
+  crnt_serve_stats st{};  // the library's counters over the point
 };
+
+double pct(std::vector<double>& v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  return v[std::min(v.size() - 1, (size_t)(q * (double)v.size()))];
+}
 
 Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
                 const std::vector<const int8_t*>& ptr, int ues, int cells, double seconds,
@@ -71,17 +89,22 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
   // ticket -> (arrival, A); results that arrive before their ticket is
   // registered wait in `early` (ticket -> (done time, status))
   std::unordered_map<uint64_t, std::pair<int64_t, uint32_t>> pending;
-  std::unordered_map<uint64_t, std::pair<int64_t, int>> early;
-  std::vector<double> lat;
+  std::unordered_map<uint64_t, crnt_tb_result> early;
+  std::vector<double> lat, parts[3];
   std::atomic<int> submitting{nthreads};
   long n_bits = 0, errors = 0;
   const int64_t t0 = now_ns() + 2000000;
   const int64_t t_end = t0 + (int64_t)(seconds * 1e9);
-  auto record = [&](int64_t arrival, uint32_t A, int64_t done, int status) {
-    if (status != CRNT_OK) errors++;
-    lat.push_back((double)(done - arrival) / 1e3);
+  auto record = [&](int64_t arrival, uint32_t A, const crnt_tb_result& r) {
+    if (r.status != CRNT_OK) errors++;
+    lat.push_back((double)((int64_t)r.t_done_ns - arrival) / 1e3);
+    parts[0].push_back((double)((int64_t)r.t_submit_ns - arrival) / 1e3);
+    parts[1].push_back((double)((int64_t)r.t_start_ns - (int64_t)r.t_submit_ns) / 1e3);
+    parts[2].push_back((double)((int64_t)r.t_done_ns - (int64_t)r.t_start_ns) / 1e3);
     n_bits += A;
   };
+  crnt_serve_stats st0;
+  crnt_serve_stats_get(ctx, &st0);
   // poller
   std::thread poller([&] {
     std::vector<crnt_tb_result> res(4096);
@@ -93,10 +116,10 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
       for (int i = 0; i < k; i++) {
         auto it = pending.find(res[i].ticket);
         if (it == pending.end()) {
-          early[res[i].ticket] = {(int64_t)res[i].t_done_ns, res[i].status};
+          early[res[i].ticket] = res[i];
           continue;
         }
-        record(it->second.first, it->second.second, (int64_t)res[i].t_done_ns, res[i].status);
+        record(it->second.first, it->second.second, res[i]);
         pending.erase(it);
       }
       if (submitting.load() == 0 && pending.empty() && early.empty()) break;
@@ -143,7 +166,7 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
         for (int u = 0; u < ues; u++) {
           auto it = early.find(tk[u]);
           if (it != early.end()) {
-            record(ev.first, tb[u].A, it->second.first, it->second.second);
+            record(ev.first, tb[u].A, it->second);
             early.erase(it);
           } else {
             pending[tk[u]] = {ev.first, tb[u].A};
@@ -183,6 +206,26 @@ Point run_point(crnt_ctx* ctx, const std::vector<crnt_tb_params>& par,
     p.miss = (double)miss / (double)lat.size();
   }
   p.gbit = (double)n_bits / seconds / 1e9;
+  for (int k = 0; k < 3; k++) {
+    p.part[k][1] = pct(parts[k], 0.99);
+    p.part[k][0] = pct(parts[k], 0.5);
+  }
+  crnt_serve_stats st1;
+  crnt_serve_stats_get(ctx, &st1);
+  p.st = st1;  // counters over the point; the model fields are its state at the end
+  p.st.submit_calls -= st0.submit_calls;
+  p.st.refused_calls -= st0.refused_calls;
+  p.st.refused_deadline -= st0.refused_deadline;
+  p.st.offered_tbs -= st0.offered_tbs;
+  p.st.admitted_tbs -= st0.admitted_tbs;
+  p.st.done_tbs -= st0.done_tbs;
+  p.st.late_tbs -= st0.late_tbs;
+  p.st.batches -= st0.batches;
+  p.st.worker_plan_ns -= st0.worker_plan_ns;
+  p.st.worker_launch_ns -= st0.worker_launch_ns;
+  p.st.worker_harvest_ns -= st0.worker_harvest_ns;
+  p.st.worker_ns -= st0.worker_ns;
+  p.st.submit_copy_ns -= st0.submit_copy_ns;
   return p;
 }
 
@@ -218,7 +261,7 @@ int main(int argc, char** argv) {
     argv += 2;
     argc -= 2;
   }
-  uint32_t extra_flags = 0;
+  uint32_t extra_flags = 0, admission = 0;
   bool poisson = false;
   int nthreads = 4;
   for (;;) {
@@ -226,6 +269,8 @@ int main(int argc, char** argv) {
       extra_flags = CRNT_F_PURGE;
     } else if (argc > 1 && strcmp(argv[1], "--poisson") == 0) {
       poisson = true;
+    } else if (argc > 1 && strcmp(argv[1], "--admit-by-count") == 0) {
+      admission = 1;
     } else if (argc > 2 && strcmp(argv[1], "--threads") == 0) {
       nthreads = std::max(1, std::min(64, atoi(argv[2])));
       argv += 1;
@@ -238,8 +283,8 @@ int main(int argc, char** argv) {
   }
   if (argc < 7) {
     fprintf(stderr,
-            "usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--threads T] FILE UES "
-            "SECONDS RETX SEED CELLS...\n");
+            "usage: crnt_loadgen [--tune TABLE] [--purge] [--poisson] [--admit-by-count] "
+            "[--threads T] FILE UES SECONDS RETX SEED CELLS...\n");
     return 2;
   }
   FILE* f = fopen(argv[1], "rb");
@@ -266,6 +311,7 @@ int main(int argc, char** argv) {
   memset(&cfg, 0, sizeof cfg);
   cfg.harq_slots = (uint32_t)std::max(4096, max_cells * ues * 8);
   cfg.max_inflight = 65536;
+  cfg.admission = admission;
   crnt_ctx* ctx = nullptr;
   if (crnt_create(&ctx, &cfg) != CRNT_OK) return 3;
   // warm-up passes (not reported): the serving loop's buffers, the HARQ
@@ -277,10 +323,22 @@ int main(int argc, char** argv) {
     const int cells = atoi(argv[a]);
     const Point p =
         run_point(ctx, par, ptr, ues, cells, seconds, retx, seed, extra_flags, poisson, nthreads);
+    const crnt_serve_stats& s = p.st;
+    const double wall = s.worker_ns ? (double)s.worker_ns : 1.0;
     printf("{\"cells\": %d, \"tbs\": %ld, \"subframes\": %ld, \"refused_subframes\": %ld, "
            "\"errors\": %ld, \"p50_us\": %.1f, \"p99_us\": %.1f, \"deadline_miss\": %.6f, "
-           "\"gbit_s\": %.4f}\n",
-           p.cells, p.tbs, p.subframes, p.refused, p.errors, p.p50, p.p99, p.miss, p.gbit);
+           "\"gbit_s\": %.4f, \"submit_lag_us\": [%.1f, %.1f], \"queue_us\": [%.1f, %.1f], "
+           "\"device_us\": [%.1f, %.1f], \"offered_tbs\": %llu, \"admitted_tbs\": %llu, "
+           "\"refused_deadline\": %llu, \"batches\": %llu, \"worker_busy\": "
+           "{\"plan\": %.3f, \"launch\": %.3f, \"harvest\": %.3f}, "
+           "\"copy_cores\": %.3f, \"model\": {\"a_us\": %.1f, \"rate\": %.1f, "
+           "\"sigma_us\": %.1f}}\n",
+           p.cells, p.tbs, p.subframes, p.refused, p.errors, p.p50, p.p99, p.miss, p.gbit,
+           p.part[0][0], p.part[0][1], p.part[1][0], p.part[1][1], p.part[2][0], p.part[2][1],
+           (unsigned long long)s.offered_tbs, (unsigned long long)s.admitted_tbs,
+           (unsigned long long)s.refused_deadline, (unsigned long long)s.batches,
+           s.worker_plan_ns / wall, s.worker_launch_ns / wall, s.worker_harvest_ns / wall,
+           s.submit_copy_ns / wall, s.model_a_us, s.model_rate, s.model_sigma_us);
     fflush(stdout);
     // far past saturation: most subframes late by more than 20 ms at p99 (an
     // isolated host stall can push p99 up at light load without that)

@@ -120,12 +120,30 @@ struct TbPre {
   crnt::KTmpl tm, tp;       // descriptor templates of K- and K+
 };
 
+// One TB prepared for any batch (tb_prepare): its segmentation, soft-buffer
+// binding and templates, and its CB descriptors in r order with the LLR and
+// debug offsets counted from the TB's own first LLR byte and debug element.
+struct TbPrep {
+  crnt::lte::Seg s;
+  TbPre pr;
+  uint16_t p_used;
+  crnt::CbDesc cb[CRNT_MAX_CB];
+};
+
+// Where a batch put one TB.
+struct TbBase {
+  int64_t llr, dbg;  // its first LLR byte (from the launch's LLR pointer), debug base
+  uint32_t cb0;      // index of its first CB in TB order
+};
+
 // A planned batch.  Its buffers are grow-only, so re-planning a plan object
 // (plan_build) allocates nothing once it has seen a batch as large.
 struct crnt_plan {
   crnt_ctx* ctx = nullptr;
   std::vector<crnt_tb_params> tbs;
-  std::vector<TbPre> pre;
+  std::vector<TbBase> base;
+  std::vector<TbPrep> prep;             // plan_build's prepared TBs
+  std::vector<const TbPrep*> prep_ptr;
   std::vector<uint64_t> keyed;       // sort keys (low bits: CB index in TB order)
   std::vector<uint32_t> owner;       // CB index in TB order -> TB
   std::vector<int> cb_tb, cb_r;      // sorted index -> (tb, r)
@@ -167,13 +185,24 @@ namespace crnt {
 // null means the TBs' LLRs are concatenated in order.
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
                cudaStream_t stream, const int64_t* llr_base = nullptr);
+// The two halves of plan_build: tb_prepare validates one TB, binds its soft
+// buffer (CRNT_F_HARQ; last, so a TB refused binds none) and writes its CB
+// descriptors; plan_assemble plans a batch of prepared TBs.  out_base (may
+// be null): byte offset of each TB's output from the output pointer given at
+// launch; null means concatenated in order.
+int tb_prepare(crnt_ctx* ctx, const crnt_tb_params& tp, TbPrep* out);
+int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const* preps,
+                  uint32_t n, crnt_plan* pl, cudaStream_t stream, const int64_t* llr_base,
+                  const int64_t* out_base);
 // Size a plan's buffers for batches of up to max_tbs TBs and max_cbs CBs, so
 // that planning such batches later allocates nothing.
 bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs);
 // state_uploaded: the caller launches right after plan_build, whose upload
 // already zeroed the per-launch state (skips one memset).
+// gate, gate_us: see crnt_plan_launch_gated (null: no wait).
 int plan_launch(crnt_plan* pl, const int8_t* llr, uint8_t* out, cudaStream_t s, int8_t* dbg_d,
-                int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded = false);
+                int16_t* dbg_ext, uint8_t* dbg_hard, bool state_uploaded = false,
+                const uint32_t* gate = nullptr, uint32_t gate_us = 0);
 // Enqueue the D2H copy of the per-CB / per-TB results into h_res.
 int plan_fetch_results(crnt_plan* pl, cudaStream_t s);
 // Fill res[n] from h_res (after the stream has passed plan_fetch_results).

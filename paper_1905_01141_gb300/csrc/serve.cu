@@ -2,23 +2,32 @@
 //
 // Requests (transport blocks with their LLRs) arrive from many cells at any
 // time.  A worker thread batches whatever is pending into the next free
-// slot -- a CUDA stream with its own reusable plan and pinned/device
-// buffers -- and launches the fused decode there, while earlier batches are
-// still running on other slots, so work admitted later overlaps on the
-// device with work admitted earlier.  Finished batches are harvested by
-// polling their events; results wait in a done queue for crnt_poll.
-// crnt_submit copies each TB's LLRs (a CPU memcpy) into a ring of
-// page-locked host memory that the decode kernel reads in place over the
-// CPU-GPU link, and the kernel writes the decoded bits straight into
-// page-locked output buffers, so neither side issues a copy: the worker only
-// plans and launches.  Admission is by in-flight TB count and by space in
-// that ring (the memory a request holds while queued or running); beyond
-// either, crnt_submit returns CRNT_EAGAIN.  Waits are bounded: the worker sleeps on a condition variable
-// with a timeout and crnt_poll honours its timeout.
+// slot -- a CUDA stream with its own reusable plan -- and launches the fused
+// decode there, while earlier batches are still running on other slots, so
+// work admitted later overlaps on the device with work admitted earlier.
+// Finished batches are harvested by polling their events; results wait in a
+// done queue for crnt_poll.
+//
+// The submitting threads do the per-TB work: crnt_submit validates and
+// prepares each TB (segmentation, soft-buffer binding, CB descriptors) and
+// copies its LLRs (a CPU memcpy) into a ring of page-locked host memory that
+// the decode kernel reads in place over the CPU-GPU link; it also reserves
+// the TB's output bytes in a second page-locked ring, which the kernel
+// writes and crnt_poll hands out in place.  Neither side issues a copy of
+// payload data: the worker only assembles batches, launches and collects.
+//
+// Admission: by in-flight TB count, by space in the two rings (the memory a
+// request holds while queued, running or unpolled) and, unless the context
+// is configured otherwise, by predicted completion (see Admission below);
+// a refused crnt_submit returns CRNT_EAGAIN and queues nothing.  Waits are
+// bounded: the worker sleeps on a condition variable with a timeout and
+// crnt_poll honours its timeout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -39,9 +48,62 @@ constexpr uint32_t kMaxBatchTbs = 1024;
 struct Req {
   uint64_t ticket;
   crnt_tb_params tb;
+  std::unique_ptr<TbPrep> prep;  // prepared by the submitting thread
   int64_t llr_off;   // byte offset of its LLRs in the LLR ring
   uint64_t alloc;    // allocation sequence number (ring release order)
+  int64_t out_off;   // byte offset of its decoded bits in the output ring
+  uint64_t out_alloc;
   int64_t t_submit;
+  double work;       // expected decode work: trellis steps x iteration limit
+  double ahead;      // outstanding work when its subframe was admitted (itself included)
+};
+
+// Admission by predicted completion.  A TB admitted now finishes, on
+// average, a + b X after its submission, where X is the expected decode
+// work -- trellis steps times the iteration limit -- of every TB admitted
+// and not yet finished, its own subframe's included: the work ahead of it
+// drains at a rate 1/b, and a covers the launch, one decode and the
+// collection.  (a, b) is refitted by least squares, with exponential
+// forgetting, to the completions seen -- each TB gives one (X at its
+// admission, latency) pair -- and held near prior values by a penalty that
+// counts as a few pseudo-observations, so a cold start, or a load that
+// leaves X nearly constant, keeps a sensible slope.  The residuals' spread
+// sigma gives the margin: a subframe is refused when a + b X + z sigma
+// passes the deadline, unless nothing at all is outstanding.
+struct Admission {
+  static constexpr double kA0 = 150.0;     // prior latency with nothing ahead (us)
+  static constexpr double kB0 = 1.0e-5;    // prior us per unit of work (1e11 units/s)
+  static constexpr double kBmin = 2.0e-6;  // at most 5e11 units/s (~4x a full decode)
+  static constexpr double kBmax = 1.0e-3;
+  static constexpr double kPrior = 16.0;   // weight of the prior, in observations
+  static constexpr double kXs = 2.0e7;     // work scale at which the slope prior acts
+  static constexpr double kMemory = 50000.0;  // TBs after which an observation's weight is 1/e
+  static constexpr double kZ = 3.0;
+  double sw = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
+  double a = kA0, b = kB0, sigma = 50.0;
+  double predict(double x) const { return a + b * x + kZ * sigma; }
+  // Fold in one batch's sums (n observations) and refit.
+  void update(double n, double bw, double bx, double by, double bxx, double bxy, double byy) {
+    const double f = std::exp(-n / kMemory);
+    sw = sw * f + bw;
+    sx = sx * f + bx;
+    sy = sy * f + by;
+    sxx = sxx * f + bxx;
+    sxy = sxy * f + bxy;
+    syy = syy * f + byy;
+    const double ka = kPrior, kb = kPrior * kXs * kXs;
+    const double m00 = sw + ka, m01 = sx, m11 = sxx + kb;
+    const double v0 = sy + ka * kA0, v1 = sxy + kb * kB0;
+    const double det = m00 * m11 - m01 * m01;
+    if (!(det > 0)) return;
+    a = std::min(2000.0, std::max(10.0, (v0 * m11 - m01 * v1) / det));
+    b = std::min(kBmax, std::max(kBmin, (m00 * v1 - m01 * v0) / det));
+    if (sw > 0) {
+      const double sse = syy - 2 * a * sy - 2 * b * sxy + a * a * sw + 2 * a * b * sx +
+                         b * b * sxx;
+      sigma = std::max(10.0, std::sqrt(std::max(0.0, sse / sw)));
+    }
+  }
 };
 
 // Ring holding the LLRs of queued and running requests, released in
@@ -86,15 +148,18 @@ struct Ring {
 
 struct Done {
   crnt_tb_result res;
-  std::vector<uint8_t> bits;
+  const uint8_t* bits;  // in the output ring, or null
+  uint64_t out_alloc;   // released at the crnt_poll after the one handing it out
 };
 
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   crnt_plan plan;
-  Buf h_out{true};  // page-locked; the kernel writes the decoded bits here
   std::vector<Req> reqs;
+  std::vector<crnt_tb_params> tbs;
+  std::vector<const TbPrep*> preps;
+  std::vector<int64_t> llr_base, out_base;
   std::vector<crnt_tb_result> tmp;
   bool busy = false;
   int64_t t_start = 0;
@@ -112,10 +177,20 @@ struct Serving {
   std::vector<std::unique_ptr<Slot>> slots;
   uint64_t next_ticket = 1;
   uint64_t inflight_tbs = 0;  // queued + running
+  double work_out = 0;        // expected work of the TBs queued and running
+  Admission adm;
   int device_error = 0;
   int8_t* arena = nullptr;    // page-locked LLR ring (host address)
   int8_t* arena_dev = nullptr;  // the same ring as kernels address it
   Ring ring;
+  uint8_t* out_arena = nullptr;  // page-locked output ring the kernels write
+  uint8_t* out_arena_dev = nullptr;
+  Ring out_ring;
+  // counters of crnt_serve_stats: those under mu, and the time counters
+  // the worker and the submitting threads add without it
+  crnt_serve_stats st{};
+  std::atomic<uint64_t> t_plan{0}, t_launch{0}, t_harvest{0}, t_copy{0};
+  int64_t t_loop0 = 0;
 
   void run();
   bool launch(Slot* s, std::vector<Req>&& batch);
@@ -124,24 +199,30 @@ struct Serving {
 
 bool Serving::launch(Slot* s, std::vector<Req>&& batch) {
   s->reqs = std::move(batch);
+  const int64_t t0 = now_ns();
   const uint32_t n = (uint32_t)s->reqs.size();
-  std::vector<crnt_tb_params> tbs(n);
-  std::vector<int64_t> base(n);
+  s->tbs.resize(n);
+  s->preps.resize(n);
+  s->llr_base.resize(n);
+  s->out_base.resize(n);
   for (uint32_t i = 0; i < n; i++) {
-    tbs[i] = s->reqs[i].tb;
-    base[i] = s->reqs[i].llr_off;
+    const Req& r = s->reqs[i];
+    s->tbs[i] = r.tb;
+    s->preps[i] = r.prep.get();
+    s->llr_base[i] = r.llr_off;
+    s->out_base[i] = r.out_off;
   }
-  if (plan_build(ctx, tbs.data(), n, &s->plan, s->stream, base.data()) != CRNT_OK) return false;
-  const size_t out_bytes = s->plan.info.out_bytes;
-  if (!s->h_out.ensure(out_bytes)) return false;
-  uint8_t* out_dev = nullptr;
-  if (cudaHostGetDevicePointer((void**)&out_dev, s->h_out.p, 0) != cudaSuccess) return false;
+  if (plan_assemble(ctx, s->tbs.data(), s->preps.data(), n, &s->plan, s->stream,
+                    s->llr_base.data(), s->out_base.data()) != CRNT_OK)
+    return false;
   s->t_start = now_ns();
-  if (plan_launch(&s->plan, arena_dev, out_dev, s->stream, nullptr, nullptr, nullptr, true) !=
+  t_plan += (uint64_t)(s->t_start - t0);
+  if (plan_launch(&s->plan, arena_dev, out_arena_dev, s->stream, nullptr, nullptr, nullptr, true) !=
           CRNT_OK ||
       plan_fetch_results(&s->plan, s->stream) != CRNT_OK ||
       cudaEventRecord(s->ev, s->stream) != cudaSuccess)
     return false;
+  t_launch += (uint64_t)(now_ns() - s->t_start);
   s->busy = true;
   return true;
 }
@@ -155,33 +236,49 @@ void Serving::harvest(Slot* s, bool failed) {
     plan_fill_results(&s->plan, s->tmp.data());
     s->plan.upload_pending = false;  // the slot's event passed the upload
   }
-  size_t off = 0;
+  uint64_t late = 0;
+  const int64_t deadline = (int64_t)ctx->cfg.deadline_us * 1000;
+  double bw = 0, bx = 0, by = 0, bxx = 0, bxy = 0, byy = 0, work = 0;
   for (uint32_t i = 0; i < n; i++) {
     Done& d = out[i];
     const Req& r = s->reqs[i];
     if (failed) {
       memset(&d.res, 0, sizeof d.res);
       d.res.status = CRNT_EDEVICE;
+      d.bits = nullptr;
     } else {
       d.res = s->tmp[i];
-      const uint8_t* src = (const uint8_t*)s->h_out.p + off;
-      d.bits.assign(src, src + r.tb.A / 8);
+      d.bits = out_arena + r.out_off;
     }
-    off += r.tb.A / 8;
+    d.out_alloc = r.out_alloc;
     d.res.ticket = r.ticket;
     d.res.t_submit_ns = (uint64_t)r.t_submit;
     d.res.t_start_ns = (uint64_t)s->t_start;
     d.res.t_done_ns = (uint64_t)t_done;
+    late += t_done - r.t_submit > deadline;
+    const double x = r.ahead, y = (double)(t_done - r.t_submit) * 1e-3;
+    bw += 1;
+    bx += x;
+    by += y;
+    bxx += x * x;
+    bxy += x * y;
+    byy += y * y;
+    work += r.work;
   }
   {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& d : out) done.push_back(std::move(d));
     for (auto& r : s->reqs) ring.release(r.alloc);
     inflight_tbs -= n;
+    work_out = inflight_tbs ? std::max(0.0, work_out - work) : 0.0;
+    if (!failed) adm.update((double)n, bw, bx, by, bxx, bxy, byy);
+    st.done_tbs += n;
+    st.late_tbs += late;
   }
   s->reqs.clear();
   s->busy = false;
   cv_done.notify_all();
+  t_harvest += (uint64_t)(now_ns() - t_done);
 }
 
 void Serving::run() {
@@ -225,6 +322,10 @@ void Serving::run() {
       }
     }
     if (!batch.empty()) {
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        st.batches++;
+      }
       if (!launch(free_slot, std::move(batch))) harvest(free_slot, true);
       progress = true;
     }
@@ -250,10 +351,15 @@ static Serving* serving_get(crnt_ctx* ctx) {
   sv->ctx = ctx;
   cudaSetDevice(ctx->device);
   sv->ring.cap = (size_t)std::min<uint64_t>(ctx->cfg.mem_budget / 8, 256ull << 20);
+  sv->out_ring.cap = (size_t)std::min<uint64_t>(ctx->cfg.mem_budget / 32, 64ull << 20);
   if (cudaHostAlloc((void**)&sv->arena, sv->ring.cap, cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostGetDevicePointer((void**)&sv->arena_dev, sv->arena, 0) != cudaSuccess) {
+      cudaHostGetDevicePointer((void**)&sv->arena_dev, sv->arena, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&sv->out_arena, sv->out_ring.cap, cudaHostAllocMapped) !=
+          cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&sv->out_arena_dev, sv->out_arena, 0) != cudaSuccess) {
     cudaGetLastError();
     if (sv->arena) cudaFreeHost(sv->arena);
+    if (sv->out_arena) cudaFreeHost(sv->out_arena);
     return nullptr;
   }
   for (int i = 0; i < kSlots; i++) {
@@ -262,11 +368,11 @@ static Serving* serving_get(crnt_ctx* ctx) {
     std::unique_ptr<Slot> s(new (std::nothrow) Slot);
     if (!s || cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
-        !plan_reserve(&s->plan, kMaxBatchTbs, kMaxBatchTbs * CRNT_MAX_CB) ||
-        !s->h_out.ensure((size_t)kMaxBatchTbs * 4096))
+        !plan_reserve(&s->plan, kMaxBatchTbs, kMaxBatchTbs * CRNT_MAX_CB))
       return nullptr;
     sv->slots.push_back(std::move(s));
   }
+  sv->t_loop0 = now_ns();
   sv->th = std::thread([p = sv.get()] { p->run(); });
   ctx->serving = sv.release();
   return ctx->serving;
@@ -292,6 +398,7 @@ void serving_stop(crnt_ctx* ctx) {
     if (s->stream) cudaStreamDestroy(s->stream);
   }
   if (sv->arena) cudaFreeHost(sv->arena);
+  if (sv->out_arena) cudaFreeHost(sv->out_arena);
   delete sv;
 }
 
@@ -304,10 +411,14 @@ extern "C" {
 int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* llrs, uint32_t n,
                 uint64_t* tickets_out) {
   if (!ctx || !tbs || !llrs || !tickets_out || n == 0) return CRNT_EINVAL;
+  std::vector<Req> reqs(n);
+  double work = 0;
   for (uint32_t i = 0; i < n; i++) {
     lte::Seg s;
     int rc = validate(tbs[i], &s);
     if (rc) return rc;
+    reqs[i].work = (double)(s.Cm * s.Km + (s.C - s.Cm) * s.Kp) * tbs[i].max_iter;
+    work += reqs[i].work;
     if (!llrs[i]) return CRNT_EINVAL;
     if ((tbs[i].flags & CRNT_F_HARQ) && !tbs[i].new_data) {
       std::lock_guard<std::mutex> lk(ctx->harq_mu);
@@ -318,24 +429,67 @@ int crnt_submit(crnt_ctx* ctx, const crnt_tb_params* tbs, const int8_t* const* l
   Serving* sv = serving_get(ctx);
   if (!sv) return CRNT_EDEVICE;
   const int64_t t = now_ns();
-  std::vector<Req> reqs(n);
+  // gives back what admission took (with the lock held), for refusals and
+  // for a TB that fails its preparation
+  auto give_back = [&](uint32_t n_llr, uint32_t n_out) {
+    for (uint32_t j = 0; j < n_llr; j++) sv->ring.release(reqs[j].alloc);
+    for (uint32_t j = 0; j < n_out; j++) sv->out_ring.release(reqs[j].out_alloc);
+  };
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->device_error) return sv->device_error;
-    if (sv->inflight_tbs + n > ctx->cfg.max_inflight) return CRNT_EAGAIN;
+    sv->st.submit_calls++;
+    sv->st.offered_tbs += n;
+    if (sv->inflight_tbs + n > ctx->cfg.max_inflight) {
+      sv->st.refused_calls++;
+      return CRNT_EAGAIN;
+    }
+    const double ahead = sv->work_out + work;
+    if (ctx->cfg.admission == 0 && sv->inflight_tbs > 0 &&
+        sv->adm.predict(ahead) > (double)ctx->cfg.deadline_us) {
+      sv->st.refused_calls++;
+      sv->st.refused_deadline++;
+      return CRNT_EAGAIN;
+    }
     for (uint32_t i = 0; i < n; i++) {
-      size_t off;
+      size_t off, oo;
       if (!sv->ring.alloc(tbs[i].G, &off, &reqs[i].alloc)) {
-        for (uint32_t j = 0; j < i; j++) sv->ring.release(reqs[j].alloc);
+        give_back(i, i);
+        sv->st.refused_calls++;
+        return CRNT_EAGAIN;
+      }
+      if (!sv->out_ring.alloc(tbs[i].A / 8, &oo, &reqs[i].out_alloc)) {
+        give_back(i + 1, i);
+        sv->st.refused_calls++;
         return CRNT_EAGAIN;
       }
       reqs[i].llr_off = (int64_t)off;
+      reqs[i].out_off = (int64_t)oo;
     }
     sv->inflight_tbs += n;
+    sv->work_out = ahead;
+    for (uint32_t i = 0; i < n; i++) reqs[i].ahead = ahead;
+    sv->st.admitted_tbs += n;
+  }
+  // This thread prepares its TBs (descriptors, soft-buffer binding), so the
+  // serving worker only assembles batches.
+  for (uint32_t i = 0; i < n; i++) {
+    reqs[i].prep.reset(new (std::nothrow) TbPrep);
+    const int rc = reqs[i].prep ? tb_prepare(ctx, tbs[i], reqs[i].prep.get()) : CRNT_ENOMEM;
+    if (rc) {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      give_back(n, n);
+      sv->inflight_tbs -= n;
+      sv->work_out = sv->inflight_tbs ? std::max(0.0, sv->work_out - work) : 0.0;
+      sv->st.admitted_tbs -= n;
+      return rc;
+    }
   }
   // the LLRs are in the ring before the requests become visible (the
   // worker's launch, which reads them, follows the publication below)
+  const int64_t tc = now_ns();
   for (uint32_t i = 0; i < n; i++) memcpy(sv->arena + reqs[i].llr_off, llrs[i], tbs[i].G);
+  sv->t_copy += (uint64_t)(now_ns() - tc);
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     for (uint32_t i = 0; i < n; i++) {
@@ -356,21 +510,44 @@ int crnt_poll(crnt_ctx* ctx, crnt_tb_result* done, const uint8_t** bits, uint32_
   Serving* sv = serving_get(ctx);
   if (!sv) return CRNT_EDEVICE;
   std::unique_lock<std::mutex> lk(sv->mu);
+  // the bytes handed out by the previous call are no longer needed
+  for (const Done& d : sv->polled) sv->out_ring.release(d.out_alloc);
   sv->polled.clear();
   if (sv->done.empty() && timeout_us)
     sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us),
                          [sv] { return !sv->done.empty(); });
   uint32_t k = 0;
   while (k < max && !sv->done.empty()) {
-    sv->polled.push_back(std::move(sv->done.front()));
+    sv->polled.push_back(sv->done.front());
     sv->done.pop_front();
     k++;
   }
   for (uint32_t i = 0; i < k; i++) {
     done[i] = sv->polled[i].res;
-    if (bits) bits[i] = sv->polled[i].bits.empty() ? nullptr : sv->polled[i].bits.data();
+    if (bits) bits[i] = sv->polled[i].bits;
   }
   return (int)k;
+}
+
+int crnt_serve_stats_get(crnt_ctx* ctx, crnt_serve_stats* out) {
+  if (!ctx || !out) return CRNT_EINVAL;
+  memset(out, 0, sizeof *out);
+  std::lock_guard<std::mutex> lk(ctx->serving_mu);
+  Serving* sv = ctx->serving;
+  if (!sv) return CRNT_OK;
+  {
+    std::lock_guard<std::mutex> lk2(sv->mu);
+    *out = sv->st;
+    out->model_a_us = sv->adm.a;
+    out->model_rate = 1.0 / sv->adm.b;
+    out->model_sigma_us = sv->adm.sigma;
+  }
+  out->worker_plan_ns = sv->t_plan.load();
+  out->worker_launch_ns = sv->t_launch.load();
+  out->worker_harvest_ns = sv->t_harvest.load();
+  out->submit_copy_ns = sv->t_copy.load();
+  out->worker_ns = (uint64_t)(now_ns() - sv->t_loop0);
+  return CRNT_OK;
 }
 
 }  // extern "C"

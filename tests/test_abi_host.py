@@ -36,6 +36,7 @@ def test_struct_sizes(crnt_lib):
     assert ctypes.sizeof(crnt_lib.CbLayout) == 40
     assert ctypes.sizeof(crnt_lib.PlanInfo) == 64
     assert ctypes.sizeof(crnt_lib.CbTiming) == 48
+    assert ctypes.sizeof(crnt_lib.ServeStats) == 128
     assert crnt_lib.version() == 2
     assert crnt_lib.strerror(-1) == "invalid argument"
 

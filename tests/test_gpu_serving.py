@@ -71,16 +71,45 @@ def test_results_same_alone_and_in_the_mix(orc, crnt_lib, ctx):
 
 
 def test_admission_refuses_beyond_inflight(crnt_lib):
-    with crnt_lib.Context(0, max_inflight=4) as c:
+    with crnt_lib.Context(0, max_inflight=4, admission=1) as c:
         t = dict(A=6120, G=18444, Qm=2)
         llr = np.zeros(18444, dtype=np.int8)
+        assert c.submit([t] * 5, [llr] * 5) is None  # CRNT_EAGAIN: 5 > 4 in flight
         tk = c.submit([t] * 4, [llr] * 4)
         assert tk is not None
-        assert c.submit([t], [llr]) is None  # CRNT_EAGAIN
         got = drain(c, tk)
         assert len(got) == 4
+        st = c.serve_stats()
+        assert st["submit_calls"] == 2 and st["refused_calls"] == 1
+        assert st["offered_tbs"] == 9 and st["admitted_tbs"] == 4 and st["done_tbs"] == 4
+        assert st["refused_deadline"] == 0
         assert c.submit([t], [llr]) is not None
         assert c.poll(8, 5_000_000)
+
+
+def test_admission_refuses_by_predicted_completion(crnt_lib):
+    # a 50 us latency target: with work outstanding, the model (its prior
+    # latency alone is 150 us) predicts any further subframe late and
+    # refuses it; with nothing outstanding a subframe is always admitted
+    with crnt_lib.Context(0, deadline_us=50, max_inflight=4096) as c:
+        big = dict(A=75376, G=86400, Qm=6, max_iter=16, early_stop=0)  # 13 CBs x 16 iterations
+        llr_big = np.zeros(86400, dtype=np.int8)
+        small = dict(A=1000, G=1200, Qm=2)
+        llr_small = np.zeros(1200, dtype=np.int8)
+        tk = c.submit([big] * 32, [llr_big] * 32)
+        assert tk is not None
+        assert c.submit([small], [llr_small]) is None  # CRNT_EAGAIN
+        st = c.serve_stats()
+        assert st["refused_deadline"] == 1 and st["refused_calls"] == 1
+        assert st["admitted_tbs"] == 32 and st["offered_tbs"] == 33
+        got = drain(c, tk)
+        assert all(d["status"] == 0 for d, _ in got.values())
+        st = c.serve_stats()
+        assert st["done_tbs"] == 32 and st["late_tbs"] == 32  # each took more than 50 us
+        assert st["model_a_us"] > 0 and st["model_rate"] > 0
+        tk2 = c.submit([small], [llr_small])
+        assert tk2 is not None
+        drain(c, tk2)
 
 
 def test_poll_timeout_returns_empty(crnt_lib):
