@@ -398,11 +398,14 @@ def run_ours(args):
         tt = (None if args.no_autotune
               else crnt.tune_get() + crnt.tune_radix_get() + crnt.tune_shape_get())
         line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
-        line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(40, 48, 56, 64, 72),
+        line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(48, 64, 80, 96),
                                             tune_table=tt, purge=True)
         line["serving_poisson"] = serving_leg(crnt, dev, args.seed,
-                                              cells_list=(24, 32, 40, 48, 56, 64, 72),
+                                              cells_list=(32, 48, 56, 64, 72, 80, 96),
                                               tune_table=tt, poisson=True)
+        line["serving_admit_by_count"] = serving_leg(crnt, dev, args.seed,
+                                                     cells_list=(64, 72, 80, 96), tune_table=tt,
+                                                     admit_by_count=True)
         line["single_cb"] = single_cb_config(crnt, ctx, dev)
         line["captor"] = captor_leg(crnt, ctx, tbs, llr_d, dev)
         line["pusch"] = pusch_leg(crnt, ctx, dev, args.seed, flush)
