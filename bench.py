@@ -639,18 +639,22 @@ def subframe_latency(crnt, ctx, dev):
     return out
 
 
-def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 44, 48, 52, 56, 64, 72, 80,
-                                              96),
+def serving_leg(crnt, dev, seed, cells_list=(8, 16, 32, 48, 56, 64, 72, 80, 96, 112, 128),
                 seconds=1.5, tune_table=None, purge=False, poisson=False, threads=None,
-                extra_args=()):
+                extra_args=(), admit_by_count=False):
     """Serving loop under cell load, driven by the native open-loop load
     generator (crnt_loadgen, a client of crnt_submit / crnt_poll): every cell
     submits one subframe (8 UEs, TB mix of the TTI workload) per 1 ms period
     with a random phase and +-200 us jitter; 10 % of TBs are HARQ
     retransmissions (rv cycling 2, 3, 1, 0) combined in the device-resident
-    soft buffers.  Latency = completion - scheduled arrival.  Returns per cell
-    count p50/p99 latency, deadline-miss fraction and the largest cell count
-    whose p99 stays within 1 ms."""
+    soft buffers.  Latency = completion - scheduled arrival.  The library
+    admits a subframe only if its predicted completion is within the 1 ms
+    deadline (admit_by_count: by its in-flight and memory limits only).
+    Returns per cell count p50/p99 latency of the admitted TBs, the
+    deadline-miss fraction, offered vs admitted TBs, the latency split and
+    the serving worker's time shares; the largest cell count whose p99 stays
+    within 1 ms with nothing refused, and the largest offered cell count
+    whose admitted TBs keep p99 within 1 ms."""
     import struct
     import subprocess as sp
     from paper_1905_01141_gb300 import build as crnt_build
@@ -685,13 +689,22 @@ def serving_leg(crnt, dev, seed, cells_list=(4, 8, 16, 24, 32, 40, 44, 48, 52, 5
             cmd += ["--poisson"]
         if threads:
             cmd += ["--threads", str(threads)]
+        if admit_by_count:
+            cmd += ["--admit-by-count"]
         cmd += list(extra_args)
         cmd += [path, str(ues), str(seconds), "0.1", str(seed)] + [str(c) for c in cells_list]
         out = sp.run(cmd, capture_output=True, text=True, timeout=600)
     rows = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    for r in rows:
+        r["admitted_fraction"] = (r["admitted_tbs"] / r["offered_tbs"]) if r.get("offered_tbs") \
+            else None
     ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["refused_subframes"] == 0
           and r["errors"] == 0]
+    ok_adm = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["errors"] == 0]
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
+            "max_offered_cells_p99_le_1ms": max(ok_adm) if ok_adm else 0,
+            "admission": "by in-flight count and memory" if admit_by_count
+                         else "by predicted completion within 1 ms",
             "load_generator": "crnt_loadgen (native, open loop)", "rc": out.returncode,
             "purge_on_failure": purge,
             "arrivals": "exponential, mean 1 ms per cell" if poisson
