@@ -258,10 +258,14 @@ static int build_dm(uint32_t* hd, uint8_t* fkey, int n, int K, int P, int F) {
 }
 
 // Byte offset of the (K, P, F) de-rate-matching map inside the (K, P) entry
-// (after the address tables; maps for F = 0, 8, ..., 56 in turn).
+// (after the address tables, from a 16-byte boundary; maps for F = 0, 8,
+// ..., 56 in turn).  A map holds 3 (K + 4) - 2 F entries of 4 bytes, a
+// multiple of 16 bytes (K + 4 is a multiple of 4, F of 8), so every map
+// starts on a 16-byte boundary and the decoder may bulk-copy it in 16-byte
+// units.
 static size_t dm_offset(int K, int P, int F) {
   const int W = (K + P - 1) / P, ng = (W + kSub - 1) / kSub + 2;
-  size_t off = (size_t)ng * P * 24;
+  size_t off = ((size_t)ng * P * 24 + 15) & ~size_t(15);
   for (int f = 0; f < F; f += 8) off += (size_t)(3 * (K + 4) - 2 * f) * 4;
   return off;
 }

@@ -82,7 +82,8 @@ struct WorkItem {
 // Per-batch device state written by the kernel.
 struct DecState {
   int32_t head;       // work-queue head
-  int32_t err;        // 1: the wait on the launch's gate expired (0 = none)
+  int32_t err;        // a bounded wait expired (0 = none): 1 the launch's gate,
+                      // 2 a bulk copy into shared memory
 };
 
 struct DecParams {

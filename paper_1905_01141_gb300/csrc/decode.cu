@@ -396,9 +396,63 @@ __device__ __forceinline__ uint32_t crc_word(uint32_t r, uint32_t w, const uint3
 // their copy staged in shared memory by stage_llrs.
 // STR: the slot's index stride (1 one-CB slot, 2 lane of a pair slot; the
 // caller zeroes a pair slot's extrinsics).
+// ---- bulk copies: cp.async.bulk global -> shared, completed on an
+// mbarrier (transaction count in bytes).  A CTA owns two barriers (Bulk);
+// every thread tracks the parity each waits for next (the same sequence of
+// waits runs on all threads).  Waits are bounded: after 2^22 polls the
+// wait records an error in the launch state (reported as CRNT_ETIMEDOUT),
+// waits once more with the same bound for the copy still in flight, and
+// returns.
+struct Bulk {
+  uint32_t bar;    // shared address of barrier 0; barrier 1 at bar + 8
+  uint32_t phase;  // bit b: parity barrier b completes next
+  int32_t* err;
+};
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bulk_fence() {
+  // orders this thread's (and, after a barrier, the CTA's) earlier
+  // shared-memory accesses before the asynchronous proxy's writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// one copy of `bytes` (a multiple of 16, both addresses 16-byte aligned),
+// announced on the barrier by this thread's arrival
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); i++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_wait(Bulk& bk, int b) {
+  const uint32_t bar = bk.bar + 8u * (uint32_t)b, par = (bk.phase >> b) & 1u;
+  if (!mbar_poll(bar, par)) {
+    atomicCAS(bk.err, 0, 2);
+    mbar_poll(bar, par);
+  }
+  bk.phase ^= 1u << b;
+}
+
 template <int STR>
 __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
-                        int8_t* __restrict__ soft_arena, int tid, int nthr) {
+                        int8_t* __restrict__ soft_arena, int tid, int nthr, uint8_t* mbuf,
+                        int mbuf_bytes, Bulk& bk) {
   // descriptor fields in registers: the shared-memory stores below go
   // through generic pointers and would otherwise force reloads
   const int K = d.K, F = d.F, R = d.R, E = d.E, Nv = d.Nv, rank0 = d.rank0;
@@ -421,9 +475,7 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     // entries, and the filler loop below fills the filler places.
     int8_t* const base = sl.sys;
     const int tp3 = 3 * W * P;
-#pragma unroll 8
-    for (int r = tid; r < Nv; r += nthr) {
-      const uint32_t m = __ldg(dm + r);
+    auto visit = [&](uint32_t m, int r) {
       int k = r - rank0;
       if (k < 0) k += Nv;
       const int pos = (int)(m >> 16), dst = (int)(m & 0xFFFFu);
@@ -433,6 +485,41 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
       if (dst < tp3) base[STR * dst] = v;  // streams are contiguous: s tp + t -> STR (s tp + t)
       else sl.tail[dst - tp3] = v;
       if (soft) soft[pos] = v;
+    };
+    if (mbuf_bytes >= 2048) {
+      // the map streamed through mbuf (free until the first SISO pass) in
+      // two alternating chunks of ce entries, each one bulk copy; chunk c + 2
+      // is issued once every thread is done with chunk c.  The map starts
+      // 16-byte aligned and holds a multiple of 4 entries, so every copy is
+      // whole 16-byte units inside the map.
+      const int ce = min(2048, ((mbuf_bytes >> 1) >> 4) << 2);
+      const int nch = (Nv + ce - 1) / ce;
+      const uint32_t b0 = smem_u32(mbuf);
+      auto issue = [&](int c) {
+        const int r0 = c * ce;
+        const uint32_t bytes = 4u * (uint32_t)(min(Nv, r0 + ce) - r0);
+        bulk_load(b0 + 4u * (uint32_t)((c & 1) * ce), dm + r0, bytes, bk.bar + 8u * (c & 1));
+      };
+      if (tid == 0) {
+        bulk_fence();
+        issue(0);
+        if (nch > 1) issue(1);
+      }
+      for (int c = 0; c < nch; c++) {
+        bulk_wait(bk, c & 1);
+        const uint32_t* m = (const uint32_t*)mbuf + (c & 1) * ce;
+        const int r0 = c * ce, r1 = min(Nv, r0 + ce);
+#pragma unroll 4
+        for (int r = r0 + tid; r < r1; r += nthr) visit(m[r - r0], r);
+        __syncthreads();  // chunk c read by all: its buffer can be refilled
+        if (tid == 0 && c + 2 < nch) {
+          bulk_fence();
+          issue(c + 2);
+        }
+      }
+    } else {
+#pragma unroll 8
+      for (int r = tid; r < Nv; r += nthr) visit(__ldg(dm + r), r);
     }
   }
   // otherwise rows x = unit * R + i, walked with (unit, i) updated incrementally
@@ -1519,7 +1606,7 @@ __device__ void finish_cb(const DecParams& prm, const CbDesc& d, const CbSlot& s
 // A pair item: two CBs of equal (K, P) on threads 0..P-1, one pair slot.
 __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkItem& wi, uint8_t* slots, int tid,
                               const uint32_t* tabA, const uint32_t* tabB, const int* mi_tab,
-                              int* s_remaining, int* s_maxit) {
+                              int* s_remaining, int* s_maxit, Bulk& bk) {
   const CbDesc* cbs = prm.cbs + wi.cb0;
   const CbDesc* dA = cbs;
   const CbDesc* dB = cbs + 1;
@@ -1530,19 +1617,25 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
   const CbSlot sB = make_pair_slot(slots, K, P, W, 1);
   if (tid == 0) stamp(prm, wi.cb0, 2, 0, gtime());
   // ---- phase 0: de-rate-matching of both CBs, one after the other (they
-  // share the staging area), and the pair's extrinsics cleared
-  {
-    const PairLayout l = pair_layout(K, P, W);
-    uint4* e16 = (uint4*)(slots + l.o_ext);
-    for (int k = tid; k < (4 * W * P + 15) / 16; k += kThreads) e16[k] = make_uint4(0u, 0u, 0u, 0u);
-  }
+  // share the staging area, and the extrinsic area holds the streamed map),
+  // then the pair's extrinsics cleared
+  const PairLayout l = pair_layout(K, P, W);
+  uint8_t* const ext_area = slots + l.o_ext;
+  const int ext_bytes = align16(4 * W * P);
   stage_llrs(*dA, sA, prm.llr, tid, kThreads);
   __syncthreads();
-  derm_cb<2>(*dA, sA, llr_src(*dA, sA, prm.llr), prm.soft, tid, kThreads);
+  derm_cb<2>(*dA, sA, llr_src(*dA, sA, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
+             bk);
   __syncthreads();
   stage_llrs(*dB, sB, prm.llr, tid, kThreads);
   __syncthreads();
-  derm_cb<2>(*dB, sB, llr_src(*dB, sB, prm.llr), prm.soft, tid, kThreads);
+  derm_cb<2>(*dB, sB, llr_src(*dB, sB, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
+             bk);
+  __syncthreads();
+  {
+    uint4* e16 = (uint4*)ext_area;
+    for (int k = tid; k < ext_bytes / 16; k += kThreads) e16[k] = make_uint4(0u, 0u, 0u, 0u);
+  }
   if (tid == 0) {
     *s_remaining = 2;
     *s_maxit = max((int)dA->max_iter, (int)dB->max_iter);
@@ -1593,7 +1686,7 @@ template <bool R4, bool QT>
 __device__ __forceinline__ void run_single_item(const DecParams& prm, const WorkItem& wi,
                                                 uint8_t* slots, int tid, const uint32_t* tabA,
                                                 const uint32_t* tabB, const int* mi_tab,
-                                                int* s_remaining, int* s_maxit) {
+                                                int* s_remaining, int* s_maxit, Bulk& bk) {
   const CbDesc* cbs = prm.cbs + wi.cb0;
   const int P = cbs[0].P;
   const int G = wi.n;
@@ -1614,7 +1707,8 @@ __device__ __forceinline__ void run_single_item(const DecParams& prm, const Work
   for (int g = 0; g < G; g++) {
     const CbDesc& dg = cbs[g];
     const CbSlot sg = make_slot(slots + g * wi.smem_per_cb, dg.K, dg.P, dg.W);
-    derm_cb<1>(dg, sg, llr_src(dg, sg, prm.llr), prm.soft, tid, kThreads);
+    derm_cb<1>(dg, sg, llr_src(dg, sg, prm.llr), prm.soft, tid, kThreads, (uint8_t*)sg.ext,
+               align16(2 * dg.W * dg.P), bk);
   }
   if (tid == 0) {
     *s_remaining = G;
@@ -1672,8 +1766,8 @@ template <bool R4, bool QT>
 __device__ __noinline__ void run_single_item_call(const DecParams& prm, const WorkItem& wi,
                                                   uint8_t* slots, int tid, const uint32_t* tabA,
                                                   const uint32_t* tabB, const int* mi_tab,
-                                                  int* s_remaining, int* s_maxit) {
-  run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, s_remaining, s_maxit);
+                                                  int* s_remaining, int* s_maxit, Bulk& bk) {
+  run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, s_remaining, s_maxit, bk);
 }
 
 // The launch gate (crnt_plan_launch_gated): thread 0 of a CTA polls the
@@ -1711,6 +1805,7 @@ __global__ void __launch_bounds__(kThreads, PAIR ? kCtasPerSmPair : kCtasPerSm)
   __shared__ int s_item;
   __shared__ int s_remaining;
   __shared__ int s_maxit;
+  __shared__ __align__(8) uint64_t s_bar[2];
   uint32_t* tabA = (uint32_t*)smem;
   uint32_t* tabB = tabA + 256;
   int* mi_tab = (int*)(smem + 2048);
@@ -1726,6 +1821,13 @@ __global__ void __launch_bounds__(kThreads, PAIR ? kCtasPerSmPair : kCtasPerSm)
     (i < 256 ? tabA : tabB)[i & 255] = r & 0xFFFFFFu;
   }
 
+  Bulk bk{smem_u32(s_bar), 0u, &prm.state->err};
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bk.bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bk.bar + 8u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   if (prm.gate) {
     if (tid == 0) s_item = gate_wait(prm);
     __syncthreads();
@@ -1739,14 +1841,15 @@ __global__ void __launch_bounds__(kThreads, PAIR ? kCtasPerSmPair : kCtasPerSm)
     if (item >= prm.n_items) break;
     const WorkItem wi = prm.items[item];
     if (PAIR && wi.mode == 1) {
-      run_pair_item(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining, &s_maxit);
+      run_pair_item(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining, &s_maxit, bk);
       continue;
     }
     if (PAIR)
       run_single_item_call<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining,
-                                   &s_maxit);
+                                   &s_maxit, bk);
     else
-      run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining, &s_maxit);
+      run_single_item<R4, QT>(prm, wi, slots, tid, tabA, tabB, mi_tab, &s_remaining, &s_maxit,
+                              bk);
   }
 }
 
