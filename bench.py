@@ -62,6 +62,10 @@ def parse():
                     help="CTA shape: the autotuner's choice per K, or one for all K (1 one CB "
                          "per thread, 2 CB pairs in 16-bit lanes)")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
+    ap.add_argument("--legs", default=None,
+                    help="comma-separated subset of the extra legs to run (steady, e2e, "
+                         "subframe, serving, single_cb, captor, pusch, radix4, encoder, "
+                         "cpu_baseline); default all")
     ap.add_argument("--sweep", choices=["bler", "stop", "peak"],
                     help="quality sweep instead of the bench line (stop: CRC vs mutual "
                          "information stop rule)")
@@ -264,8 +268,9 @@ def run_ours(args):
         # or a table saved by an earlier run
         t0 = time.perf_counter()
         if args.tune_table:
-            with open(args.tune_table) as f:
-                vals = [int(x) for x in f.read().split()]
+            with open(args.tune_table) as f:  # '#' lines are comments
+                vals = [int(x) for ln in f if not ln.lstrip().startswith("#")
+                        for x in ln.split()]
             table = vals[:crnt.NUM_K]
             crnt.tune_set(table)
             if len(vals) >= 2 * crnt.NUM_K:
@@ -342,12 +347,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk.start()
     t_wall = time.perf_counter()
+    # an NVTX range around the timed steps: a profiler can capture exactly
+    # these launches (ncu --nvtx --nvtx-include "timed/")
+    torch.cuda.nvtx.range_push("timed")
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
             step()
             ev[i][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     clocks = clk.stop()
@@ -392,26 +401,41 @@ def run_ours(args):
             "payload_matches_truth": truth}
 
     if not args.no_extras and rank == 0:
-        line["steady"] = steady_leg(plan, llr_d, out_d, flush, stream, info, local)
-        line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
-        line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
+        want = set(args.legs.split(",")) if args.legs else None
+
+        def leg(name):
+            return want is None or name in want
+
         tt = (None if args.no_autotune
               else crnt.tune_get() + crnt.tune_radix_get() + crnt.tune_shape_get())
-        line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
-        line["serving_purge"] = serving_leg(crnt, dev, args.seed, cells_list=(48, 64, 80, 96),
-                                            tune_table=tt, purge=True)
-        line["serving_poisson"] = serving_leg(crnt, dev, args.seed,
-                                              cells_list=(32, 48, 56, 64, 72, 80, 96),
-                                              tune_table=tt, poisson=True)
-        line["serving_admit_by_count"] = serving_leg(crnt, dev, args.seed,
-                                                     cells_list=(64, 72, 80, 96), tune_table=tt,
-                                                     admit_by_count=True)
-        line["single_cb"] = single_cb_config(crnt, ctx, dev)
-        line["captor"] = captor_leg(crnt, ctx, tbs, llr_d, dev)
-        line["pusch"] = pusch_leg(crnt, ctx, dev, args.seed, flush)
-        line["radix4_forward"] = radix_leg(crnt, ctx, tbs, llr_d, flush, dev)
-        line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
-        if not args.no_cpu_baseline and ws == 1:
+        if leg("steady"):
+            line["steady"] = steady_leg(plan, llr_d, out_d, flush, stream, info, local)
+        if leg("e2e"):
+            line["e2e"] = e2e_leg(ctx, tbs, llr_h, info, args)
+        if leg("subframe"):
+            line["subframe_latency"] = subframe_latency(crnt, ctx, dev)
+        if leg("serving"):
+            line["serving"] = serving_leg(crnt, dev, args.seed, tune_table=tt)
+            line["serving_purge"] = serving_leg(crnt, dev, args.seed,
+                                                cells_list=(48, 64, 80, 96), tune_table=tt,
+                                                purge=True)
+            line["serving_poisson"] = serving_leg(crnt, dev, args.seed,
+                                                  cells_list=(32, 48, 56, 64, 72, 80, 96),
+                                                  tune_table=tt, poisson=True)
+            line["serving_admit_by_count"] = serving_leg(crnt, dev, args.seed,
+                                                         cells_list=(64, 72, 80, 96),
+                                                         tune_table=tt, admit_by_count=True)
+        if leg("single_cb"):
+            line["single_cb"] = single_cb_config(crnt, ctx, dev)
+        if leg("captor"):
+            line["captor"] = captor_leg(crnt, ctx, tbs, llr_d, dev)
+        if leg("pusch"):
+            line["pusch"] = pusch_leg(crnt, ctx, dev, args.seed, flush)
+        if leg("radix4"):
+            line["radix4_forward"] = radix_leg(crnt, ctx, tbs, llr_d, flush, dev)
+        if leg("encoder"):
+            line["encoder"] = encoder_rate(crnt, ctx, dev, tbs, pay)
+        if not args.no_cpu_baseline and ws == 1 and leg("cpu_baseline"):
             line["cpu_baseline"] = cpu_baseline(shapes, args.seed)
     plan.close()
     ctx.close()
