@@ -677,8 +677,10 @@ def serving_leg(crnt, dev, seed, cells_list=(8, 16, 32, 48, 56, 64, 72, 80, 96, 
     Returns per cell count p50/p99 latency of the admitted TBs, the
     deadline-miss fraction, offered vs admitted TBs, the latency split and
     the serving worker's time shares; the largest cell count whose p99 stays
-    within 1 ms with nothing refused, and the largest offered cell count
-    whose admitted TBs keep p99 within 1 ms."""
+    within 1 ms with nothing refused (and with at most 0.1 % of subframes
+    refused: admission turns away the odd subframe that arrives during a
+    transient backlog), and the largest offered cell count whose admitted
+    TBs keep p99 within 1 ms."""
     import struct
     import subprocess as sp
     from paper_1905_01141_gb300 import build as crnt_build
@@ -725,7 +727,10 @@ def serving_leg(crnt, dev, seed, cells_list=(8, 16, 32, 48, 56, 64, 72, 80, 96, 
     ok = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["refused_subframes"] == 0
           and r["errors"] == 0]
     ok_adm = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["errors"] == 0]
+    ok_rare = [r["cells"] for r in rows if r["p99_us"] <= 1000.0 and r["errors"] == 0
+               and r["refused_subframes"] <= 0.001 * r["subframes"]]
     return {"points": rows, "max_cells_p99_le_1ms": max(ok) if ok else 0,
+            "max_cells_p99_le_1ms_refused_le_0.1pct": max(ok_rare) if ok_rare else 0,
             "max_offered_cells_p99_le_1ms": max(ok_adm) if ok_adm else 0,
             "admission": "by in-flight count and memory" if admit_by_count
                          else "by predicted completion within 1 ms",

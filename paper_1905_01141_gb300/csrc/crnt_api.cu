@@ -549,7 +549,7 @@ int tb_prepare(crnt_ctx* ctx, const crnt_tb_params& tp, TbPrep* out) {
 }
 
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
-               cudaStream_t stream, const int64_t* llr_base) {
+               cudaStream_t stream, const int64_t* llr_base, uint32_t batch_cbs) {
   if (pl->prep.size() < n) pl->prep.resize(n);
   pl->prep_ptr.resize(n);
   for (uint32_t t = 0; t < n; t++) {
@@ -557,12 +557,13 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
     if (rc) return rc;
     pl->prep_ptr[t] = &pl->prep[t];
   }
-  return plan_assemble(ctx, tbs, pl->prep_ptr.data(), n, pl, stream, llr_base, nullptr);
+  return plan_assemble(ctx, tbs, pl->prep_ptr.data(), n, pl, stream, llr_base, nullptr,
+                       batch_cbs);
 }
 
 int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const* preps,
                   uint32_t n, crnt_plan* pl, cudaStream_t stream, const int64_t* llr_base,
-                  const int64_t* out_base) {
+                  const int64_t* out_base, uint32_t batch_cbs) {
   pl->ctx = ctx;
   pl->tbs.assign(tbs, tbs + n);
   pl->segs.resize(n);
@@ -692,10 +693,13 @@ int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const*
   // Pairs shorten a batch that fills at least two waves of CTAs in either
   // shape; a smaller batch (one subframe, a few TBs) finishes sooner with
   // one CB per thread (more CTAs in flight, one CB each), so it runs that
-  // way -- the shape never changes a decoded value.
+  // way -- the shape never changes a decoded value.  A chunk of a larger
+  // call counts that call's CBs (batch_cbs): its kernels overlap the other
+  // chunks', so throughput, not the chunk's own latency, decides.
   const int pair_min_cbs =
       ctx->cfg.pair_min_cbs ? (int)ctx->cfg.pair_min_cbs : 2 * kCtasPerSm * ctx->num_sms;
-  const bool allow_pairs = qtab_all && (int)ncb >= pair_min_cbs;
+  const bool allow_pairs =
+      qtab_all && (int64_t)std::max<uint32_t>(ncb, batch_cbs) >= (int64_t)pair_min_cbs;
   int max_item_bytes = 0;
   bool pair_any = false;
   WorkItem wi{0, 0, 0, 0};
@@ -1192,6 +1196,13 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   // next ones and their LLRs are still in flight.  Chunk c runs on its own
   // stream, so a later chunk's CTAs fill the SMs as an earlier chunk's drain.
   uint32_t bnd[NC + 1] = {0, n, n, n};
+  // the call's CBs: C = 1 for B = A + 24 <= 6144, else ceil(B / 6120) (TS
+  // 36.212 5.1.2); invalid TBs are refused by the planner
+  uint32_t total_cbs = 0;
+  for (uint32_t t = 0; t < n; t++) {
+    const uint32_t B = tbs[t].A + 24u;
+    total_cbs += B <= 6144u ? 1u : (B + 6119u) / 6120u;
+  }
   int nch = 1;
   if (n >= 24) {
     nch = 3;
@@ -1260,7 +1271,7 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
       rc = CRNT_EDEVICE;
       break;
     }
-    rc = plan_build(ctx, tbs + t0, m, plan, s);
+    rc = plan_build(ctx, tbs + t0, m, plan, s, nullptr, total_cbs);
     if (rc) break;
     if (!llr_dev && llr_at[c + 1] > llr_at[c] &&
         cudaStreamWaitEvent(s, ctx->chunk_ev[c], 0) != cudaSuccess) {

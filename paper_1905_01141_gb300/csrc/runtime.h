@@ -183,8 +183,10 @@ namespace crnt {
 // buffers are already large enough; allocates otherwise).  llr_base (may be
 // null): byte offset of each TB's LLRs from the LLR pointer given at launch;
 // null means the TBs' LLRs are concatenated in order.
+// batch_cbs: CBs of the whole call this batch belongs to, when larger than
+// the batch itself (it decides whether CB pairs are formed); 0 = the batch's.
 int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* pl,
-               cudaStream_t stream, const int64_t* llr_base = nullptr);
+               cudaStream_t stream, const int64_t* llr_base = nullptr, uint32_t batch_cbs = 0);
 // The two halves of plan_build: tb_prepare validates one TB, binds its soft
 // buffer (CRNT_F_HARQ; last, so a TB refused binds none) and writes its CB
 // descriptors; plan_assemble plans a batch of prepared TBs.  out_base (may
@@ -193,7 +195,7 @@ int plan_build(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, crnt_plan* 
 int tb_prepare(crnt_ctx* ctx, const crnt_tb_params& tp, TbPrep* out);
 int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const* preps,
                   uint32_t n, crnt_plan* pl, cudaStream_t stream, const int64_t* llr_base,
-                  const int64_t* out_base);
+                  const int64_t* out_base, uint32_t batch_cbs = 0);
 // Size a plan's buffers for batches of up to max_tbs TBs and max_cbs CBs, so
 // that planning such batches later allocates nothing.
 bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs);

@@ -69,12 +69,18 @@ struct Req {
 // counts as a few pseudo-observations, so a cold start, or a load that
 // leaves X nearly constant, keeps a sensible slope.  The residuals' spread
 // sigma gives the margin: a subframe is refused when a + b X + z sigma
-// passes the deadline, unless nothing at all is outstanding.
+// passes the deadline, unless nothing at all is outstanding.  The fit is
+// robust to single stalls (a TB that waited for a one-time allocation, a
+// descheduled thread): each latency enters clipped to within max(4 sigma,
+// 100 us) of the current prediction, so one outlier moves the fit and the
+// spread by a bounded step, while a lasting change still moves them batch by
+// batch; and the rate stays above 5e10 units/s (a full batch at the
+// iteration limit drains ~1.2e11).
 struct Admission {
   static constexpr double kA0 = 150.0;     // prior latency with nothing ahead (us)
   static constexpr double kB0 = 1.0e-5;    // prior us per unit of work (1e11 units/s)
   static constexpr double kBmin = 2.0e-6;  // at most 5e11 units/s (~4x a full decode)
-  static constexpr double kBmax = 1.0e-3;
+  static constexpr double kBmax = 2.0e-5;  // at least 5e10 units/s
   static constexpr double kPrior = 16.0;   // weight of the prior, in observations
   static constexpr double kXs = 2.0e7;     // work scale at which the slope prior acts
   static constexpr double kMemory = 50000.0;  // TBs after which an observation's weight is 1/e
@@ -82,6 +88,11 @@ struct Admission {
   double sw = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
   double a = kA0, b = kB0, sigma = 50.0;
   double predict(double x) const { return a + b * x + kZ * sigma; }
+  // a latency observation as it enters the fit
+  double clip(double x, double y) const {
+    const double p = a + b * x, m = std::max(4.0 * sigma, 100.0);
+    return std::min(p + m, std::max(p - m, y));
+  }
   // Fold in one batch's sums (n observations) and refit.
   void update(double n, double bw, double bx, double by, double bxx, double bxy, double byy) {
     const double f = std::exp(-n / kMemory);
@@ -256,7 +267,8 @@ void Serving::harvest(Slot* s, bool failed) {
     d.res.t_start_ns = (uint64_t)s->t_start;
     d.res.t_done_ns = (uint64_t)t_done;
     late += t_done - r.t_submit > deadline;
-    const double x = r.ahead, y = (double)(t_done - r.t_submit) * 1e-3;
+    // (the worker is the model's only writer, so it reads it without the lock)
+    const double x = r.ahead, y = adm.clip(x, (double)(t_done - r.t_submit) * 1e-3);
     bw += 1;
     bx += x;
     by += y;
