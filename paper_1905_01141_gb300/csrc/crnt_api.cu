@@ -399,7 +399,7 @@ int validate(const crnt_tb_params& t, lte::Seg* seg) {
   if (lte::e_r((int)t.G, t.Qm, t.NL, seg->C, 0) < 1) return CRNT_EINVAL;
   if (t.flags & CRNT_F_PUSCH) {
     const int ncol = pusch_cols(t);
-    if (ncol > 14 || t.c_init >> 31 || t.G > (uint32_t)(kPuschChunk * kPuschMaxChunks) ||
+    if (ncol > kPuschMaxCols || t.c_init >> 31 || t.G > (uint32_t)(kPuschChunk * kPuschMaxChunks) ||
         t.G % (uint32_t)(t.Qm * t.NL * ncol))
       return CRNT_EINVAL;
   }

@@ -160,6 +160,7 @@ struct PuschChunk {
 };
 // One front-stage tile: whole interleaver rows, at most kPuschTile bytes.
 constexpr int kPuschTile = 8192;
+constexpr int kPuschMaxCols = 14;  // interleaver columns (SC-FDMA data symbols) at most
 __host__ __device__ inline int pusch_tile_rows(int qmnl, int ncol) {
   const int r = kPuschTile / (qmnl * ncol);
   return r > 0 ? r : 1;
