@@ -449,10 +449,37 @@ __device__ __forceinline__ void bulk_wait(Bulk& bk, int b) {
   bk.phase ^= 1u << b;
 }
 
+// Where one CB's de-rate-matched LLRs come from and go (the map path).
+struct DermTarget {
+  const int8_t* e;  // its E received LLRs (staged copy or global)
+  int8_t* base;     // the slot's streams (sys, then par1, par2)
+  int8_t* tail;     // its tail LLRs
+  int8_t* soft;     // its soft buffer, or null
+  bool combine;     // add the soft buffer's contents
+  int rank0, E;
+};
+__device__ __forceinline__ DermTarget derm_target(const CbDesc& d, const CbSlot& sl,
+                                                  const int8_t* e, int8_t* soft_arena) {
+  DermTarget t;
+  t.e = e;
+  t.base = sl.sys;
+  t.tail = sl.tail;
+  t.soft = d.soft_off >= 0 ? soft_arena + d.soft_off : nullptr;
+  t.combine = t.soft != nullptr && !d.new_data;
+  t.rank0 = d.rank0;
+  t.E = d.E;
+  return t;
+}
+
+// De-rate-matching of a CB into its slot.  d2 / s2 / e2 (optional, only
+// with a map): a second CB with the same (K, P, F) -- the other CB of a
+// pair -- de-rate-matched in the same pass over the map, which is then
+// streamed into shared memory once for both.
 template <int STR>
 __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
                         int8_t* __restrict__ soft_arena, int tid, int nthr, uint8_t* mbuf,
-                        int mbuf_bytes, Bulk& bk) {
+                        int mbuf_bytes, Bulk& bk, const CbDesc* d2 = nullptr,
+                        const CbSlot* s2 = nullptr, const int8_t* e2 = nullptr) {
   // descriptor fields in registers: the shared-memory stores below go
   // through generic pointers and would otherwise force reloads
   const int K = d.K, F = d.F, R = d.R, E = d.E, Nv = d.Nv, rank0 = d.rank0;
@@ -473,53 +500,81 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     // the slot (streams at s W P, tail bits after 3 W P).  NULL positions
     // (dummies, filler bits) are not visited: no step reads their soft
     // entries, and the filler loop below fills the filler places.
-    int8_t* const base = sl.sys;
     const int tp3 = 3 * W * P;
-    auto visit = [&](uint32_t m, int r) {
-      int k = r - rank0;
+    const DermTarget tA = derm_target(d, sl, e, soft_arena);
+    DermTarget tB = tA;
+    if (d2) tB = derm_target(*d2, *s2, e2, soft_arena);
+    // rank r's received LLRs are e[k], e[k + Nv], ... for k = r - rank0
+    // (mod Nv) below E, summed (with the soft buffer's entry when combining)
+    // and saturated to int8
+    auto visit = [&](const DermTarget& t, uint32_t m, int r) {
+      int k = r - t.rank0;
       if (k < 0) k += Nv;
       const int pos = (int)(m >> 16), dst = (int)(m & 0xFFFFu);
-      int acc = combine ? soft[pos] : 0;
-      for (; k < E; k += Nv) acc = max(min(acc + (int)e[k], 127), -127);
+      int acc = t.combine ? t.soft[pos] : 0;
+      for (; k < t.E; k += Nv) acc = max(min(acc + (int)t.e[k], 127), -127);
       const int8_t v = (int8_t)acc;
-      if (dst < tp3) base[STR * dst] = v;  // streams are contiguous: s tp + t -> STR (s tp + t)
-      else sl.tail[dst - tp3] = v;
-      if (soft) soft[pos] = v;
+      if (dst < tp3) t.base[STR * dst] = v;  // streams are contiguous: s tp + t -> STR (s tp + t)
+      else t.tail[dst - tp3] = v;
+      if (t.soft) t.soft[pos] = v;
     };
-    if (mbuf_bytes >= 2048) {
-      // the map streamed through mbuf (free until the first SISO pass) in
-      // two alternating chunks of ce entries, each one bulk copy; chunk c + 2
-      // is issued once every thread is done with chunk c.  The map starts
-      // 16-byte aligned and holds a multiple of 4 entries, so every copy is
-      // whole 16-byte units inside the map.
-      const int ce = min(2048, ((mbuf_bytes >> 1) >> 4) << 2);
-      const int nch = (Nv + ce - 1) / ce;
-      const uint32_t b0 = smem_u32(mbuf);
-      auto issue = [&](int c) {
-        const int r0 = c * ce;
-        const uint32_t bytes = 4u * (uint32_t)(min(Nv, r0 + ce) - r0);
-        bulk_load(b0 + 4u * (uint32_t)((c & 1) * ce), dm + r0, bytes, bk.bar + 8u * (c & 1));
-      };
-      if (tid == 0) {
-        bulk_fence();
-        issue(0);
-        if (nch > 1) issue(1);
-      }
-      for (int c = 0; c < nch; c++) {
-        bulk_wait(bk, c & 1);
-        const uint32_t* m = (const uint32_t*)mbuf + (c & 1) * ce;
-        const int r0 = c * ce, r1 = min(Nv, r0 + ce);
-#pragma unroll 4
-        for (int r = r0 + tid; r < r1; r += nthr) visit(m[r - r0], r);
-        __syncthreads();  // chunk c read by all: its buffer can be refilled
-        if (tid == 0 && c + 2 < nch) {
+    // the common case -- no soft buffer and E <= Nv, so at most one LLR per
+    // rank -- with the same result: max(e[k], -127), or 0 when k >= E
+    auto visit_one = [&](const DermTarget& t, uint32_t m, int r) {
+      int k = r - t.rank0;
+      if (k < 0) k += Nv;
+      const int dst = (int)(m & 0xFFFFu);
+      const int8_t v = k < t.E ? (int8_t)max((int)t.e[k], -127) : (int8_t)0;
+      if (dst < tp3) t.base[STR * dst] = v;
+      else t.tail[dst - tp3] = v;
+    };
+    auto run = [&](auto vis) {
+      if (mbuf_bytes >= 2048) {
+        // the map streamed through mbuf (free until the first SISO pass) in
+        // two alternating chunks of ce entries, each one bulk copy; chunk c +
+        // 2 is issued once every thread is done with chunk c.  The map starts
+        // 16-byte aligned and holds a multiple of 4 entries, so every copy is
+        // whole 16-byte units inside the map.
+        const int ce = min(2048, ((mbuf_bytes >> 1) >> 4) << 2);
+        const int nch = (Nv + ce - 1) / ce;
+        const uint32_t b0 = smem_u32(mbuf);
+        auto issue = [&](int c) {
+          const int r0 = c * ce;
+          const uint32_t bytes = 4u * (uint32_t)(min(Nv, r0 + ce) - r0);
+          bulk_load(b0 + 4u * (uint32_t)((c & 1) * ce), dm + r0, bytes, bk.bar + 8u * (c & 1));
+        };
+        if (tid == 0) {
           bulk_fence();
-          issue(c + 2);
+          issue(0);
+          if (nch > 1) issue(1);
         }
-      }
-    } else {
+        for (int c = 0; c < nch; c++) {
+          bulk_wait(bk, c & 1);
+          const uint32_t* m = (const uint32_t*)mbuf + (c & 1) * ce;
+          const int r0 = c * ce, r1 = min(Nv, r0 + ce);
+#pragma unroll 4
+          for (int r = r0 + tid; r < r1; r += nthr) vis(m[r - r0], r);
+          __syncthreads();  // chunk c read by all: its buffer can be refilled
+          if (tid == 0 && c + 2 < nch) {
+            bulk_fence();
+            issue(c + 2);
+          }
+        }
+      } else {
 #pragma unroll 8
-      for (int r = tid; r < Nv; r += nthr) visit(__ldg(dm + r), r);
+        for (int r = tid; r < Nv; r += nthr) vis(__ldg(dm + r), r);
+      }
+    };
+    const bool one = tA.soft == nullptr && E <= Nv && (!d2 || (tB.soft == nullptr && tB.E <= Nv));
+    if (d2) {
+      if (one)
+        run([&](uint32_t m, int r) { visit_one(tA, m, r); visit_one(tB, m, r); });
+      else
+        run([&](uint32_t m, int r) { visit(tA, m, r); visit(tB, m, r); });
+    } else if (one) {
+      run([&](uint32_t m, int r) { visit_one(tA, m, r); });
+    } else {
+      run([&](uint32_t m, int r) { visit(tA, m, r); });
     }
   }
   // otherwise rows x = unit * R + i, walked with (unit, i) updated incrementally
@@ -554,6 +609,10 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     const int t = tr(k);
     sl.sys[STR * t] = 127;
     sl.par1[STR * t] = 0;
+    if (d2) {
+      s2->sys[STR * t] = 127;
+      s2->par1[STR * t] = 0;
+    }
   }
   if (STR == 1) {
     const int tp = W * P;
@@ -561,16 +620,9 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     for (int k = tid; k < (2 * tp + 15) / 16; k += nthr) ext16[k] = make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) {
-    sl.flags[0] = 0;
-    sl.flags[1] = 0;
-    sl.flags[2] = 0;
-    sl.flags[3] = 0;
-    sl.flags[4] = 0;
-    sl.flags[5] = 0;
-    sl.flags[6] = 0;
-    sl.flags[7] = 0;
-    sl.flags[8] = 0;
-    sl.flags[9] = 0;
+    for (int k = 0; k < 10; k++) sl.flags[k] = 0;
+    if (d2)
+      for (int k = 0; k < 10; k++) s2->flags[k] = 0;
   }
 }
 
@@ -1622,15 +1674,31 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
   const PairLayout l = pair_layout(K, P, W);
   uint8_t* const ext_area = slots + l.o_ext;
   const int ext_bytes = align16(4 * W * P);
-  stage_llrs(*dA, sA, prm.llr, tid, kThreads);
-  __syncthreads();
-  derm_cb<2>(*dA, sA, llr_src(*dA, sA, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
-             bk);
-  __syncthreads();
-  stage_llrs(*dB, sB, prm.llr, tid, kThreads);
-  __syncthreads();
-  derm_cb<2>(*dB, sB, llr_src(*dB, sB, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
-             bk);
+  // When both CBs use the same map (same K, P, F) and their LLRs fit the
+  // staging area together -- B's from the first 16-byte boundary after A's
+  // -- one pass over the map de-rate-matches both.
+  const int offB = (dA->E + 30) & ~15;
+  if (dA->dm != nullptr && dA->dm == dB->dm && ext_bytes >= 2048 &&
+      offB + dB->E + 15 <= sA.stage_cap) {
+    CbSlot sB2 = sB;
+    sB2.stage = sA.stage + offB;
+    sB2.stage_cap = sA.stage_cap - offB;
+    stage_llrs(*dA, sA, prm.llr, tid, kThreads);
+    stage_llrs(*dB, sB2, prm.llr, tid, kThreads);
+    __syncthreads();
+    derm_cb<2>(*dA, sA, llr_src(*dA, sA, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
+               bk, dB, &sB, llr_src(*dB, sB2, prm.llr));
+  } else {
+    stage_llrs(*dA, sA, prm.llr, tid, kThreads);
+    __syncthreads();
+    derm_cb<2>(*dA, sA, llr_src(*dA, sA, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
+               bk);
+    __syncthreads();
+    stage_llrs(*dB, sB, prm.llr, tid, kThreads);
+    __syncthreads();
+    derm_cb<2>(*dB, sB, llr_src(*dB, sB, prm.llr), prm.soft, tid, kThreads, ext_area, ext_bytes,
+               bk);
+  }
   __syncthreads();
   {
     uint4* e16 = (uint4*)ext_area;
