@@ -1644,10 +1644,15 @@ __device__ void finish_cb(const DecParams& prm, const CbDesc& d, const CbSlot& s
       contrib = ((contrib << 8) & 0xFFFFFFu) ^ tabA[(contrib >> 16) & 0xFFu];
     atomicXor(&prm.tb_crc[2 * d.tb], contrib);
     if (!cb_ok) atomicOr(&prm.tb_crc[2 * d.tb + 1], 1u);
-    __threadfence();
-    const int done = atomicAdd(&prm.tb_done[d.tb], 1);
+    // count the CB with acquire-release semantics: its CRC updates above
+    // happen before the count, and the TB's last CB, which reads every
+    // update after its own count, sees them all
+    int done;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                 : "=r"(done)
+                 : "l"(&prm.tb_done[d.tb])
+                 : "memory");
     if (done == tb.C - 1) {
-      __threadfence();
       const uint32_t x = atomicOr(&prm.tb_crc[2 * d.tb], 0u);
       const uint32_t bad = atomicOr(&prm.tb_crc[2 * d.tb + 1], 0u);
       prm.tb_ok[d.tb] = (x == 0u && bad == 0u) ? 1 : 0;
@@ -1742,10 +1747,12 @@ __device__ __forceinline__ void run_pair_item(const DecParams& prm, const WorkIt
     finish_share(prm, *dB, sB, p, tabA);
   }
   __syncthreads();
-  if (tid == 0) {
-    finish_cb(prm, *dA, sA, wi.cb0, tabA);
-    finish_cb(prm, *dB, sB, wi.cb0 + 1, tabA);
-    stamp(prm, wi.cb0, 2, 3, gtime());
+  // the two CBs' results on threads of different warps, concurrently
+  if (tid == 0) finish_cb(prm, *dA, sA, wi.cb0, tabA);
+  if (tid == 32) finish_cb(prm, *dB, sB, wi.cb0 + 1, tabA);
+  if (prm.cb_time) {
+    __syncthreads();
+    if (tid == 0) stamp(prm, wi.cb0, 2, 3, gtime());
   }
 }
 
