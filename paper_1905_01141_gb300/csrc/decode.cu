@@ -528,6 +528,22 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
       if (dst < tp3) t.base[STR * dst] = v;
       else t.tail[dst - tp3] = v;
     };
+    // both CBs of a pair in the common case: their streams are interleaved
+    // byte by byte (STR 2, B's at A's + 1), so one 16-bit store places both
+    auto visit_two = [&](uint32_t m, int r) {
+      int kA = r - tA.rank0, kB = r - tB.rank0;
+      if (kA < 0) kA += Nv;
+      if (kB < 0) kB += Nv;
+      const int dst = (int)(m & 0xFFFFu);
+      const int vA = kA < tA.E ? max((int)tA.e[kA], -127) : 0;
+      const int vB = kB < tB.E ? max((int)tB.e[kB], -127) : 0;
+      if (dst < tp3) {
+        *(uint16_t*)(tA.base + 2 * dst) = (uint16_t)((vA & 0xFF) | ((vB & 0xFF) << 8));
+      } else {
+        tA.tail[dst - tp3] = (int8_t)vA;
+        tB.tail[dst - tp3] = (int8_t)vB;
+      }
+    };
     auto run = [&](auto vis) {
       if (mbuf_bytes >= 2048) {
         // the map streamed through mbuf (free until the first SISO pass) in
@@ -567,7 +583,9 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
     };
     const bool one = tA.soft == nullptr && E <= Nv && (!d2 || (tB.soft == nullptr && tB.E <= Nv));
     if (d2) {
-      if (one)
+      if (one && STR == 2 && tB.base == tA.base + 1)
+        run(visit_two);
+      else if (one)
         run([&](uint32_t m, int r) { visit_one(tA, m, r); visit_one(tB, m, r); });
       else
         run([&](uint32_t m, int r) { visit(tA, m, r); visit(tB, m, r); });
