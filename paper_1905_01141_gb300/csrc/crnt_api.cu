@@ -597,16 +597,19 @@ int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const*
     for (int r = 0; r < s.C; r++) {
       const CbDesc& c = pp.cb[r];
       const uint64_t cost = (uint64_t)(c.W * c.max_iter);  // < 2^17
-      // descending W max_iter, then K, then P; ascending (t, r) -- one
-      // integer sorted ascending
+      // descending W max_iter, then K, then P; ascending filler count F
+      // (CBs of one (K, P, F) are adjacent, so CB pairs share their
+      // de-rate-matching map), then (t, r) -- one integer sorted ascending:
+      // cost 17 bits, K 13, P 8, F / 8 3, CB index 22
       pl->keyed.push_back(((0x1FFFFull - cost) << 46) | ((uint64_t)(0x1FFF - c.K) << 33) |
-                          ((uint64_t)(0xFF - c.P) << 25) | (uint64_t)(ncb + r));
+                          ((uint64_t)(0xFF - c.P) << 25) | ((uint64_t)(c.F >> 3) << 22) |
+                          (uint64_t)(ncb + r));
       pl->owner.push_back(t);
       dbg_off += c.K + 4;
       steps += c.K;
     }
     ncb += s.C;
-    if (ncb >= (1u << 25)) return CRNT_EINVAL;
+    if (ncb >= (1u << 22)) return CRNT_EINVAL;
     llr_off += tp.G;
     out_off += tp.A / 8;
     info_bits += tp.A;
@@ -669,7 +672,7 @@ int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const*
   // ---- pass 2: descriptors in sorted order
   bool radix4_any = false, qtab_all = true;
   for (uint32_t i = 0; i < ncb; i++) {
-    const uint32_t g = (uint32_t)(pl->keyed[i] & 0x1FFFFFF);
+    const uint32_t g = (uint32_t)(pl->keyed[i] & 0x3FFFFF);
     const uint32_t t = pl->owner[g];
     const TbBase& b = pl->base[t];
     const int r = (int)(g - b.cb0);
