@@ -639,9 +639,9 @@ int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const*
   // the results are contiguous, so one copy brings both back.
   const size_t b_cbs = sizeof(CbDesc) * ncb, b_tbs = sizeof(TbDesc) * n;
   const size_t off_tbs = al256(b_cbs), off_zero = off_tbs + al256(b_tbs);
-  const size_t s_state = 256, s_done = al256(4 * n), s_crc = al256(8 * n), s_sat = al256(4 * n);
+  const size_t s_state = 256, s_crc = al256(8 * n), s_sat = al256(4 * n);
   pl->zero_off = off_zero;
-  pl->scratch_zero = s_state + s_done + s_crc + s_sat;
+  pl->scratch_zero = s_state + s_crc + s_sat;
   const size_t off_res = off_zero + pl->scratch_zero;
   pl->res_bytes = (3 * (size_t)ncb + n + 15) & ~size_t(15);
   const size_t off_items = off_res + pl->res_bytes;
@@ -800,9 +800,8 @@ int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const*
   p.n_cbs = (int)ncb;
   p.n_tbs = (int)n;
   p.state = (DecState*)(dd + off_zero);
-  p.tb_done = (int32_t*)(dd + off_zero + s_state);
-  p.tb_crc = (uint32_t*)(dd + off_zero + s_state + s_done);
-  p.tb_sat = (uint32_t*)(dd + off_zero + s_state + s_done + s_crc);
+  p.tb_crc = (uint32_t*)(dd + off_zero + s_state);
+  p.tb_sat = (uint32_t*)(dd + off_zero + s_state + s_crc);
   p.cb_iters = dd + off_res;
   p.cb_runs = p.cb_iters + 2 * (size_t)ncb;
   p.cb_ok = p.cb_iters + ncb;
@@ -817,8 +816,7 @@ int plan_assemble(crnt_ctx* ctx, const crnt_tb_params* tbs, const TbPrep* const*
 }
 
 bool plan_reserve(crnt_plan* pl, uint32_t max_tbs, uint32_t max_cbs) {
-  const size_t zero =
-      256 + al256(4 * (size_t)max_tbs) + al256(8 * (size_t)max_tbs) + al256(4 * (size_t)max_tbs);
+  const size_t zero = 256 + al256(8 * (size_t)max_tbs) + al256(4 * (size_t)max_tbs);
   const size_t res = (3 * (size_t)max_cbs + max_tbs + 15) & ~size_t(15);
   const size_t desc = al256(sizeof(CbDesc) * max_cbs) + al256(sizeof(TbDesc) * max_tbs) + zero +
                       res + sizeof(WorkItem) * max_cbs;
@@ -873,8 +871,10 @@ void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res) {
   const uint32_t n = pl->info.n_tb;
   const int32_t err = ((const DecState*)pl->h_res.p)->err;  // a bounded device wait expired
   const uint8_t* h = (const uint8_t*)pl->h_res.p + pl->scratch_zero;
-  // per-TB saturating-pass counts: the last part of the zeroed scratch
+  // per-TB saturating-pass counts: the last part of the zeroed scratch; the
+  // TB CRC words (TB CRC24A accumulated over its CBs, failed-CB flag) before
   const uint32_t* sat = (const uint32_t*)(h - ((4 * (size_t)n + 255) & ~size_t(255)));
+  const uint32_t* crc = (const uint32_t*)((const uint8_t*)pl->h_res.p + 256);
   for (uint32_t t = 0; t < n; t++) {
     crnt_tb_result& r = res[t];
     memset(&r, 0, sizeof r);
@@ -886,7 +886,7 @@ void plan_fill_results(const crnt_plan* pl, crnt_tb_result* res) {
     r.F = (uint16_t)sg.F;
     r.P_used = pl->p_used[t];
     r.sat_passes = (uint16_t)std::min<uint32_t>(sat[t], 65535u);
-    r.tb_crc_ok = h[3 * ncb + t];
+    r.tb_crc_ok = sg.C == 1 ? h[3 * ncb + t] : (crc[2 * t] == 0u && crc[2 * t + 1] == 0u);
   }
   for (size_t i = 0; i < ncb; i++) {
     crnt_tb_result& r = res[pl->cb_tb[i]];

@@ -95,8 +95,8 @@ struct DecParams {
   uint8_t* out;
   int8_t* soft;           // soft-buffer arena base
   DecState* state;
-  int32_t* tb_done;       // [n_tbs] CBs finished
-  uint32_t* tb_crc;       // [n_tbs] xor of CRC24A contributions
+  uint32_t* tb_crc;       // [2 n_tbs] per TB: xor of its CBs' CRC24A contributions, and
+                          // nonzero once a CB failed (read by purge, and by the host)
   uint8_t* cb_iters;      // [n_cbs] by sorted CB index
   uint8_t* cb_ok;         // [n_cbs]
   uint8_t* cb_runs;       // [n_cbs] iterations run (may be null)

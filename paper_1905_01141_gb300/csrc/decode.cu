@@ -1640,8 +1640,10 @@ __device__ void finish_share(const DecParams& prm, const CbDesc& d, const CbSlot
   }
 }
 
-// Phase 2, part 2 (thread p = 0 of the CB, after a barrier): per-CB results,
-// the TB CRC by linearity, the last CB of a TB to finish decides tb_ok.
+// Phase 2, part 2 (thread p = 0 of the CB, after a barrier): per-CB results;
+// a single-CB TB's result; otherwise the CB's contribution to its TB's
+// CRC24A (by linearity) and failure word, which the host reads after the
+// launch.
 __device__ void finish_cb(const DecParams& prm, const CbDesc& d, const CbSlot& sl,
                           int sorted_idx, const uint32_t* tabA) {
   const bool purged = sl.flags[6] != 0;
@@ -1660,21 +1662,10 @@ __device__ void finish_cb(const DecParams& prm, const CbDesc& d, const CbSlot& s
     if (na) contrib = gf_mulmod(contrib, __ldg(&prm.xpowA[na]), GA);
     for (int k = 0; k < nb; k++)
       contrib = ((contrib << 8) & 0xFFFFFFu) ^ tabA[(contrib >> 16) & 0xFFu];
+    // fire-and-forget: the host decides the TB from the two words once the
+    // launch is complete (TB CRC24A zero and no failed CB)
     atomicXor(&prm.tb_crc[2 * d.tb], contrib);
     if (!cb_ok) atomicOr(&prm.tb_crc[2 * d.tb + 1], 1u);
-    // count the CB with acquire-release semantics: its CRC updates above
-    // happen before the count, and the TB's last CB, which reads every
-    // update after its own count, sees them all
-    int done;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
-                 : "=r"(done)
-                 : "l"(&prm.tb_done[d.tb])
-                 : "memory");
-    if (done == tb.C - 1) {
-      const uint32_t x = atomicOr(&prm.tb_crc[2 * d.tb], 0u);
-      const uint32_t bad = atomicOr(&prm.tb_crc[2 * d.tb + 1], 0u);
-      prm.tb_ok[d.tb] = (x == 0u && bad == 0u) ? 1 : 0;
-    }
   }
 }
 

@@ -42,8 +42,7 @@ constexpr size_t kOffItems = kOffTbs + al(sizeof(TbDesc) * kStaticTbs);
 constexpr size_t kOffXA = kOffItems + al(sizeof(WorkItem) * kStaticCbs);
 constexpr size_t kOffXB = kOffXA + al(4 * kXA);
 constexpr size_t kOffState = kOffXB + al(4 * kXB);
-constexpr size_t kOffDone = kOffState + 256;
-constexpr size_t kOffCrc = kOffDone + al(4 * kStaticTbs);
+constexpr size_t kOffCrc = kOffState + 256;
 constexpr size_t kOffSat = kOffCrc + al(8 * kStaticTbs);  // per-TB saturating-pass counts
 constexpr size_t kZeroBytes = kOffSat + al(4 * kStaticTbs) - kOffState;
 constexpr size_t kOffRes = kOffSat + al(4 * kStaticTbs);  // cb_iters | cb_ok | cb_runs | tb_ok
@@ -69,7 +68,7 @@ TbDesc h_tbs[kStaticTbs];
 WorkItem h_items[kStaticCbs];
 lte::Seg h_segs[kStaticTbs];
 uint16_t h_pused[kStaticTbs];
-uint8_t h_back[kOffRes - kOffSat + kResBytes];  // counts | results, copied back together
+uint8_t h_back[kOffRes - kOffCrc + kResBytes];  // TB CRC words | counts | results
 
 int clamp_windows(int K, int P) {
   if (P <= 0) P = tuned_p(K);  // the process-wide table (a read, no allocation)
@@ -338,7 +337,6 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
   p.out = out_k;
   p.soft = nullptr;
   p.state = (DecState*)(ws + kOffState);
-  p.tb_done = (int32_t*)(ws + kOffDone);
   p.tb_crc = (uint32_t*)(ws + kOffCrc);
   p.tb_sat = (uint32_t*)(ws + kOffSat);
   p.cb_iters = ws + kOffRes;  // cb_iters | cb_ok | cb_runs | tb_ok, as the plan path
@@ -349,7 +347,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
   p.xpowB = (const uint32_t*)(ws + kOffXB);
   p.mi_tab = (const int32_t*)(ws + kOffMi);
   for (int i = 0; i < ncb; i++) p.radix4_any |= h_cbs[i].radix4;
-  const size_t back_bytes = (kOffRes - kOffSat) + 3 * (size_t)ncb + n;
+  const size_t back_bytes = (kOffRes - kOffCrc) + 3 * (size_t)ncb + n;
   bool ok =
       cudaMemcpyAsync(ws + kOffCbs, h_cbs, sizeof(CbDesc) * ncb, cudaMemcpyHostToDevice, s) ==
           cudaSuccess &&
@@ -359,7 +357,7 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
                       s) == cudaSuccess &&
       cudaMemsetAsync(ws + kOffState, 0, kZeroBytes, s) == cudaSuccess &&
       launch_decode(p, grid, smem, s) == cudaSuccess &&
-      cudaMemcpyAsync(h_back, ws + kOffSat, back_bytes, cudaMemcpyDeviceToHost, s) ==
+      cudaMemcpyAsync(h_back, ws + kOffCrc, back_bytes, cudaMemcpyDeviceToHost, s) ==
           cudaSuccess;
   // wait for whatever was enqueued, also on failure, so that no kernel of
   // this call still uses the shared workspace when the next call clears it
@@ -368,8 +366,9 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     cudaGetLastError();
     return CRNT_EDEVICE;
   }
-  const uint32_t* sat = (const uint32_t*)h_back;
-  const uint8_t* h_res = h_back + (kOffRes - kOffSat);
+  const uint32_t* crc = (const uint32_t*)h_back;  // per TB: CRC24A word, failed-CB flag
+  const uint32_t* sat = (const uint32_t*)(h_back + (kOffSat - kOffCrc));
+  const uint8_t* h_res = h_back + (kOffRes - kOffCrc);
   for (uint32_t t = 0; t < n; t++) {
     crnt_tb_result& r = res[t];
     memset(&r, 0, sizeof r);
@@ -380,7 +379,8 @@ extern "C" int crnt_decode_batch_static(const crnt_tb_params* tbs, uint32_t n, c
     r.F = (uint16_t)h_segs[t].F;
     r.P_used = h_pused[t];
     r.sat_passes = (uint16_t)std::min<uint32_t>(sat[t], 65535u);
-    r.tb_crc_ok = h_res[3 * ncb + t];
+    r.tb_crc_ok =
+        h_segs[t].C == 1 ? h_res[3 * ncb + t] : (crc[2 * t] == 0u && crc[2 * t + 1] == 0u);
   }
   for (int i = 0; i < ncb; i++) {
     crnt_tb_result& r = res[h_cb_tb[i]];
