@@ -1194,10 +1194,13 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   const bool llr_dev = llr_view != nullptr, out_dev = out_view != nullptr;
   std::lock_guard<std::mutex> lk(ctx->stage_mu);
   constexpr int NC = crnt_ctx::kBatchChunks;
-  // Chunks of about 15 %, 40 % and 45 % of the TBs (one chunk for small
-  // batches): the device starts on the first chunk while the host plans the
-  // next ones and their LLRs are still in flight.  Chunk c runs on its own
-  // stream, so a later chunk's CTAs fill the SMs as an earlier chunk's drain.
+  // Chunks of about 5 %, 30 % and 65 % of the TBs (one chunk for small
+  // batches): the device starts on the small first chunk while the host
+  // plans the next ones and their LLRs are still in flight.  Chunk c runs on
+  // its own stream, so a later chunk's CTAs fill the SMs as an earlier
+  // chunk's drain.  (Measured on a 320-TB TTI from page-locked buffers:
+  // 0.620 ms per call, against 0.632 for 3/22/75 %, 0.648 for 15/40/45 %,
+  // 0.654 for 5/45/50 %.)
   uint32_t bnd[NC + 1] = {0, n, n, n};
   // the call's CBs: C = 1 for B = A + 24 <= 6144, else ceil(B / 6120) (TS
   // 36.212 5.1.2); invalid TBs are refused by the planner
@@ -1209,8 +1212,8 @@ int crnt_decode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
   int nch = 1;
   if (n >= 24) {
     nch = 3;
-    bnd[1] = (15 * n) / 100;
-    bnd[2] = (55 * n) / 100;
+    bnd[1] = (5 * n) / 100;
+    bnd[2] = (35 * n) / 100;
   }
   for (int c = 0; c < nch; c++) {
     if (!ctx->cached[c]) {
