@@ -148,3 +148,19 @@ def test_pairs_harq(orc, crnt_lib, ctx, pairs):
         if ok2:
             assert np.array_equal(np.unpackbits(g2["out"][u * (A // 8):(u + 1) * (A // 8)]), bits2)
         assert ctx.harq_release(5, u, 1) == 0
+
+
+def test_pairs_joint_derate_matching(orc, crnt_lib, ctx, pairs):
+    # pairs whose two CBs share a de-rate-matching map are de-rate-matched in
+    # one pass over it: here with different redundancy versions, with
+    # repetition (E = 19200 > Nv = 18444 at K = 6144, both CBs' LLRs still
+    # staged side by side), and next to a pair whose maps differ (a TB's
+    # first CB with filler bits beside one without) -- every d-stream,
+    # extrinsic and payload bit-exact
+    specs = [dict(A=6120, G=19200, Qm=2, P=128, rv=rv, max_iter=4, early_stop=0, seed=1300 + i,
+                  ebn0=1.5) for i, rv in enumerate((0, 2, 3, 1))]
+    specs += [dict(A=12200, G=36000, Qm=2, P=0, max_iter=4, early_stop=0, seed=1310, ebn0=1.5)]
+    tbs, llrs = batch(orc, specs)
+    g = run_gpu(crnt_lib, ctx, tbs, np.concatenate(llrs))
+    assert g["info"]["pair_items"] >= 2
+    check_batch(orc, crnt_lib, tbs, llrs, g)
