@@ -544,7 +544,33 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
         tB.tail[dst - tp3] = (int8_t)vB;
       }
     };
-    auto run = [&](auto vis) {
+    // two consecutive ranks r, r + 1 of both CBs (r even; Nv is even, so
+    // r + 1 < Nv): one 8-byte map read, the second offsets from the first
+    auto visit_two2 = [&](uint2 mm, int r) {
+      int kA = r - tA.rank0, kB = r - tB.rank0;
+      if (kA < 0) kA += Nv;
+      if (kB < 0) kB += Nv;
+      const int kA1 = kA + 1 == Nv ? 0 : kA + 1, kB1 = kB + 1 == Nv ? 0 : kB + 1;
+      const int d0 = (int)(mm.x & 0xFFFFu), d1 = (int)(mm.y & 0xFFFFu);
+      const int vA0 = kA < tA.E ? max((int)tA.e[kA], -127) : 0;
+      const int vB0 = kB < tB.E ? max((int)tB.e[kB], -127) : 0;
+      const int vA1 = kA1 < tA.E ? max((int)tA.e[kA1], -127) : 0;
+      const int vB1 = kB1 < tB.E ? max((int)tB.e[kB1], -127) : 0;
+      if (d0 < tp3) {
+        *(uint16_t*)(tA.base + 2 * d0) = (uint16_t)((vA0 & 0xFF) | ((vB0 & 0xFF) << 8));
+      } else {
+        tA.tail[d0 - tp3] = (int8_t)vA0;
+        tB.tail[d0 - tp3] = (int8_t)vB0;
+      }
+      if (d1 < tp3) {
+        *(uint16_t*)(tA.base + 2 * d1) = (uint16_t)((vA1 & 0xFF) | ((vB1 & 0xFF) << 8));
+      } else {
+        tA.tail[d1 - tp3] = (int8_t)vA1;
+        tB.tail[d1 - tp3] = (int8_t)vB1;
+      }
+    };
+    auto run = [&](auto vis, auto wide) {
+      constexpr bool WIDE = decltype(wide)::value;
       if (mbuf_bytes >= 2048) {
         // the map streamed through mbuf (free until the first SISO pass) in
         // two alternating chunks of ce entries, each one bulk copy; chunk c +
@@ -568,31 +594,41 @@ __device__ void derm_cb(const CbDesc& d, const CbSlot& sl, const int8_t* e,
           bulk_wait(bk, c & 1);
           const uint32_t* m = (const uint32_t*)mbuf + (c & 1) * ce;
           const int r0 = c * ce, r1 = min(Nv, r0 + ce);
+          if constexpr (WIDE) {
+            // ranks in pairs (r1 - r0 is even: Nv and ce are)
+#pragma unroll 2
+            for (int r = r0 + 2 * tid; r < r1; r += 2 * nthr)
+              vis(*(const uint2*)(m + (r - r0)), r);
+          } else {
 #pragma unroll 4
-          for (int r = r0 + tid; r < r1; r += nthr) vis(m[r - r0], r);
+            for (int r = r0 + tid; r < r1; r += nthr) vis(m[r - r0], r);
+          }
           __syncthreads();  // chunk c read by all: its buffer can be refilled
           if (tid == 0 && c + 2 < nch) {
             bulk_fence();
             issue(c + 2);
           }
         }
+      } else if constexpr (WIDE) {
+        for (int r = 2 * tid; r < Nv; r += 2 * nthr) vis(__ldg((const uint2*)(dm + r)), r);
       } else {
 #pragma unroll 8
         for (int r = tid; r < Nv; r += nthr) vis(__ldg(dm + r), r);
       }
     };
+    const std::false_type narrow{};
     const bool one = tA.soft == nullptr && E <= Nv && (!d2 || (tB.soft == nullptr && tB.E <= Nv));
     if (d2) {
       if (one && STR == 2 && tB.base == tA.base + 1)
-        run(visit_two);
+        run(visit_two2, std::true_type{});
       else if (one)
-        run([&](uint32_t m, int r) { visit_one(tA, m, r); visit_one(tB, m, r); });
+        run([&](uint32_t m, int r) { visit_one(tA, m, r); visit_one(tB, m, r); }, narrow);
       else
-        run([&](uint32_t m, int r) { visit(tA, m, r); visit(tB, m, r); });
+        run([&](uint32_t m, int r) { visit(tA, m, r); visit(tB, m, r); }, narrow);
     } else if (one) {
-      run([&](uint32_t m, int r) { visit_one(tA, m, r); });
+      run([&](uint32_t m, int r) { visit_one(tA, m, r); }, narrow);
     } else {
-      run([&](uint32_t m, int r) { visit(tA, m, r); });
+      run([&](uint32_t m, int r) { visit(tA, m, r); }, narrow);
     }
   }
   // otherwise rows x = unit * R + i, walked with (unit, i) updated incrementally
