@@ -369,10 +369,19 @@ int crnt_encode_batch(crnt_ctx* ctx, const crnt_tb_params* tbs, uint32_t n, cons
 int crnt_encode_tb(crnt_ctx* ctx, const uint8_t* bits, const crnt_tb_params* tb, uint8_t* e_out);
 
 /* ---- serving: continuous batching ------------------------------------- */
-/* Submit n TBs whose LLRs are host buffers llrs[i] (G_i bytes each).  The
- * LLRs are copied before return.  Work starts on the device as soon as
- * in-flight capacity and memory allow; tickets_out[i] receives a ticket.
- * CRNT_EAGAIN when admission is refused (nothing of the call is queued).
+/* Submit n TBs whose LLRs are host buffers llrs[i] (G_i bytes each) -- one
+ * subframe, say.  The TBs are prepared (segmentation, soft-buffer binding,
+ * descriptors) and their LLRs copied on the calling thread before return;
+ * the serving worker batches and launches them; tickets_out[i] receives a
+ * ticket.  CRNT_EAGAIN when admission is refused, and nothing of the call is
+ * queued: beyond max_inflight TBs, when the library's page-locked LLR or
+ * output ring is full (results not yet polled hold output space), or --
+ * with crnt_config.admission 0 -- when the call's predicted completion
+ * passes deadline_us while other work is outstanding (the prediction is
+ * fitted to the completions seen: latency against the decode work ahead).
+ * If a TB fails its preparation (another code) nothing is queued either, but
+ * soft buffers already bound for earlier CRNT_F_HARQ TBs of the call stay
+ * bound.
  * TBs that share a HARQ key (cell, ue, harq_pid) must not be in flight at
  * the same time (a retransmission is submitted after the previous
  * transmission's result was polled, as the HARQ round trip implies).
