@@ -70,12 +70,14 @@ struct Req {
 // leaves X nearly constant, keeps a sensible slope.  The residuals' spread
 // sigma gives the margin: a subframe is refused when a + b X + z sigma
 // passes the deadline, unless nothing at all is outstanding.  The fit is
-// robust to single stalls (a TB that waited for a one-time allocation, a
-// descheduled thread): each latency enters clipped to within max(4 sigma,
-// 100 us) of the current prediction, so one outlier moves the fit and the
-// spread by a bounded step, while a lasting change still moves them batch by
-// batch; and the rate stays above 5e10 units/s (a full batch at the
-// iteration limit drains ~1.2e11).
+// robust to stalls (TBs that waited for a one-time allocation, a descheduled
+// thread): a latency above 8 deadlines is a stall, not queueing, and is left
+// out; the others enter clipped to within max(2 sigma, 50 us) of the current
+// prediction, so one outlier moves the fit and the spread by a bounded step
+// (sigma at most doubles per batch) while a lasting change still moves them
+// batch by batch; sigma stays at or below a sixth of the deadline (so that
+// the margin alone never refuses everything); and the rate stays above 5e10
+// units/s (a full batch at the iteration limit drains ~1.2e11).
 struct Admission {
   static constexpr double kA0 = 150.0;     // prior latency with nothing ahead (us)
   static constexpr double kB0 = 1.0e-5;    // prior us per unit of work (1e11 units/s)
@@ -90,11 +92,12 @@ struct Admission {
   double predict(double x) const { return a + b * x + kZ * sigma; }
   // a latency observation as it enters the fit
   double clip(double x, double y) const {
-    const double p = a + b * x, m = std::max(4.0 * sigma, 100.0);
+    const double p = a + b * x, m = std::max(2.0 * sigma, 50.0);
     return std::min(p + m, std::max(p - m, y));
   }
   // Fold in one batch's sums (n observations) and refit.
-  void update(double n, double bw, double bx, double by, double bxx, double bxy, double byy) {
+  void update(double n, double bw, double bx, double by, double bxx, double bxy, double byy,
+              double sigma_max) {
     const double f = std::exp(-n / kMemory);
     sw = sw * f + bw;
     sx = sx * f + bx;
@@ -112,7 +115,7 @@ struct Admission {
     if (sw > 0) {
       const double sse = syy - 2 * a * sy - 2 * b * sxy + a * a * sw + 2 * a * b * sx +
                          b * b * sxx;
-      sigma = std::max(10.0, std::sqrt(std::max(0.0, sse / sw)));
+      sigma = std::min(sigma_max, std::max(10.0, std::sqrt(std::max(0.0, sse / sw))));
     }
   }
 };
@@ -268,14 +271,16 @@ void Serving::harvest(Slot* s, bool failed) {
     d.res.t_done_ns = (uint64_t)t_done;
     late += t_done - r.t_submit > deadline;
     // (the worker is the model's only writer, so it reads it without the lock)
-    const double x = r.ahead, y = adm.clip(x, (double)(t_done - r.t_submit) * 1e-3);
+    const double y_raw = (double)(t_done - r.t_submit) * 1e-3;
+    work += r.work;
+    if (y_raw > 8e-3 * (double)deadline) continue;  // a stall: nothing to learn
+    const double x = r.ahead, y = adm.clip(x, y_raw);
     bw += 1;
     bx += x;
     by += y;
     bxx += x * x;
     bxy += x * y;
     byy += y * y;
-    work += r.work;
   }
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -283,7 +288,7 @@ void Serving::harvest(Slot* s, bool failed) {
     for (auto& r : s->reqs) ring.release(r.alloc);
     inflight_tbs -= n;
     work_out = inflight_tbs ? std::max(0.0, work_out - work) : 0.0;
-    if (!failed) adm.update((double)n, bw, bx, by, bxx, bxy, byy);
+    if (!failed) adm.update((double)n, bw, bx, by, bxx, bxy, byy, ctx->cfg.deadline_us / 6.0);
     st.done_tbs += n;
     st.late_tbs += late;
   }
