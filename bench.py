@@ -33,6 +33,8 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "decoded info Gbit/s per GB300 at 6 iters"
+LEGS = ("steady", "e2e", "subframe", "serving", "single_cb", "captor", "pusch", "radix4",
+        "encoder", "cpu_baseline")
 OPS_PER_STEP = 98        # algorithmic int ops per trellis step of one SISO pass
 LANES_PER_SM = 128       # int32 lanes issuing per SM per clock (4 SMSPs x 32)
 WORKLOAD = ("batched uneven load: 40 cells x 8 UEs per 1 ms TTI (320 TBs), A uniform over "
@@ -63,16 +65,19 @@ def parse():
                          "per thread, 2 CB pairs in 16-bit lanes)")
     ap.add_argument("--no-extras", action="store_true", help="skip latency / e2e / cpu legs")
     ap.add_argument("--legs", default=None,
-                    help="comma-separated subset of the extra legs to run (steady, e2e, "
-                         "subframe, serving, single_cb, captor, pusch, radix4, encoder, "
-                         "cpu_baseline); default all")
+                    help="comma-separated subset of the extra legs to run (%s); default all"
+                         % ", ".join(LEGS))
     ap.add_argument("--sweep", choices=["bler", "stop", "peak"],
                     help="quality sweep instead of the bench line (stop: CRC vs mutual "
                          "information stop rule)")
     ap.add_argument("--bler-cbs", type=int, default=0,
                     help="CBs per (K, P, Eb/N0) point (0: 1e6 for K=40, 1e5 for K=6144 "
                          "with P>=16, 2e4 for P=4 and 1e4 for P=1)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    unknown = set(args.legs.split(",")) - set(LEGS) if args.legs else set()
+    if unknown:
+        ap.error("unknown legs: %s (known: %s)" % (", ".join(sorted(unknown)), ", ".join(LEGS)))
+    return args
 
 
 def dist_env():
