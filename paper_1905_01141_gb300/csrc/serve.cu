@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "runtime.h"
+#include "serve_model.h"
 
 namespace crnt {
 
@@ -56,108 +57,6 @@ struct Req {
   int64_t t_submit;
   double work;       // expected decode work: trellis steps x iteration limit
   double ahead;      // outstanding work when its subframe was admitted (itself included)
-};
-
-// Admission by predicted completion.  A TB admitted now finishes, on
-// average, a + b X after its submission, where X is the expected decode
-// work -- trellis steps times the iteration limit -- of every TB admitted
-// and not yet finished, its own subframe's included: the work ahead of it
-// drains at a rate 1/b, and a covers the launch, one decode and the
-// collection.  (a, b) is refitted by least squares, with exponential
-// forgetting, to the completions seen -- each TB gives one (X at its
-// admission, latency) pair -- and held near prior values by a penalty that
-// counts as a few pseudo-observations, so a cold start, or a load that
-// leaves X nearly constant, keeps a sensible slope.  The residuals' spread
-// sigma gives the margin: a subframe is refused when a + b X + z sigma
-// passes the deadline, unless nothing at all is outstanding.  The fit is
-// robust to stalls (TBs that waited for a one-time allocation, a descheduled
-// thread): a latency above 8 deadlines is a stall, not queueing, and is left
-// out; the others enter clipped to within max(2 sigma, 50 us) of the current
-// prediction, so one outlier moves the fit and the spread by a bounded step
-// (sigma at most doubles per batch) while a lasting change still moves them
-// batch by batch; sigma stays at or below a sixth of the deadline (so that
-// the margin alone never refuses everything); and the rate stays above 5e10
-// units/s (a full batch at the iteration limit drains ~1.2e11).
-struct Admission {
-  static constexpr double kA0 = 150.0;     // prior latency with nothing ahead (us)
-  static constexpr double kB0 = 1.0e-5;    // prior us per unit of work (1e11 units/s)
-  static constexpr double kBmin = 2.0e-6;  // at most 5e11 units/s (~4x a full decode)
-  static constexpr double kBmax = 2.0e-5;  // at least 5e10 units/s
-  static constexpr double kPrior = 16.0;   // weight of the prior, in observations
-  static constexpr double kXs = 2.0e7;     // work scale at which the slope prior acts
-  static constexpr double kMemory = 50000.0;  // TBs after which an observation's weight is 1/e
-  static constexpr double kZ = 3.0;
-  double sw = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
-  double a = kA0, b = kB0, sigma = 50.0;
-  double predict(double x) const { return a + b * x + kZ * sigma; }
-  // a latency observation as it enters the fit
-  double clip(double x, double y) const {
-    const double p = a + b * x, m = std::max(2.0 * sigma, 50.0);
-    return std::min(p + m, std::max(p - m, y));
-  }
-  // Fold in one batch's sums (n observations) and refit.
-  void update(double n, double bw, double bx, double by, double bxx, double bxy, double byy,
-              double sigma_max) {
-    const double f = std::exp(-n / kMemory);
-    sw = sw * f + bw;
-    sx = sx * f + bx;
-    sy = sy * f + by;
-    sxx = sxx * f + bxx;
-    sxy = sxy * f + bxy;
-    syy = syy * f + byy;
-    const double ka = kPrior, kb = kPrior * kXs * kXs;
-    const double m00 = sw + ka, m01 = sx, m11 = sxx + kb;
-    const double v0 = sy + ka * kA0, v1 = sxy + kb * kB0;
-    const double det = m00 * m11 - m01 * m01;
-    if (!(det > 0)) return;
-    a = std::min(2000.0, std::max(10.0, (v0 * m11 - m01 * v1) / det));
-    b = std::min(kBmax, std::max(kBmin, (m00 * v1 - m01 * v0) / det));
-    if (sw > 0) {
-      const double sse = syy - 2 * a * sy - 2 * b * sxy + a * a * sw + 2 * a * b * sx +
-                         b * b * sxx;
-      sigma = std::min(sigma_max, std::max(10.0, std::sqrt(std::max(0.0, sse / sw))));
-    }
-  }
-};
-
-// Ring holding the LLRs of queued and running requests, released in
-// allocation order.  Each allocation is contiguous.
-struct Ring {
-  size_t cap = 0, head = 0, tail = 0;
-  struct A {
-    size_t end;
-    bool done;
-  };
-  std::deque<A> q;
-  uint64_t first_seq = 0;  // sequence number of q.front()
-  bool alloc(size_t n, size_t* off, uint64_t* seq) {
-    if (q.empty()) head = tail = 0;
-    if (head >= tail) {  // free space: [head, cap) and [0, tail)
-      if (cap - head >= n) {
-        *off = head;
-      } else if (tail > n) {
-        *off = 0;
-      } else {
-        return false;
-      }
-    } else if (tail - head > n) {  // free space: [head, tail)
-      *off = head;
-    } else {
-      return false;
-    }
-    head = *off + n;
-    *seq = first_seq + q.size();
-    q.push_back(A{head, false});
-    return true;
-  }
-  void release(uint64_t seq) {
-    q[seq - first_seq].done = true;
-    while (!q.empty() && q.front().done) {
-      tail = q.front().end;
-      q.pop_front();
-      first_seq++;
-    }
-  }
 };
 
 struct Done {
@@ -252,7 +151,8 @@ void Serving::harvest(Slot* s, bool failed) {
   }
   uint64_t late = 0;
   const int64_t deadline = (int64_t)ctx->cfg.deadline_us * 1000;
-  double bw = 0, bx = 0, by = 0, bxx = 0, bxy = 0, byy = 0, work = 0;
+  Admission::Batch bt;
+  double work = 0;
   for (uint32_t i = 0; i < n; i++) {
     Done& d = out[i];
     const Req& r = s->reqs[i];
@@ -271,16 +171,8 @@ void Serving::harvest(Slot* s, bool failed) {
     d.res.t_done_ns = (uint64_t)t_done;
     late += t_done - r.t_submit > deadline;
     // (the worker is the model's only writer, so it reads it without the lock)
-    const double y_raw = (double)(t_done - r.t_submit) * 1e-3;
     work += r.work;
-    if (y_raw > 8e-3 * (double)deadline) continue;  // a stall: nothing to learn
-    const double x = r.ahead, y = adm.clip(x, y_raw);
-    bw += 1;
-    bx += x;
-    by += y;
-    bxx += x * x;
-    bxy += x * y;
-    byy += y * y;
+    adm.observe(bt, r.ahead, (double)(t_done - r.t_submit) * 1e-3, (double)ctx->cfg.deadline_us);
   }
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -288,7 +180,7 @@ void Serving::harvest(Slot* s, bool failed) {
     for (auto& r : s->reqs) ring.release(r.alloc);
     inflight_tbs -= n;
     work_out = inflight_tbs ? std::max(0.0, work_out - work) : 0.0;
-    if (!failed) adm.update((double)n, bw, bx, by, bxx, bxy, byy, ctx->cfg.deadline_us / 6.0);
+    if (!failed) adm.update(bt, (double)ctx->cfg.deadline_us);
     st.done_tbs += n;
     st.late_tbs += late;
   }
