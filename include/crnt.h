@@ -398,8 +398,13 @@ int crnt_poll(crnt_ctx* ctx, crnt_tb_result* done, const uint8_t** bits, uint32_
 int crnt_harq_release(crnt_ctx* ctx, uint32_t cell, uint32_t ue, uint32_t harq_pid);
 
 /* Serving counters since the context's serving loop started (all zero
- * before the first crnt_submit).  Cumulative: take differences to measure
- * an interval.  A subframe is one crnt_submit call. */
+ * before the first crnt_submit) -- the serving side of the paper's
+ * performance captor (Sec. IV-B): where time goes between submission and
+ * result, and what admission turned away.  Cumulative: take differences to
+ * measure an interval.  A subframe is one crnt_submit call.  Safe to call
+ * from any thread while serving runs (a consistent snapshot of the counts;
+ * the time counters are read separately).  Returns CRNT_OK, or CRNT_EINVAL
+ * for a null argument. */
 typedef struct crnt_serve_stats {
     uint64_t submit_calls;     /* crnt_submit calls that reached admission */
     uint64_t refused_calls;    /* of which refused with CRNT_EAGAIN */
@@ -409,7 +414,7 @@ typedef struct crnt_serve_stats {
     uint64_t done_tbs;         /* results handed to the done queue */
     uint64_t late_tbs;         /* of which finished later than submit + deadline_us */
     uint64_t batches;          /* decode launches of the serving worker */
-    uint64_t worker_plan_ns;   /* worker time building plans */
+    uint64_t worker_plan_ns;   /* worker time assembling batches (plans of prepared TBs) */
     uint64_t worker_launch_ns; /* worker time in launch calls */
     uint64_t worker_harvest_ns;/* worker time collecting finished batches */
     uint64_t worker_ns;        /* wall time since the loop started */
